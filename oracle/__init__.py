@@ -1,0 +1,129 @@
+"""Python front for the CPU oracle (oracle.c) -- TEST INFRASTRUCTURE ONLY.
+
+Only the test suite, ``__graft_entry__.smoke()`` and ``bench.py``'s CPU
+baseline leg import this package. It shares nothing with the GPU engine.
+"""
+import ctypes
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+from . import build as _build
+
+PIVOT_FULL, PIVOT_IP, NO_PIVOT = 0, 1, 2
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        lib = ctypes.CDLL(_build.build())
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        u64p = ctypes.POINTER(ctypes.c_uint64)
+        lib.oracle_validate.argtypes = [ctypes.c_int32, i32p, i32p]
+        lib.oracle_peel.argtypes = [ctypes.c_int32, i32p, i32p, i32p, i32p, i32p]
+        lib.oracle_peel.restype = ctypes.c_int64
+        lib.oracle_mce.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                   u64p, u64p, u64p, ctypes.c_int32, i32p, u64p, u64p, u64p]
+        lib.oracle_mce_roots.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                         i32p, ctypes.c_int64, u64p, u64p, u64p, ctypes.c_int32,
+                                         i32p, u64p, u64p, u64p]
+        lib.oracle_clique_hash.argtypes = [i32p, ctypes.c_int32]
+        lib.oracle_clique_hash.restype = ctypes.c_uint64
+        lib.oracle_default_threads.restype = ctypes.c_int32
+        _lib = lib
+    return _lib
+
+
+def _i32(a):
+    a = np.ascontiguousarray(a, dtype=np.int32)
+    return a, a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+
+
+def _u64(a):
+    if a is None:
+        return None
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+
+
+@dataclass
+class Result:
+    count: int
+    hash: int
+    hist: np.ndarray          # hist[k] = number of maximal cliques of size k
+    max_size: int
+    root_count: Optional[np.ndarray] = None   # per input vertex id
+    root_hash: Optional[np.ndarray] = None
+    root_nodes: Optional[np.ndarray] = None
+
+
+def validate(row_ptr, col) -> bool:
+    rp, rpp = _i32(row_ptr)
+    c, cp = _i32(col if len(col) else np.zeros(1, np.int32))
+    return _load().oracle_validate(len(rp) - 1, rpp, cp) == 0
+
+
+def peel(row_ptr, col):
+    """(core, rank, order, sub_rounds) of the level-synchronous peel."""
+    rp, rpp = _i32(row_ptr)
+    c, cp = _i32(col if len(col) else np.zeros(1, np.int32))
+    n = len(rp) - 1
+    core = np.zeros(max(n, 1), np.int32)
+    rank = np.zeros(max(n, 1), np.int32)
+    order = np.zeros(max(n, 1), np.int32)
+    P = ctypes.POINTER(ctypes.c_int32)
+    rounds = _load().oracle_peel(n, rpp, cp, core.ctypes.data_as(P), rank.ctypes.data_as(P),
+                                 order.ctypes.data_as(P))
+    if rounds < 0:
+        raise MemoryError("oracle_peel failed")
+    return core[:n], rank[:n], order[:n], int(rounds)
+
+
+def mce(row_ptr, col, mode: int = PIVOT_FULL, threads: int = 0, per_root: bool = False,
+        roots=None, hist_len: int = 0) -> Result:
+    """All maximal cliques (or those of the listed roots' first-level subtrees)."""
+    rp, rpp = _i32(row_ptr)
+    c, cp = _i32(col if len(col) else np.zeros(1, np.int32))
+    n = len(rp) - 1
+    if hist_len <= 0:
+        hist_len = int(np.diff(rp).max()) + 2 if n else 2
+    hist = np.zeros(hist_len, np.uint64)
+    cnt = ctypes.c_uint64()
+    hsh = ctypes.c_uint64()
+    mx = ctypes.c_int32()
+    rc_arr = rh_arr = rn_arr = None
+    if per_root:
+        rc_arr = np.zeros(max(n, 1), np.uint64)
+        rh_arr = np.zeros(max(n, 1), np.uint64)
+        rn_arr = np.zeros(max(n, 1), np.uint64)
+    lib = _load()
+    if roots is None:
+        rc = lib.oracle_mce(n, rpp, cp, mode, threads, ctypes.byref(cnt), ctypes.byref(hsh),
+                            _u64(hist), hist_len, ctypes.byref(mx), _u64(rc_arr), _u64(rh_arr),
+                            _u64(rn_arr))
+    else:
+        ro, rop = _i32(roots)
+        rc = lib.oracle_mce_roots(n, rpp, cp, mode, threads, rop, len(ro), ctypes.byref(cnt),
+                                  ctypes.byref(hsh), _u64(hist), hist_len, ctypes.byref(mx),
+                                  _u64(rc_arr), _u64(rh_arr), _u64(rn_arr))
+    if rc == 1:
+        raise ValueError("oracle: invalid graph")
+    if rc == 2:
+        raise MemoryError("oracle: out of memory")
+    if rc == 5:
+        raise RuntimeError("oracle: hist_len too short")
+    res = Result(int(cnt.value), int(hsh.value), hist[: mx.value + 1].copy(), int(mx.value))
+    if per_root:
+        res.root_count, res.root_hash, res.root_nodes = rc_arr[:n], rh_arr[:n], rn_arr[:n]
+    return res
+
+
+def clique_hash(ids) -> int:
+    a, ap = _i32(ids)
+    return int(_load().oracle_clique_hash(ap, len(a)))
+
+
+def default_threads() -> int:
+    return int(_load().oracle_default_threads())

@@ -1,0 +1,296 @@
+"""Pins for the CPU oracle: closed forms, the paper's worked example, brute
+force over all vertex subsets, cross-checks between Algorithms 1 and 2,
+permutation invariance, disjoint-union additivity and the degeneracy
+peel's properties. None of these expected values comes from the GPU engine,
+and none re-calls the oracle's own routines to produce an expected value."""
+import itertools
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+import oracle
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+M64 = (1 << 64) - 1
+
+
+# ----- independent restatement of the clique hash (definition, not the oracle's code)
+def _mix(z):
+    z &= M64
+    z = ((z ^ (z >> 30)) * 0xBF58476D1CE4E5B9) & M64
+    z = ((z ^ (z >> 27)) * 0x94D049BB133111EB) & M64
+    return z ^ (z >> 31)
+
+
+def h_clique(ids):
+    s = sum(_mix(int(c) + 1) for c in ids) & M64
+    return _mix(s + len(ids) * 0x9E3779B97F4A7C15)
+
+
+def summarise(cliques):
+    cliques = [tuple(sorted(c)) for c in cliques]
+    hist = {}
+    for c in cliques:
+        hist[len(c)] = hist.get(len(c), 0) + 1
+    return len(cliques), hist, sum(h_clique(c) for c in cliques) & M64
+
+
+def hist_dict(arr):
+    return {k: int(v) for k, v in enumerate(arr) if v}
+
+
+def brute_force(g):
+    """All maximal cliques by enumerating every vertex subset (n <= 16)."""
+    n = g.n
+    assert n <= 16
+    adj = np.zeros(n, np.int64)
+    for v in range(n):
+        for u in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+            adj[v] |= 1 << int(u)
+    S = np.arange(1 << n, dtype=np.int64)
+    clique = np.ones(S.shape, bool)
+    for v in range(n):
+        inS = (S >> v) & 1 == 1
+        clique &= ~inS | ((S & ~(adj[v] | (1 << v))) == 0)
+    maximal = clique.copy()
+    for w in range(n):
+        inS = (S >> w) & 1 == 1
+        maximal &= inS | ((S & ~adj[w]) != 0)
+    out = []
+    for s in S[maximal]:
+        out.append([v for v in range(n) if (int(s) >> v) & 1])
+    return out
+
+
+def run_all_modes(g):
+    return [oracle.mce(g.row_ptr, g.col, mode=m, threads=2) for m in
+            (oracle.PIVOT_FULL, oracle.PIVOT_IP, oracle.NO_PIVOT)]
+
+
+def check(g, cliques):
+    cnt, hist, hsh = summarise(cliques)
+    for r in run_all_modes(g):
+        assert r.count == cnt
+        assert hist_dict(r.hist) == hist
+        assert r.hash == hsh
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("n", [1, 2, 3, 5, 8, 13])
+def test_complete_graph(n):
+    check(gen.complete(n), [list(range(n))])
+
+
+@pytest.mark.parametrize("n", [0, 1, 4, 17])
+def test_empty_graph(n):
+    check(gen.empty(n), [[v] for v in range(n)])
+
+
+@pytest.mark.parametrize("n", [4, 5, 9, 30])
+def test_cycle(n):
+    check(gen.cycle(n), [[i, (i + 1) % n] for i in range(n)])
+
+
+def test_triangle_is_cycle_3():
+    check(gen.cycle(3), [[0, 1, 2]])
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4, 6, 7])
+def test_moon_moser(k):
+    # K_{3,...,3}: a maximal clique picks exactly one vertex from each part
+    g = gen.moon_moser(k)
+    cl = [list(p) for p in itertools.product(*[range(3 * i, 3 * i + 3) for i in range(k)])]
+    assert len(cl) == 3 ** k
+    check(g, cl)
+
+
+@pytest.mark.parametrize("k", [1, 3, 5, 8])
+def test_cocktail_party(k):
+    g = gen.multipartite(k, 2)
+    cl = [list(p) for p in itertools.product(*[range(2 * i, 2 * i + 2) for i in range(k)])]
+    assert len(cl) == 2 ** k
+    check(g, cl)
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_forest(seed):
+    g = gen.random_forest(40, seed)
+    deg = g.degrees()
+    cl = [[v] for v in range(g.n) if deg[v] == 0]
+    for v in range(g.n):
+        for u in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+            if v < u:
+                cl.append([v, int(u)])
+    check(g, cl)
+
+
+def test_worked_example_golden():
+    with open(os.path.join(GOLDEN, "worked_example.json")) as f:
+        fx = json.load(f)
+    idx = {name: i for i, name in enumerate(fx["vertices"])}
+    g = gen.from_edges(len(idx), [(idx[a], idx[b]) for a, b in fx["edges"]])
+    deg = g.degrees()
+    assert int(deg.argmax()) == idx[fx["max_degree_vertex"]] and deg.max() == fx["max_degree"]
+    check(g, [[idx[v] for v in c] for c in fx["maximal_cliques"]])
+    assert g.n == len(gen.worked_example().row_ptr) - 1
+    assert np.array_equal(g.col, gen.worked_example().col)
+
+
+# ------------------------------------------------------------------ brute force
+
+@pytest.mark.parametrize("n,p,seed", [(n, p, s) for n in (6, 11, 16) for p in (0.1, 0.3, 0.5, 0.7, 0.9)
+                                      for s in (0, 1)])
+def test_brute_force(n, p, seed):
+    g = gen.small_gnp(n, p, seed)
+    check(g, brute_force(g))
+
+
+# ------------------------------------------------------- cross-checks / invariants
+
+@pytest.mark.parametrize("seed", range(4))
+def test_algorithms_agree_midsize(seed):
+    g = gen.gnp(300, 0.08 + 0.04 * seed, seed)
+    full, ip, nopiv = run_all_modes(g)
+    for r in (ip, nopiv):
+        assert (r.count, r.hash, r.max_size) == (full.count, full.hash, full.max_size)
+        assert np.array_equal(r.hist, full.hist)
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_permutation_invariance(seed):
+    g = gen.gnp(120, 0.15, seed)
+    perm = np.random.default_rng(seed).permutation(g.n)
+    gp = gen.relabel(g, perm)
+    a = oracle.mce(g.row_ptr, g.col)
+    b = oracle.mce(gp.row_ptr, gp.col)
+    assert a.count == b.count and np.array_equal(a.hist, b.hist)
+    # small case: the permuted cliques' hash equals the hash of the mapped cliques
+    g = gen.small_gnp(14, 0.5, seed)
+    perm = np.random.default_rng(seed + 10).permutation(g.n)
+    gp = gen.relabel(g, perm)
+    mapped = [[int(perm[v]) for v in c] for c in brute_force(g)]
+    assert oracle.mce(gp.row_ptr, gp.col).hash == summarise(mapped)[2]
+
+
+def test_disjoint_union_additive():
+    parts = [gen.gnp(80, 0.2, 5), gen.moon_moser(4), gen.complete(6), gen.empty(3)]
+    u = gen.disjoint_union(parts)
+    ru = oracle.mce(u.row_ptr, u.col)
+    tot_c, tot_h, hist = 0, 0, {}
+    for gpart, off in zip(parts, u.graph_ptr[:-1]):
+        # shift ids: build the part's graph with ids offset, through from_edges
+        src = np.repeat(np.arange(gpart.n), gpart.degrees())
+        e = np.stack([src, gpart.col], 1)
+        shifted = gen.from_edges(u.n, (e + int(off)).tolist())
+        # isolated vertices of other parts would add size-1 cliques; restrict via roots
+        r = oracle.mce(shifted.row_ptr, shifted.col,
+                       roots=np.arange(off, off + gpart.n, dtype=np.int32))
+        tot_c += r.count
+        tot_h = (tot_h + r.hash) & M64
+        for k, v in hist_dict(r.hist).items():
+            hist[k] = hist.get(k, 0) + v
+    assert ru.count == tot_c and ru.hash == tot_h and hist_dict(ru.hist) == hist
+
+
+def test_per_root_sums_match_totals():
+    g = gen.gnp(500, 0.05, 9)
+    r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=True)
+    assert int(r.root_count.sum()) == r.count
+    assert int(r.root_hash.astype(object).sum()) & M64 == r.hash
+    sub = np.array([3, 77, 499, 0], np.int32)
+    rs = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, roots=sub, per_root=True)
+    assert rs.count == int(r.root_count[sub].sum())
+    assert np.array_equal(rs.root_nodes[sub], r.root_nodes[sub])
+
+
+@pytest.mark.parametrize("n", [2, 5, 9])
+def test_node_counts_complete_graph(n):
+    # K_n: the peel removes every vertex in one sub-round, ranks = ids.
+    # Full Tomita: root 0 walks a chain of n calls; every later root's X holds
+    # vertex 0, adjacent to all of P, so it is the pivot and no branch exists.
+    g = gen.complete(n)
+    full = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_FULL, per_root=True)
+    assert full.root_nodes.tolist() == [n] + [1] * (n - 1)
+    # pivot restricted to P u X_P: root r walks a chain of n - r calls
+    ip = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=True)
+    assert ip.root_nodes.tolist() == [n - r for r in range(n)]
+    assert ip.root_count.tolist() == [1] + [0] * (n - 1)
+
+
+# ------------------------------------------------------------ degeneracy peel
+
+def naive_cores(g):
+    """Sequential min-degree peel (Matula-Beck), O(n^2): core numbers."""
+    n = g.n
+    deg = g.degrees().astype(np.int64)
+    alive = np.ones(n, bool)
+    core = np.zeros(n, np.int64)
+    k = 0
+    for _ in range(n):
+        d = np.where(alive, deg, np.iinfo(np.int64).max)
+        v = int(d.argmin())
+        k = max(k, int(deg[v]))
+        core[v] = k
+        alive[v] = False
+        for u in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+            deg[u] -= 1
+    return core
+
+
+@pytest.mark.parametrize("maker", [lambda: gen.workload("er_2000"), lambda: gen.gnp(400, 0.05, 3),
+                                   lambda: gen.moon_moser(5), gen.worked_example,
+                                   lambda: gen.random_forest(100, 4), lambda: gen.cycle(12)])
+def test_peel_properties(maker):
+    g = maker()
+    core, rank, order, rounds = oracle.peel(g.row_ptr, g.col)
+    assert np.array_equal(core, naive_cores(g))
+    assert np.array_equal(np.sort(rank), np.arange(g.n))
+    assert np.array_equal(order[rank], np.arange(g.n))
+    src = np.repeat(np.arange(g.n), g.degrees())
+    later = np.bincount(src[rank[g.col] > rank[src]], minlength=g.n)
+    assert (later <= core).all()           # |P| <= core(v) <= d (Sec. II-C)
+    # core is non-decreasing along the order
+    assert (np.diff(core[order]) >= 0).all()
+    assert rounds >= 1 or g.n == 0
+
+
+def test_worked_example_order():
+    # Sec. II-C: after degeneracy ordering A has no later neighbours. Our
+    # tie-break (ascending id within a peel sub-round) removes E and F first
+    # (core 2), then A, B, C, D together (core 3); A's later neighbours are
+    # B, C, D, which is within the degeneracy d = 3.
+    g = gen.worked_example()
+    core, rank, order, _ = oracle.peel(g.row_ptr, g.col)
+    assert core.tolist() == [3, 3, 3, 3, 2, 2]
+    assert order.tolist() == [4, 5, 0, 1, 2, 3]
+
+
+# ----------------------------------------------------------------- validation
+
+@pytest.mark.parametrize("bad", ["unsorted", "asym", "loop", "dup", "range", "rowptr"])
+def test_validate_rejects(bad):
+    g = gen.gnp(30, 0.3, 1)
+    rp, col = g.row_ptr.copy(), g.col.copy()
+    v = int(np.argmax(np.diff(rp) >= 2))
+    a, b = rp[v], rp[v + 1]
+    if bad == "unsorted":
+        col[a], col[a + 1] = col[a + 1], col[a]
+    elif bad == "asym":
+        col = col.copy()
+        col[a] = [x for x in range(30) if x != v and x not in set(col[a:b])][0]
+        col[a:b] = np.sort(col[a:b])
+    elif bad == "loop":
+        col[a] = v
+        col[a:b] = np.sort(col[a:b])
+    elif bad == "dup":
+        col[a + 1] = col[a]
+    elif bad == "range":
+        col[b - 1] = 30
+    elif bad == "rowptr":
+        rp[5] = rp[6] + 1
+    assert oracle.validate(g.row_ptr, g.col)
+    assert not oracle.validate(rp, col)
