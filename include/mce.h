@@ -1,0 +1,184 @@
+/*
+ * mce.h -- C ABI of the GB300 (sm_103a) maximal clique enumeration engine.
+ *
+ * The engine enumerates every maximal clique of a simple undirected graph by
+ * Bron-Kerbosch with pivoting (Algorithm 2 of "Parallelizing Maximal Clique
+ * Enumeration on GPUs", Sec. II-B), over one independent first-level subtree
+ * per vertex (Algorithm 3, Sec. II-C) in degeneracy order (Sec. II-C), with
+ * each subtree walked depth-first on the GPU over bitset-encoded induced
+ * subgraphs (Sec. III-A, III-D), a compact excluded set (Sec. III-E) and a
+ * worker list for dynamic load balancing (Sec. III-C).
+ *
+ * Results are exact integers: the number of maximal cliques, the clique-size
+ * histogram, and an order-independent 64-bit hash of the cliques,
+ *     hash = sum over maximal cliques C of h(C)  (mod 2^64),
+ *     h(C) = mix( sum_{c in C} mix(c + 1) + |C| * 0x9E3779B97F4A7C15 ),
+ * with c the INPUT vertex ids and mix the SplitMix64 output finaliser
+ * (z ^= z>>30; z *= 0xBF58476D1CE4E5B9; z ^= z>>27; z *= 0x94D049BB133111EB;
+ * z ^= z>>31). The paper reports counts only (Sec. IV-A); the histogram and
+ * the hash are added so that results can be compared exactly.
+ *
+ * Conventions shared by every entry point:
+ *   - Return value: an MCE_* status. On failure nothing is written to the
+ *     outputs unless stated; mce_last_error() gives a message.
+ *   - Graphs are CSR with int32 ids and offsets: row_ptr[n+1], col[row_ptr[n]],
+ *     each row sorted ascending, symmetric, no self-loops, no duplicates.
+ *     Input that breaks any of these is rejected with MCE_EINVAL.
+ *   - Ownership: the engine copies what it needs; caller buffers are never
+ *     retained after a call returns.
+ *   - Streams: all GPU work of a handle runs on the stream given at create
+ *     time (NULL = a stream the handle creates). Every call is synchronous
+ *     with respect to the host on return.
+ *   - Threading: one handle must not be used by two host threads at once;
+ *     distinct handles are independent.
+ */
+#ifndef MCE_H
+#define MCE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ------------------------------------------------------------ status codes */
+#define MCE_OK 0
+#define MCE_EINVAL 1       /* bad argument or non-canonical graph */
+#define MCE_ENOMEM 2       /* device or host allocation failed */
+#define MCE_ECUDA 3        /* a CUDA call failed (message has the CUDA error) */
+#define MCE_ETIMEOUT 4     /* a device wait exceeded opts.timeout_ms; results discarded */
+#define MCE_ERANGE 5       /* hist_len <= max clique size; out->max_size is still set */
+#define MCE_EUNSUPPORTED 6 /* graph beyond the engine's limits (degeneracy > MCE_MAX_DEGENERACY) */
+
+/* largest degeneracy (= largest per-root candidate set |P|) the engine handles */
+#define MCE_MAX_DEGENERACY 4096
+
+/* create flags */
+#define MCE_FLAG_DEVICE_PTRS 1u /* row_ptr/col (and graph_ptr) are device pointers */
+
+/* pivot selection (Sec. III-D, III-E, IV-D) */
+#define MCE_PIVOT_AUTO 0 /* IP when max_degree/degeneracy > 200, else IPX (Sec. IV-D heuristic) */
+#define MCE_PIVOT_IP 1   /* pivot from P u X_P (partial induced subgraph) */
+#define MCE_PIVOT_IPX 2  /* pivot from P u X_P u X_X (full induced subgraph) */
+
+/* root ordering */
+#define MCE_ORDER_PLAIN 0   /* roots in degeneracy order within each width class */
+#define MCE_ORDER_PRIORITY 1/* roots by descending opts.root_priority (e.g. learned work estimate) */
+
+typedef struct mce_graph mce_graph; /* opaque; owns its device copies */
+
+/*
+ * Optional device allocator. When given, every device allocation of the
+ * handle goes through it (e.g. the PyTorch caching allocator); otherwise the
+ * engine uses cudaMallocAsync/cudaFreeAsync on the handle's stream.
+ * alloc returns NULL on failure (the call then fails with MCE_ENOMEM).
+ */
+typedef struct {
+    void *(*alloc)(size_t bytes, void *ctx);
+    void (*free)(void *ptr, void *ctx);
+    void *ctx;
+} mce_allocator;
+
+typedef struct {
+    int32_t struct_size;   /* sizeof(mce_opts); set by mce_default_opts */
+    int32_t pivot;         /* MCE_PIVOT_* */
+    int32_t order;         /* MCE_ORDER_* */
+    int32_t worker_list;   /* 1 = idle workers receive donated subtrees (Sec. III-C), 0 = off */
+    int32_t donate_min_p;  /* donate a branch only if its |P| >= this (Sec. III-C: 10) */
+    int32_t blocks;        /* persistent blocks per width class; 0 = all that fit on the GPU */
+    int32_t tune;          /* 0 = built-in launch table; 1 = use the table set by mce_set_tuning */
+    int32_t reserved;
+    int64_t timeout_ms;    /* give-up bound for every device-side wait (default 60000) */
+    /* optional DEVICE buffers, indexed by input vertex id, length n: the
+     * clique count, hash sum and Bron-Kerbosch call count (tree nodes, root
+     * call included) of each vertex's first-level subtree. */
+    uint64_t *root_count;
+    uint64_t *root_hash;
+    uint64_t *root_nodes;
+    /* DEVICE float[n] by input vertex id; read when order == MCE_ORDER_PRIORITY */
+    const float *root_priority;
+} mce_opts;
+
+typedef struct {
+    uint64_t count;       /* number of maximal cliques */
+    uint64_t hash;        /* sum of h(C) mod 2^64 */
+    int32_t max_size;     /* size of the largest maximal clique (0 for an empty graph) */
+    int32_t degeneracy;   /* d: largest core number */
+    uint64_t tree_nodes;  /* Bron-Kerbosch calls made (all subtrees) */
+    uint64_t donations;   /* subtrees handed to idle workers */
+    double ms_prep;       /* device time: validation + peel + orientation */
+    double ms_traverse;   /* device time: all traversal launches */
+} mce_result;
+
+/* Fill *opts with defaults (IP/IPX auto, plain order, worker list on,
+ * donate_min_p 10, timeout 60 s). */
+void mce_default_opts(mce_opts *opts);
+
+/*
+ * Build a handle for one graph: copy the CSR to the device, validate it,
+ * compute the degeneracy order and core numbers by level-synchronous peeling
+ * (Sec. II-C; ties inside a peel round by ascending id), and orient each
+ * vertex's neighbours into later (its root P, Algorithm 3) and earlier (its
+ * root X) lists.
+ *   row_ptr, col  CSR as described above (host, or device with MCE_FLAG_DEVICE_PTRS)
+ *   n             number of vertices (>= 0); m = number of undirected edges
+ *                 (row_ptr[n] must equal 2m)
+ *   alloc         optional device allocator (NULL = cudaMallocAsync)
+ *   stream        cudaStream_t for all of the handle's work (NULL = own stream)
+ *   out           receives the handle; NULL on failure
+ * Errors: MCE_EINVAL (bad CSR), MCE_ENOMEM, MCE_ECUDA, MCE_EUNSUPPORTED.
+ */
+int mce_create(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t m, uint32_t flags,
+               const mce_allocator *alloc, void *stream, mce_graph **out);
+
+/*
+ * Batched handle: G graphs with disjoint vertex ranges, graph g owning ids
+ * [graph_ptr[g], graph_ptr[g+1]) of one concatenated CSR (no edge may cross
+ * two ranges). All graphs are peeled and traversed together in the same
+ * persistent launches; results are kept per graph.
+ */
+int mce_batch_create(const int32_t *graph_ptr, int32_t G, const int32_t *row_ptr, const int32_t *col,
+                     int32_t n_total, int64_t m_total, uint32_t flags, const mce_allocator *alloc,
+                     void *stream, mce_graph **out);
+
+/*
+ * Enumerate the maximal cliques of a single-graph handle.
+ *   opts      NULL = defaults
+ *   out       receives count, hash, sizes and statistics
+ *   hist      optional HOST uint64[hist_len]: hist[k] = number of maximal
+ *             cliques with k vertices (hist[0] = 0)
+ * Errors: MCE_ERANGE if hist_len <= out->max_size (out is still filled;
+ * retry with a longer hist), MCE_ETIMEOUT, MCE_ECUDA, MCE_ENOMEM, MCE_EINVAL.
+ */
+int mce_run(mce_graph *g, const mce_opts *opts, mce_result *out, uint64_t *hist, int32_t hist_len);
+
+/*
+ * Batched run: per_graph[G] results and hist[G * hist_len] (row g is graph
+ * g's histogram), both HOST buffers; hist may be NULL. `total`, when not
+ * NULL, receives the sums over all graphs.
+ */
+int mce_run_batch(mce_graph *g, const mce_opts *opts, mce_result *per_graph, uint64_t *hist,
+                  int32_t hist_len, mce_result *total);
+
+/* Handle facts (host values): n, m, G, degeneracy, max degree. Any may be NULL. */
+int mce_graph_info(const mce_graph *g, int32_t *n, int64_t *m, int32_t *G, int32_t *degeneracy,
+                   int32_t *max_degree);
+
+/*
+ * Device arrays of the handle's pre-processing, copied to HOST buffers of
+ * length n (any may be NULL): core[v] = core number, rank[v] = position in
+ * the degeneracy order, out_degree[v] = |P| of v's root (later neighbours).
+ */
+int mce_get_order(const mce_graph *g, int32_t *core, int32_t *rank, int32_t *out_degree);
+
+/* Release the handle and all its device memory. NULL is a no-op. */
+void mce_destroy(mce_graph *g);
+
+/* Message for the last failing call on this thread (never NULL). */
+const char *mce_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* MCE_H */

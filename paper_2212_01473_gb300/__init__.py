@@ -1,0 +1,14 @@
+"""GB300-native exact maximal clique enumeration (arXiv 2212.01473's method).
+
+The compute path is the CUDA library libmce.so (C ABI in include/mce.h);
+this package is its Python binding. Importing the package does not load the
+library; the first call does, and raises if it has not been built.
+"""
+from .engine import (MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ERANGE, MCE_ETIMEOUT, MCE_EUNSUPPORTED,
+                     MCE_FLAG_DEVICE_PTRS, MCE_OK, MCE_ORDER_PLAIN, MCE_ORDER_PRIORITY, MCE_PIVOT_AUTO,
+                     MCE_PIVOT_IP, MCE_PIVOT_IPX, MCEError, Result, enumerate_maximal_cliques, library,
+                     mce_batch_create, mce_create, mce_default_opts, mce_destroy, mce_get_order,
+                     mce_graph_info, mce_run, mce_run_batch)
+
+__all__ = [name for name in dir() if name.startswith(("mce_", "MCE"))] + [
+    "Result", "enumerate_maximal_cliques", "library"]

@@ -1,0 +1,183 @@
+// Internal declarations of the GB300 maximal clique enumeration engine.
+// Not part of the C ABI (include/mce.h); shared by the engine's .cu files only.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/mce.h"
+
+namespace mce {
+
+// Device status word values (a kernel never traps: it records and returns).
+enum : int {
+    ST_OK = 0,
+    ST_TIMEOUT = 1,   // a bounded wait gave up
+    ST_OVERFLOW = 2,  // an internal capacity was exceeded (engine bug guard)
+    ST_BADGRAPH = 4,  // validation failed
+};
+
+// Golden-ratio increment of the clique hash (h(C) in mce.h).
+constexpr uint64_t kPhi = 0x9E3779B97F4A7C15ull;
+
+// SplitMix64 output finaliser, restated here for the device (see mce.h).
+__host__ __device__ __forceinline__ uint64_t mix64(uint64_t z) {
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+__device__ __forceinline__ uint64_t globaltimer_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int *p) {
+    int v;
+    asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ unsigned ld_acquire_u(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release(int *p, int v) {
+    asm volatile("st.release.gpu.global.s32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ void st_release_u(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int ld_relaxed(const int *p) {
+    int v;
+    asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// Grid-wide barrier for a cooperatively launched (all blocks co-resident)
+// kernel. Every wait is bounded by `deadline` (globaltimer ns); on expiry the
+// status word gets ST_TIMEOUT and the barrier returns false in every block
+// that sees it, so the kernel can return instead of hanging.
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
+
+__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t deadline) {
+    __syncthreads();
+    __shared__ int s_ok;
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        unsigned g = ld_acquire_u(&bar->gen);
+        __threadfence();
+        unsigned arrived = atomicAdd(&bar->count, 1u);
+        if (arrived == gridDim.x - 1) {
+            atomicExch(&bar->count, 0u);
+            __threadfence();
+            st_release_u(&bar->gen, g + 1);
+        } else {
+            unsigned ns = 32;
+            while (ld_acquire_u(&bar->gen) == g) {
+                if (ld_relaxed(status) & ST_TIMEOUT) { ok = 0; break; }
+                if (globaltimer_ns() > deadline) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(ns);
+                if (ns < 256) ns <<= 1;
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ----------------------------------------------------------------- handles
+
+// Everything the traversal needs about the oriented graph (device pointers).
+struct DevGraph {
+    int32_t n;
+    int32_t G;             // number of graphs (1 unless batched)
+    const int32_t *out_ptr;   // [n+1] later neighbours of rank r: out_col[out_ptr[r]..)
+    const int32_t *out_col;   // ranks, ascending within a row
+    const int32_t *in_ptr;    // [n+1] earlier neighbours
+    const int32_t *in_col;    // ranks (any order)
+    const int32_t *order;     // rank -> input id
+    const uint64_t *mixid;    // rank -> mix64(input id + 1)
+    const int32_t *gid;       // rank -> graph index (NULL when G == 1)
+};
+
+// Per-launch traversal outputs (device pointers).
+struct DevOut {
+    unsigned long long *count;   // [G]
+    unsigned long long *hash;    // [G]
+    unsigned long long *hist;    // [G * hist_len]
+    int32_t hist_len;
+    unsigned long long *nodes;   // [1] total tree nodes
+    unsigned long long *donations;  // [1]
+    int *max_size;               // [1] (atomicMax)
+    unsigned long long *root_count; // optional [n] by input id
+    unsigned long long *root_hash;
+    unsigned long long *root_nodes;
+    int *status;
+};
+
+// Host-side launch of one width class of the traversal (mce_traverse*.cu).
+struct ClassLaunch {
+    int wp;            // padded 32-bit words per bitset row
+    int gw;            // warps per cooperating group
+    int blocks;        // persistent blocks
+    int warps_per_block;
+    size_t smem;       // dynamic shared memory per block
+    bool a_global;     // A rows live in the global arena (too wide for smem)
+};
+
+struct ClassArgs {
+    const int32_t *roots;   // roots of this class, in processing order
+    int32_t n_roots;
+    int32_t rows_cap;       // max |P0| in this class (rows of A)
+    int32_t x_cap;          // max |X0| over this class's roots
+    int32_t pivot_ipx;      // 1: pivot candidates include X_X
+    int32_t worker_list;
+    int32_t donate_min_p;
+    int32_t root_chunk;     // roots claimed per atomic
+    uint64_t timeout_ns;
+    // scratch (device), sized by the host for groups = blocks * warps_per_block / gw
+    uint32_t *arena;        // per-group: stack, X rows, X index lists, (A if a_global)
+    size_t arena_words_per_group;
+    int *ctl;               // [8]: root counter, active, idle_count, ...
+    unsigned *idle_bits;    // [ceil(groups/32)]
+    int *mail_flag;         // [groups]
+    uint32_t *mail;         // [groups * mail_words]
+    int32_t mail_words;
+};
+
+enum CtlSlot { CTL_NEXT_ROOT = 0, CTL_ACTIVE = 1, CTL_IDLE = 2, CTL_NCTL = 8 };
+
+// Number of warps per block and per group, and shared memory, for a width class.
+ClassLaunch plan_class(int wp, int rows_cap, int sm_count, int max_smem_optin, int requested_blocks);
+size_t class_arena_words(const ClassLaunch &L, int rows_cap, int x_cap);
+cudaError_t launch_class(const ClassLaunch &L, const DevGraph &g, const DevOut &o, const ClassArgs &a,
+                         cudaStream_t s);
+cudaError_t launch_trivial(const DevGraph &g, const DevOut &o, const int32_t *roots, int32_t n_roots,
+                           cudaStream_t s);
+
+// Width classes: padded words per row. A row stride w with w/4 odd keeps
+// 128-bit shared loads of 8 consecutive lanes (one phase) on distinct banks.
+constexpr int kNumClasses = 9;
+__host__ __device__ constexpr int class_wp(int c) {
+    return c == 0 ? 1 : c == 1 ? 2 : c == 2 ? 4 : c == 3 ? 12 : c == 4 ? 20 : c == 5 ? 28
+         : c == 6 ? 36 : c == 7 ? 68 : 132;
+}
+// class of a root with |P0| = n0 >= 1
+__host__ __device__ inline int class_of(int n0) {
+    int w = (n0 + 31) >> 5;
+    for (int c = 0; c < kNumClasses; c++)
+        if (w <= class_wp(c)) return c;
+    return -1;
+}
+
+}  // namespace mce

@@ -1,0 +1,600 @@
+// Pre-processing on the GPU: CSR validation, degeneracy ordering by
+// level-synchronous peeling (Sec. II-C "Degeneracy Ordering"; the paper
+// times this step with the enumeration, Sec. IV-A), and orientation of each
+// vertex's neighbours into later (root P, Algorithm 3) and earlier (root X)
+// lists in rank space.
+#include <climits>
+
+#include "mce_prep.cuh"
+
+namespace mce {
+
+// ------------------------------------------------------------ validation
+
+__global__ void k_check_rowptr(int n, const int32_t *rp, int64_t m2, int *status) {
+    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i > n) return;
+    bool bad = false;
+    if (i == 0 && rp[0] != 0) bad = true;
+    if (i < n && rp[i] > rp[i + 1]) bad = true;
+    if (i == n && (int64_t)rp[n] != m2) bad = true;
+    if (bad) atomicOr(status, ST_BADGRAPH);
+}
+
+// one warp per row: ids in range, no self-loop, strictly ascending, symmetric
+__global__ void k_check_cols(int n, const int32_t *rp, const int32_t *col, int *status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t v = w0; v < n; v += nw) {
+        const int b = rp[v], e = rp[v + 1];
+        bool bad = false;
+        for (int j = b + lane; j < e; j += 32) {
+            const int32_t u = col[j];
+            if (u < 0 || u >= n || u == (int32_t)v) { bad = true; continue; }
+            if (j + 1 < e && col[j + 1] <= u) bad = true;
+            // symmetric: v in row u
+            int lo = rp[u], hi = rp[u + 1];
+            while (lo < hi) {
+                int mid = (lo + hi) >> 1;
+                if (col[mid] < (int32_t)v) lo = mid + 1; else hi = mid;
+            }
+            if (lo >= rp[u + 1] || col[lo] != (int32_t)v) bad = true;
+        }
+        if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(status, ST_BADGRAPH);
+    }
+}
+
+// -------------------------------------------------------------- helpers
+
+__device__ __forceinline__ int warp_push(int *counter, bool pred) {
+    // warp-aggregated slot reservation; returns the slot for pred lanes
+    const unsigned act = __activemask();
+    const unsigned b = __ballot_sync(act, pred);
+    const int lane = threadIdx.x & 31;
+    int base = 0;
+    const int leader = __ffs(act) - 1;
+    if (lane == leader && b) base = atomicAdd(counter, __popc(b));
+    base = __shfl_sync(act, base, leader);
+    return base + __popc(b & ((1u << lane) - 1u));
+}
+
+template <int NT>
+__device__ __forceinline__ int block_reduce_min(int x, int *sh) {
+    for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = x;
+    __syncthreads();
+    if (w == 0) {
+        x = lane < NT / 32 ? sh[lane] : INT_MAX;
+        for (int o = 16; o; o >>= 1) x = min(x, __shfl_xor_sync(0xffffffffu, x, o));
+        if (lane == 0) sh[0] = x;
+    }
+    __syncthreads();
+    int r = sh[0];
+    __syncthreads();
+    return r;
+}
+
+template <int NT>
+__device__ __forceinline__ int block_reduce_sum(int x, int *sh) {
+    x = __reduce_add_sync(0xffffffffu, x);
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    __syncthreads();
+    if (lane == 0) sh[w] = x;
+    __syncthreads();
+    int t = 0;
+    for (int i = 0; i < NT / 32; i++) t += sh[i];
+    __syncthreads();
+    return t;
+}
+
+// exclusive block scan; returns prefix, *total = block sum
+template <int NT>
+__device__ __forceinline__ int block_scan_excl(int x, int *sh, int *total) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    int inc = x;
+    for (int o = 1; o < 32; o <<= 1) {
+        int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += y;
+    }
+    __syncthreads();
+    if (lane == 31) sh[w] = inc;
+    __syncthreads();
+    int off = 0, tot = 0;
+    for (int i = 0; i < NT / 32; i++) {
+        int c = sh[i];
+        if (i < w) off += c;
+        tot += c;
+    }
+    __syncthreads();
+    *total = tot;
+    return off + inc - x;
+}
+
+// ---------------------------------------------------------------- peel
+
+constexpr int kPeelThreads = 512;
+constexpr int kSmallSort = 4096;
+
+__device__ __forceinline__ int vload(const int *p) { return *(volatile const int *)p; }
+
+// bitonic sort of a[0..len) ascending in shared memory by the whole block
+__device__ void block_bitonic(int *a, int len) {
+    int m = 1;
+    while (m < len) m <<= 1;
+    for (int i = len + threadIdx.x; i < m; i += blockDim.x) a[i] = INT_MAX;
+    __syncthreads();
+    for (int k = 2; k <= m; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < m; i += blockDim.x) {
+                int p = i ^ j;
+                if (p > i) {
+                    int x = a[i], y = a[p];
+                    bool up = (i & k) == 0;
+                    if ((x > y) == up) { a[i] = y; a[p] = x; }
+                }
+            }
+            __syncthreads();
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp, const int32_t *col,
+                                                       int32_t *deg, int32_t *rank, int32_t *core,
+                                                       int32_t *order, int32_t *remA, int32_t *remB,
+                                                       int32_t *SA, int32_t *SB, unsigned *bitmap,
+                                                       int *blocksums, PeelCtl *ctl, int *status,
+                                                       uint64_t timeout_ns) {
+    __shared__ int sh[64];
+    __shared__ int ssort[kSmallSort];
+    const uint64_t deadline = globaltimer_ns() + timeout_ns;
+    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t gwarp = tid >> 5, nwarps = nth >> 5;
+    GridBar *bar = &ctl->bar;
+
+    for (int64_t v = tid; v < n; v += nth) {
+        deg[v] = rp[v + 1] - rp[v];
+        rank[v] = -1;
+        remA[v] = (int32_t)v;
+    }
+    if (!grid_barrier(bar, status, deadline)) return;
+
+    for (;;) {
+        if (vload(&ctl->next) >= n) break;
+        int32_t *rem = vload(&ctl->remsel) ? remB : remA;
+        int32_t *rem2 = vload(&ctl->remsel) ? remA : remB;
+        const int nrem = vload(&ctl->nrem);
+        // level start: k = max(k, min remaining degree)
+        int lmin = INT_MAX;
+        for (int64_t i = tid; i < nrem; i += nth) {
+            int v = rem[i];
+            if (rank[v] < 0) lmin = min(lmin, deg[v]);
+        }
+        lmin = block_reduce_min<kPeelThreads>(lmin, sh);
+        if (threadIdx.x == 0 && lmin != INT_MAX) atomicMin(&ctl->minval, lmin);
+        if (!grid_barrier(bar, status, deadline)) return;
+        const int k = max(vload(&ctl->k), vload(&ctl->minval));
+        {
+            int32_t *S = vload(&ctl->sel) ? SB : SA;
+            const int64_t lim = (nrem + 31) / 32 * 32;
+            for (int64_t i = tid; i < lim; i += nth) {
+                bool live = false, inS = false;
+                int v = 0;
+                if (i < nrem) {
+                    v = rem[i];
+                    live = rank[v] < 0;
+                    inS = live && deg[v] <= k;
+                }
+                int ps = warp_push(&ctl->ns, inS);
+                if (inS) S[ps] = v;
+                int pk = warp_push(&ctl->nrem2, live && !inS);
+                if (live && !inS) rem2[pk] = v;
+            }
+        }
+        if (!grid_barrier(bar, status, deadline)) return;
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            ctl->k = k;
+            ctl->minval = INT_MAX;
+            ctl->remsel ^= 1;
+            ctl->nrem = ctl->nrem2;
+            ctl->nrem2 = 0;
+        }
+        if (!grid_barrier(bar, status, deadline)) return;
+
+        // sub-rounds at level k: S_t = remaining vertices with degree <= k
+        for (;;) {
+            const int ns = vload(&ctl->ns);
+            if (ns == 0) break;
+            int32_t *S = vload(&ctl->sel) ? SB : SA;
+            int32_t *S2 = vload(&ctl->sel) ? SA : SB;
+            // ranks inside a sub-round follow ascending vertex id
+            if (ns <= kSmallSort) {
+                if (blockIdx.x == 0) {
+                    for (int i = threadIdx.x; i < ns; i += blockDim.x) ssort[i] = S[i];
+                    __syncthreads();
+                    block_bitonic(ssort, ns);
+                    for (int i = threadIdx.x; i < ns; i += blockDim.x) S[i] = ssort[i];
+                }
+            } else {
+                for (int64_t i = tid; i < ns; i += nth) {
+                    int v = S[i];
+                    atomicOr(&bitmap[v >> 5], 1u << (v & 31));
+                }
+                if (!grid_barrier(bar, status, deadline)) return;
+                const int nw = (n + 31) >> 5;
+                const int chunk = (nw + gridDim.x - 1) / gridDim.x;
+                const int w_lo = min(nw, (int)blockIdx.x * chunk), w_hi = min(nw, w_lo + chunk);
+                int c = 0;
+                for (int w = w_lo + threadIdx.x; w < w_hi; w += blockDim.x) c += __popc(bitmap[w]);
+                c = block_reduce_sum<kPeelThreads>(c, sh);
+                if (threadIdx.x == 0) blocksums[blockIdx.x] = c;
+                if (!grid_barrier(bar, status, deadline)) return;
+                int off = 0;
+                for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) off += blocksums[b];
+                off = block_reduce_sum<kPeelThreads>(off, sh);
+                for (int t0 = w_lo; t0 < w_hi; t0 += blockDim.x) {
+                    int w = t0 + threadIdx.x;
+                    unsigned bits = (w < w_hi) ? bitmap[w] : 0u;
+                    int tot;
+                    int pre = block_scan_excl<kPeelThreads>(__popc(bits), sh, &tot);
+                    int pos = off + pre;
+                    while (bits) {
+                        int b = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        S[pos++] = w * 32 + b;
+                    }
+                    if (w < w_hi) bitmap[w] = 0u;
+                    off += tot;
+                }
+            }
+            if (!grid_barrier(bar, status, deadline)) return;
+            const int base = vload(&ctl->next);
+            for (int64_t i = tid; i < ns; i += nth) {
+                int v = S[i];
+                rank[v] = base + (int)i;
+                core[v] = k;
+                order[base + i] = v;
+            }
+            if (!grid_barrier(bar, status, deadline)) return;
+            for (int64_t i = gwarp; i < ns; i += nwarps) {
+                const int v = S[i];
+                const int b = rp[v], e = rp[v + 1];
+                for (int j0 = b; j0 < e; j0 += 32) {
+                    int j = j0 + lane;
+                    bool push = false;
+                    int u = 0;
+                    if (j < e) {
+                        u = col[j];
+                        if (rank[u] < 0) {
+                            int old = atomicSub(&deg[u], 1);
+                            push = (old == k + 1);
+                        }
+                    }
+                    int p = warp_push(&ctl->ns2, push);
+                    if (push) S2[p] = u;
+                }
+            }
+            if (!grid_barrier(bar, status, deadline)) return;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                ctl->next += ns;
+                ctl->ns = ctl->ns2;
+                ctl->ns2 = 0;
+                ctl->sel ^= 1;
+                ctl->rounds++;
+            }
+            if (!grid_barrier(bar, status, deadline)) return;
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scan
+
+constexpr int kScanThreads = 256, kScanItems = 8, kScanTile = kScanThreads * kScanItems;
+
+__global__ void k_scan_tiles(const int32_t *in, int32_t *out, int32_t *tile_sums, int64_t n) {
+    __shared__ int sh[32];
+    const int64_t t0 = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    int v[kScanItems];
+    int s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        v[i] = (t0 + i < n) ? in[t0 + i] : 0;
+        s += v[i];
+    }
+    int tot;
+    int pre = block_scan_excl<kScanThreads>(s, sh, &tot);
+#pragma unroll
+    for (int i = 0; i < kScanItems; i++) {
+        if (t0 + i < n) out[t0 + i] = pre;
+        pre += v[i];
+    }
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = tot;
+}
+
+__global__ void k_scan_add(int32_t *out, const int32_t *tile_off, int64_t n) {
+    const int64_t i = (int64_t)blockIdx.x * kScanTile + threadIdx.x;
+    const int add = tile_off[blockIdx.x];
+    for (int k = 0; k < kScanItems; k++) {
+        int64_t j = i + (int64_t)k * kScanThreads;
+        if (j < n) out[j] += add;
+    }
+}
+
+__global__ void k_set_total(int32_t *out, int64_t n, const int32_t *in) {
+    // out[n] = out[n-1] + in[n-1]
+    if (n > 0) out[n] = out[n - 1] + in[n - 1];
+    else out[0] = 0;
+}
+
+// exclusive scan of in[0..n) into out[0..n], out[n] = total; tmp >= scan_tmp_words(n)
+cudaError_t exclusive_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s) {
+    if (n <= 0) {
+        k_set_total<<<1, 1, 0, s>>>(out, 0, in);
+        return cudaGetLastError();
+    }
+    const int64_t tiles = (n + kScanTile - 1) / kScanTile;
+    int32_t *sums = tmp;
+    int32_t *offs = tmp + tiles;
+    k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, sums, n);
+    if (tiles > 1) {
+        cudaError_t e = exclusive_scan(sums, offs, tiles, tmp + 2 * tiles + 1, s);
+        if (e != cudaSuccess) return e;
+        k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, offs, n);
+    }
+    k_set_total<<<1, 1, 0, s>>>(out, n, in);
+    return cudaGetLastError();
+}
+
+int64_t scan_tmp_words(int64_t n) {
+    int64_t w = 0;
+    while (n > 1) {
+        int64_t tiles = (n + kScanTile - 1) / kScanTile;
+        w += 2 * tiles + 1;
+        n = tiles;
+    }
+    return w + 4;
+}
+
+// ----------------------------------------------------------- orientation
+
+__global__ void k_count_split(int n, const int32_t *rp, const int32_t *col, const int32_t *order,
+                              const int32_t *rank, int32_t *outdeg, int32_t *indeg) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nw) {
+        const int v = order[r];
+        const int b = rp[v], e = rp[v + 1];
+        int c = 0;
+        for (int j = b + lane; j < e; j += 32) c += rank[col[j]] > (int32_t)r;
+        c = __reduce_add_sync(0xffffffffu, c);
+        if (lane == 0) {
+            outdeg[r] = c;
+            indeg[r] = (e - b) - c;
+        }
+    }
+}
+
+__global__ void k_fill_split(int n, const int32_t *rp, const int32_t *col, const int32_t *order,
+                             const int32_t *rank, const int32_t *out_ptr, int32_t *out_col,
+                             const int32_t *in_ptr, int32_t *in_col) {
+    const int lane = threadIdx.x & 31;
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nw) {
+        const int v = order[r];
+        const int b = rp[v], e = rp[v + 1];
+        int oc = out_ptr[r], ic = in_ptr[r];
+        for (int j0 = b; j0 < e; j0 += 32) {
+            int j = j0 + lane;
+            int ru = 0;
+            bool valid = j < e, later = false;
+            if (valid) {
+                ru = rank[col[j]];
+                later = ru > (int32_t)r;
+            }
+            unsigned bl = __ballot_sync(0xffffffffu, valid && later);
+            unsigned be = __ballot_sync(0xffffffffu, valid && !later);
+            unsigned lt = (1u << lane) - 1u;
+            if (valid && later) out_col[oc + __popc(bl & lt)] = ru;
+            if (valid && !later) in_col[ic + __popc(be & lt)] = ru;
+            oc += __popc(bl);
+            ic += __popc(be);
+        }
+    }
+}
+
+constexpr int kRowSortWarpCap = 1024;
+constexpr int kRowSortBlockCap = 4096;
+
+// rows of length <= kRowSortWarpCap: one warp per row, bitonic in shared memory
+__global__ void __launch_bounds__(256) k_sort_rows_warp(int n, const int32_t *ptr, int32_t *colv) {
+    __shared__ int buf[8][kRowSortWarpCap];
+    const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
+    int *a = buf[wib];
+    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t r = w0; r < n; r += nw) {
+        const int b = ptr[r], len = ptr[r + 1] - b;
+        if (len <= 1 || len > kRowSortWarpCap) continue;
+        int m = 1;
+        while (m < len) m <<= 1;
+        for (int i = lane; i < m; i += 32) a[i] = i < len ? colv[b + i] : INT_MAX;
+        __syncwarp();
+        for (int k = 2; k <= m; k <<= 1)
+            for (int j = k >> 1; j > 0; j >>= 1) {
+                for (int i = lane; i < m; i += 32) {
+                    int p = i ^ j;
+                    if (p > i) {
+                        int x = a[i], y = a[p];
+                        bool up = (i & k) == 0;
+                        if ((x > y) == up) { a[i] = y; a[p] = x; }
+                    }
+                }
+                __syncwarp();
+            }
+        for (int i = lane; i < len; i += 32) colv[b + i] = a[i];
+        __syncwarp();
+    }
+}
+
+// rows longer than kRowSortWarpCap (at most the degeneracy): one block per row
+__global__ void __launch_bounds__(1024) k_sort_rows_block(int n, const int32_t *ptr, int32_t *colv) {
+    __shared__ int a[kRowSortBlockCap];
+    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+        const int b = ptr[r], len = ptr[r + 1] - b;
+        if (len <= kRowSortWarpCap || len > kRowSortBlockCap) continue;
+        for (int i = threadIdx.x; i < len; i += blockDim.x) a[i] = colv[b + i];
+        __syncthreads();
+        block_bitonic(a, len);
+        for (int i = threadIdx.x; i < len; i += blockDim.x) colv[b + i] = a[i];
+        __syncthreads();
+    }
+}
+
+__global__ void k_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t *gid,
+                          const int32_t *graph_ptr, int G) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int v = order[r];
+        mixid[r] = mix64((uint64_t)(int64_t)v + 1ull);
+        if (gid) {
+            int lo = 0, hi = G;  // largest g with graph_ptr[g] <= v
+            while (hi - lo > 1) {
+                int mid = (lo + hi) >> 1;
+                if (graph_ptr[mid] <= v) lo = mid; else hi = mid;
+            }
+            gid[r] = lo;
+        }
+    }
+}
+
+// class statistics and per-class flags
+__global__ void k_class_stats(int n, const int32_t *outdeg, const int32_t *indeg, int *cls_rows,
+                              int *cls_x, int *cls_count) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int n0 = outdeg[r];
+        const int c = n0 == 0 ? kNumClasses : class_of(n0);
+        if (c < 0) continue;
+        atomicMax(&cls_rows[c], n0);
+        atomicMax(&cls_x[c], indeg[r]);
+        atomicAdd(&cls_count[c], 1);
+    }
+}
+
+__global__ void k_class_flags(int n, const int32_t *outdeg, int c, int32_t *flags) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+        const int n0 = outdeg[r];
+        const int cr = n0 == 0 ? kNumClasses : class_of(n0);
+        flags[r] = cr == c;
+    }
+}
+
+__global__ void k_scatter_flagged(int n, const int32_t *flags, const int32_t *pos, int32_t *out) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        if (flags[r]) out[pos[r]] = (int32_t)r;
+}
+
+// ------------------------------------------------------------ host side
+
+static unsigned grid_for(int64_t work, int per_block, int cap = 1 << 20) {
+    int64_t b = (work + per_block - 1) / per_block;
+    if (b < 1) b = 1;
+    if (b > cap) b = cap;
+    return (unsigned)b;
+}
+
+cudaError_t launch_validate(int n, const int32_t *rp, const int32_t *col, int64_t m2, int *status,
+                            cudaStream_t s, bool cols) {
+    if (!cols) {
+        k_check_rowptr<<<grid_for((int64_t)n + 1, 256), 256, 0, s>>>(n, rp, m2, status);
+    } else if (n > 0) {
+        k_check_cols<<<grid_for((int64_t)n * 32, 256, 65536), 256, 0, s>>>(n, rp, col, status);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &b, int sm_count,
+                        uint64_t timeout_ns, cudaStream_t s) {
+    int per_sm = 0;
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, kPeelThreads, 0);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int blocks = sm_count * (per_sm < 2 ? per_sm : 2);
+    if (blocks > b.max_blocks) blocks = b.max_blocks;
+    void *args[] = {(void *)&n,        (void *)&rp,       (void *)&col,       (void *)&b.deg,
+                    (void *)&b.rank,   (void *)&b.core,   (void *)&b.order,   (void *)&b.remA,
+                    (void *)&b.remB,   (void *)&b.SA,     (void *)&b.SB,      (void *)&b.bitmap,
+                    (void *)&b.blocksums, (void *)&b.ctl, (void *)&b.status, (void *)&timeout_ns};
+    return cudaLaunchCooperativeKernel((void *)k_peel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
+}
+
+__global__ void k_peel_init(PeelCtl *ctl, int n) {
+    ctl->k = 0;
+    ctl->next = 0;
+    ctl->ns = 0;
+    ctl->ns2 = 0;
+    ctl->nrem = n;
+    ctl->nrem2 = 0;
+    ctl->minval = INT_MAX;
+    ctl->rounds = 0;
+    ctl->sel = 0;
+    ctl->remsel = 0;
+    ctl->bar.count = 0;
+    ctl->bar.gen = 0;
+}
+
+cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s) {
+    k_peel_init<<<1, 1, 0, s>>>(ctl, n);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const int32_t *order,
+                          const int32_t *rank, int32_t *outdeg, int32_t *indeg, int32_t *out_ptr,
+                          int32_t *out_col, int32_t *in_ptr, int32_t *in_col, int32_t *scan_tmp,
+                          cudaStream_t s) {
+    if (n == 0) {
+        cudaError_t e = exclusive_scan(outdeg, out_ptr, 0, scan_tmp, s);
+        if (e != cudaSuccess) return e;
+        return exclusive_scan(indeg, in_ptr, 0, scan_tmp, s);
+    }
+    const unsigned gw = grid_for((int64_t)n * 32, 256, 65536);
+    k_count_split<<<gw, 256, 0, s>>>(n, rp, col, order, rank, outdeg, indeg);
+    cudaError_t e = exclusive_scan(outdeg, out_ptr, n, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    e = exclusive_scan(indeg, in_ptr, n, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_fill_split<<<gw, 256, 0, s>>>(n, rp, col, order, rank, out_ptr, out_col, in_ptr, in_col);
+    k_sort_rows_warp<<<gw, 256, 0, s>>>(n, out_ptr, out_col);
+    k_sort_rows_block<<<grid_for(n, 1, 4096), 1024, 0, s>>>(n, out_ptr, out_col);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t *gid,
+                           const int32_t *graph_ptr, int G, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_mix_gid<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, order, mixid, gid, graph_ptr, G);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_classify(int n, const int32_t *outdeg, const int32_t *indeg, int *cls_rows,
+                            int *cls_x, int *cls_count, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_class_stats<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, outdeg, indeg, cls_rows, cls_x, cls_count);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_class_list(int n, const int32_t *outdeg, int c, int32_t *flags, int32_t *pos,
+                              int32_t *scan_tmp, int32_t *out, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    k_class_flags<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, outdeg, c, flags);
+    cudaError_t e = exclusive_scan(flags, pos, n, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_scatter_flagged<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, flags, pos, out);
+    return cudaGetLastError();
+}
+
+}  // namespace mce

@@ -1,0 +1,39 @@
+// Pre-processing kernels (validation, peel, orientation): host launchers.
+#pragma once
+#include "mce_internal.cuh"
+
+namespace mce {
+
+struct PeelCtl {
+    int k, next, ns, ns2, nrem, nrem2, minval, rounds, sel, remsel, pad[6];
+    GridBar bar;
+};
+
+struct PeelBufs {
+    int32_t *deg, *rank, *core, *order, *remA, *remB, *SA, *SB;
+    unsigned *bitmap;  // ceil(n/32) words, zero on entry and on exit
+    int *blocksums;    // max_blocks
+    PeelCtl *ctl;
+    int *status;
+    int max_blocks;
+};
+
+cudaError_t launch_validate(int n, const int32_t *rp, const int32_t *col, int64_t m2, int *status,
+                            cudaStream_t s, bool cols);
+cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s);
+cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &b, int sm_count,
+                        uint64_t timeout_ns, cudaStream_t s);
+cudaError_t exclusive_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s);
+int64_t scan_tmp_words(int64_t n);
+cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const int32_t *order,
+                          const int32_t *rank, int32_t *outdeg, int32_t *indeg, int32_t *out_ptr,
+                          int32_t *out_col, int32_t *in_ptr, int32_t *in_col, int32_t *scan_tmp,
+                          cudaStream_t s);
+cudaError_t launch_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t *gid,
+                           const int32_t *graph_ptr, int G, cudaStream_t s);
+cudaError_t launch_classify(int n, const int32_t *outdeg, const int32_t *indeg, int *cls_rows,
+                            int *cls_x, int *cls_count, cudaStream_t s);
+cudaError_t launch_class_list(int n, const int32_t *outdeg, int c, int32_t *flags, int32_t *pos,
+                              int32_t *scan_tmp, int32_t *out, cudaStream_t s);
+
+}  // namespace mce

@@ -1,0 +1,52 @@
+// Instantiation helper: plan and launch the traversal for one row width.
+#pragma once
+#include "mce_traverse.cuh"
+
+namespace mce {
+
+__host__ __device__ constexpr int group_warps(int wp) { return wp <= 12 ? 1 : wp <= 20 ? 4 : 8; }
+__host__ __device__ constexpr bool a_in_global(int wp) { return wp >= 68; }
+__host__ __device__ constexpr bool stack_in_smem(int wp) { return wp <= 4; }
+
+template <int WP>
+cudaError_t plan_wp(int rows, int sm_count, int max_smem_optin, int requested_blocks, ClassLaunch *L) {
+    constexpr int GW = group_warps(WP);
+    constexpr bool AG = a_in_global(WP);
+    const GrpSmem lay = grp_smem_layout(WP, GW, rows, AG, stack_in_smem(WP));
+    int gpb = 8 / GW;
+    while (gpb > 1 && (size_t)gpb * lay.total > (size_t)max_smem_optin) gpb--;
+    if ((size_t)gpb * lay.total > (size_t)max_smem_optin) return cudaErrorInvalidConfiguration;
+    L->wp = WP;
+    L->gw = GW;
+    L->warps_per_block = gpb * GW;
+    L->smem = (size_t)gpb * lay.total;
+    L->a_global = AG;
+    auto kern = k_traverse<WP, GW, AG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L->warps_per_block * 32, L->smem);
+    if (e != cudaSuccess) return e;
+    if (per_sm < 1) return cudaErrorInvalidConfiguration;
+    int blocks = per_sm * sm_count;
+    if (requested_blocks > 0 && requested_blocks < blocks) blocks = requested_blocks;
+    L->blocks = blocks;
+    return cudaSuccess;
+}
+
+template <int WP>
+cudaError_t launch_wp(const ClassLaunch &L, const DevGraph &g, const DevOut &o, const ClassArgs &a,
+                      int rows, cudaStream_t s) {
+    constexpr int GW = group_warps(WP);
+    constexpr bool AG = a_in_global(WP);
+    k_traverse<WP, GW, AG><<<L.blocks, L.warps_per_block * 32, L.smem, s>>>(g, o, a, rows,
+                                                                           stack_in_smem(WP) ? 1 : 0);
+    return cudaGetLastError();
+}
+
+#define MCE_INSTANTIATE_WP(WP)                                                                        \
+    template cudaError_t plan_wp<WP>(int, int, int, int, ClassLaunch *);                              \
+    template cudaError_t launch_wp<WP>(const ClassLaunch &, const DevGraph &, const DevOut &,         \
+                                       const ClassArgs &, int, cudaStream_t);
+
+}  // namespace mce

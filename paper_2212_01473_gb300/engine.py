@@ -1,0 +1,299 @@
+"""ctypes binding of the engine's C ABI (include/mce.h), same names as the C calls.
+
+Argument marshalling only: every step of the enumeration runs in the CUDA
+library libmce.so. PyTorch supplies device memory (through the caching
+allocator, passed to the library as its allocator) and the CUDA stream.
+There is no CPU fallback: if the library is missing, the calls raise.
+"""
+import ctypes
+import os
+from dataclasses import dataclass, field
+from typing import List, Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libmce.so")
+
+MCE_OK, MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETIMEOUT, MCE_ERANGE, MCE_EUNSUPPORTED = range(7)
+MCE_FLAG_DEVICE_PTRS = 1
+MCE_PIVOT_AUTO, MCE_PIVOT_IP, MCE_PIVOT_IPX = 0, 1, 2
+MCE_ORDER_PLAIN, MCE_ORDER_PRIORITY = 0, 1
+MCE_MAX_DEGENERACY = 4096
+
+_NAMES = {MCE_EINVAL: "MCE_EINVAL", MCE_ENOMEM: "MCE_ENOMEM", MCE_ECUDA: "MCE_ECUDA",
+          MCE_ETIMEOUT: "MCE_ETIMEOUT", MCE_ERANGE: "MCE_ERANGE", MCE_EUNSUPPORTED: "MCE_EUNSUPPORTED"}
+
+
+class MCEError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__("%s: %s" % (_NAMES.get(code, str(code)), msg))
+        self.code = code
+
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class mce_allocator(ctypes.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("ctx", ctypes.c_void_p)]
+
+
+class mce_opts(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("pivot", ctypes.c_int32), ("order", ctypes.c_int32),
+                ("worker_list", ctypes.c_int32), ("donate_min_p", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("tune", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("timeout_ms", ctypes.c_int64), ("root_count", ctypes.c_void_p),
+                ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
+                ("root_priority", ctypes.c_void_p)]
+
+
+class mce_result(ctypes.Structure):
+    _fields_ = [("count", ctypes.c_uint64), ("hash", ctypes.c_uint64), ("max_size", ctypes.c_int32),
+                ("degeneracy", ctypes.c_int32), ("tree_nodes", ctypes.c_uint64),
+                ("donations", ctypes.c_uint64), ("ms_prep", ctypes.c_double),
+                ("ms_traverse", ctypes.c_double)]
+
+
+_lib = None
+
+
+def library():
+    """Load libmce.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libmce.so is not built (run paper_2212_01473_gb300/build.py); "
+                              "the engine has no CPU fallback")
+        lib = ctypes.CDLL(LIB_PATH)
+        vp, i32, i64, u32 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_uint32
+        i32p, u64p = ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_uint64)
+        lib.mce_default_opts.argtypes = [ctypes.POINTER(mce_opts)]
+        lib.mce_default_opts.restype = None
+        lib.mce_create.argtypes = [vp, vp, i32, i64, u32, ctypes.POINTER(mce_allocator), vp,
+                                   ctypes.POINTER(vp)]
+        lib.mce_batch_create.argtypes = [vp, i32, vp, vp, i32, i64, u32,
+                                         ctypes.POINTER(mce_allocator), vp, ctypes.POINTER(vp)]
+        lib.mce_run.argtypes = [vp, ctypes.POINTER(mce_opts), ctypes.POINTER(mce_result), u64p, i32]
+        lib.mce_run_batch.argtypes = [vp, ctypes.POINTER(mce_opts), ctypes.POINTER(mce_result), u64p, i32,
+                                      ctypes.POINTER(mce_result)]
+        lib.mce_graph_info.argtypes = [vp, i32p, ctypes.POINTER(ctypes.c_int64), i32p, i32p, i32p]
+        lib.mce_get_order.argtypes = [vp, i32p, i32p, i32p]
+        lib.mce_destroy.argtypes = [vp]
+        lib.mce_destroy.restype = None
+        lib.mce_last_error.argtypes = []
+        lib.mce_last_error.restype = ctypes.c_char_p
+        _lib = lib
+    return _lib
+
+
+def _check(rc: int):
+    if rc != MCE_OK:
+        raise MCEError(rc, library().mce_last_error().decode(errors="replace"))
+
+
+# ------------------------------------------------------------ torch plumbing
+
+class _TorchAllocator:
+    """Routes the library's device allocations to the PyTorch caching allocator."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+        self._torch = torch
+        self.device = device
+        self.stream = stream
+
+        def _alloc(nbytes, ctx):
+            try:
+                return self._torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream)
+            except Exception:
+                return None
+
+        def _free(ptr, ctx):
+            if ptr:
+                self._torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.c_alloc = ALLOC_FN(_alloc)
+        self.c_free = FREE_FN(_free)
+        self.struct = mce_allocator(self.c_alloc, self.c_free, None)
+
+
+def _as_int32_buffer(a):
+    """(pointer, keepalive, is_device) for a numpy array or torch tensor of int32."""
+    try:
+        import torch
+        if isinstance(a, torch.Tensor):
+            if a.dtype != torch.int32:
+                a = a.to(torch.int32)
+            a = a.contiguous()
+            return ctypes.c_void_p(a.data_ptr()), a, a.is_cuda
+    except ImportError:
+        pass
+    arr = np.ascontiguousarray(a, dtype=np.int32)
+    return ctypes.c_void_p(arr.ctypes.data), arr, False
+
+
+def _current_stream():
+    import torch
+    return torch.cuda.current_stream().cuda_stream, torch.cuda.current_device()
+
+
+@dataclass
+class Result:
+    count: int
+    hash: int
+    max_size: int
+    degeneracy: int
+    tree_nodes: int
+    donations: int
+    ms_prep: float
+    ms_traverse: float
+    hist: Optional[np.ndarray] = None
+
+
+def _result(r: mce_result, hist=None) -> Result:
+    return Result(int(r.count), int(r.hash), int(r.max_size), int(r.degeneracy), int(r.tree_nodes),
+                  int(r.donations), float(r.ms_prep), float(r.ms_traverse), hist)
+
+
+class Handle:
+    """Owns an mce_graph* and the allocator callbacks it uses."""
+
+    def __init__(self, ptr: ctypes.c_void_p, allocator, n: int, G: int):
+        self.ptr = ptr
+        self._allocator = allocator
+        self.n = n
+        self.G = G
+
+    def __del__(self):
+        try:
+            mce_destroy(self)
+        except Exception:
+            pass
+
+
+def mce_default_opts(**kw) -> mce_opts:
+    o = mce_opts()
+    library().mce_default_opts(ctypes.byref(o))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise AttributeError("mce_opts has no field %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def _create(graph_ptr, row_ptr, col, stream, use_torch_allocator):
+    lib = library()
+    rp, rp_keep, rp_dev = _as_int32_buffer(row_ptr)
+    cp, cp_keep, cp_dev = _as_int32_buffer(col if len(col) else np.zeros(1, np.int32))
+    n = int(len(rp_keep)) - 1
+    m = int(len(col)) // 2
+    flags = MCE_FLAG_DEVICE_PTRS if rp_dev else 0
+    if rp_dev != cp_dev:
+        raise ValueError("row_ptr and col must both be host or both be device buffers")
+    s, dev = (stream, None) if stream is not None else _current_stream()
+    if dev is None:
+        import torch
+        dev = torch.cuda.current_device()
+    alloc = _TorchAllocator(dev, s) if use_torch_allocator else None
+    out = ctypes.c_void_p()
+    if graph_ptr is None:
+        rc = lib.mce_create(rp, cp, n, m, flags, ctypes.byref(alloc.struct) if alloc else None,
+                            ctypes.c_void_p(s), ctypes.byref(out))
+        G = 1
+    else:
+        gp, gp_keep, gp_dev = _as_int32_buffer(graph_ptr)
+        if gp_dev != rp_dev:
+            raise ValueError("graph_ptr must live where row_ptr lives")
+        G = int(len(gp_keep)) - 1
+        rc = lib.mce_batch_create(gp, G, rp, cp, n, m, flags,
+                                  ctypes.byref(alloc.struct) if alloc else None, ctypes.c_void_p(s),
+                                  ctypes.byref(out))
+    _check(rc)
+    return Handle(out, alloc, n, G)
+
+
+def mce_create(row_ptr, col, stream: Optional[int] = None, use_torch_allocator: bool = True) -> Handle:
+    """Build a handle from a canonical CSR (numpy / CPU tensor = host, CUDA tensor = device)."""
+    return _create(None, row_ptr, col, stream, use_torch_allocator)
+
+
+def mce_batch_create(graph_ptr, row_ptr, col, stream: Optional[int] = None,
+                     use_torch_allocator: bool = True) -> Handle:
+    return _create(graph_ptr, row_ptr, col, stream, use_torch_allocator)
+
+
+def mce_run(h: Handle, opts: Optional[mce_opts] = None, hist_len: Optional[int] = None) -> Result:
+    lib = library()
+    if hist_len is None:
+        d = mce_graph_info(h)["degeneracy"]
+        hist_len = d + 2
+    hist = np.zeros(max(hist_len, 1), np.uint64)
+    r = mce_result()
+    _check(lib.mce_run(h.ptr, ctypes.byref(opts) if opts is not None else None, ctypes.byref(r),
+                       hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), hist_len))
+    return _result(r, hist[: r.max_size + 1].copy())
+
+
+def mce_run_batch(h: Handle, opts: Optional[mce_opts] = None, hist_len: Optional[int] = None):
+    """(per-graph results, hist [G, hist_len], total)."""
+    lib = library()
+    if hist_len is None:
+        hist_len = mce_graph_info(h)["degeneracy"] + 2
+    per = (mce_result * h.G)()
+    hist = np.zeros((h.G, max(hist_len, 1)), np.uint64)
+    tot = mce_result()
+    _check(lib.mce_run_batch(h.ptr, ctypes.byref(opts) if opts is not None else None, per,
+                             hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)), hist_len,
+                             ctypes.byref(tot)))
+    return [_result(per[i]) for i in range(h.G)], hist, _result(tot)
+
+
+def mce_graph_info(h: Handle) -> dict:
+    n, G, d, md = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    m = ctypes.c_int64()
+    _check(library().mce_graph_info(h.ptr, ctypes.byref(n), ctypes.byref(m), ctypes.byref(G),
+                                    ctypes.byref(d), ctypes.byref(md)))
+    return {"n": n.value, "m": m.value, "G": G.value, "degeneracy": d.value, "max_degree": md.value}
+
+
+def mce_get_order(h: Handle):
+    """(core, rank, out_degree) numpy int32 arrays indexed by input vertex id."""
+    n = h.n
+    core = np.zeros(max(n, 1), np.int32)
+    rank = np.zeros(max(n, 1), np.int32)
+    outd = np.zeros(max(n, 1), np.int32)
+    P = ctypes.POINTER(ctypes.c_int32)
+    _check(library().mce_get_order(h.ptr, core.ctypes.data_as(P), rank.ctypes.data_as(P),
+                                   outd.ctypes.data_as(P)))
+    return core[:n], rank[:n], outd[:n]
+
+
+def mce_destroy(h: Handle):
+    if h is not None and h.ptr:
+        library().mce_destroy(h.ptr)
+        h.ptr = ctypes.c_void_p()
+
+
+def enumerate_maximal_cliques(row_ptr, col, per_root: bool = False, **opt_fields):
+    """One-shot convenience: create, run, destroy. With per_root, also returns
+    per-vertex subtree (count, hash, nodes) as numpy uint64 arrays."""
+    import torch
+    h = mce_create(row_ptr, col)
+    try:
+        opts = mce_default_opts(**opt_fields)
+        keep = []
+        if per_root:
+            n = max(h.n, 1)
+            for name in ("root_count", "root_hash", "root_nodes"):
+                t = torch.zeros(n, dtype=torch.int64, device="cuda")
+                keep.append(t)
+                setattr(opts, name, t.data_ptr())
+        res = mce_run(h, opts)
+        if per_root:
+            torch.cuda.current_stream().synchronize()
+            arrs = [t.cpu().numpy().view(np.uint64)[: h.n] for t in keep]
+            return res, arrs
+        return res
+    finally:
+        mce_destroy(h)

@@ -1,0 +1,219 @@
+"""GPU engine vs the CPU oracle, through the C ABI: every result bit-exact.
+
+Compared per graph: clique count, size histogram, 64-bit hash, largest
+clique; per root vertex: the subtree's clique count, hash sum and number of
+Bron-Kerbosch calls (the engine walks the same tree as the oracle's
+pivot-from-P-u-X_P mode, so even the node counts agree); the degeneracy
+peel's core numbers and ranks.
+"""
+import numpy as np
+import pytest
+
+import gen
+import oracle
+from test_oracle import M64, h_clique
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2212_01473_gb300 as mce  # noqa: E402
+
+
+def run(g, per_root=False, **opts):
+    return mce.enumerate_maximal_cliques(g.row_ptr, g.col, per_root=per_root, **opts)
+
+
+def same(r, o):
+    assert r.count == o.count
+    assert r.hash == o.hash
+    assert r.max_size == o.max_size
+    assert np.array_equal(r.hist.astype(np.uint64), o.hist.astype(np.uint64))
+
+
+def check_against_oracle(g, per_root=True, **opts):
+    o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=per_root)
+    if per_root:
+        r, (rc, rh, rn) = run(g, per_root=True, **opts)
+        same(r, o)
+        assert np.array_equal(rc, o.root_count)
+        assert np.array_equal(rh, o.root_hash)
+        assert np.array_equal(rn, o.root_nodes)
+        assert r.tree_nodes == int(o.root_nodes.sum())
+    else:
+        r = run(g, **opts)
+        same(r, o)
+    return r, o
+
+
+CLOSED = [gen.complete(1), gen.complete(2), gen.complete(7), gen.empty(5), gen.cycle(4), gen.cycle(3),
+          gen.cycle(33), gen.moon_moser(2), gen.moon_moser(6), gen.multipartite(7, 2),
+          gen.worked_example(), gen.random_forest(60, 1)]
+
+
+@pytest.mark.parametrize("g", CLOSED, ids=[g.name for g in CLOSED])
+def test_closed_forms(g):
+    check_against_oracle(g)
+
+
+@pytest.mark.parametrize("n,p,seed", [(30, 0.3, 0), (64, 0.5, 1), (100, 0.2, 2), (150, 0.6, 3),
+                                      (300, 0.1, 4), (500, 0.05, 5), (120, 0.85, 6), (1000, 0.02, 7)])
+def test_random_graphs(n, p, seed):
+    check_against_oracle(gen.gnp(n, p, seed))
+
+
+def test_er_2000_per_root():
+    check_against_oracle(gen.workload("er_2000"))
+
+
+@pytest.mark.parametrize("maker", [lambda: gen.workload("er_2000"), lambda: gen.gnp(3000, 0.01, 3),
+                                   lambda: gen.moon_moser(8), lambda: gen.random_forest(500, 2),
+                                   lambda: gen.chung_lu(20000, 8.0, 2.1, 500.0, 5, 8, 16, 11)])
+def test_peel_matches_oracle(maker):
+    g = maker()
+    core_o, rank_o, order_o, _ = oracle.peel(g.row_ptr, g.col)
+    h = mce.mce_create(g.row_ptr, g.col)
+    core, rank, outd = mce.mce_get_order(h)
+    info = mce.mce_graph_info(h)
+    mce.mce_destroy(h)
+    assert np.array_equal(core, core_o)
+    assert np.array_equal(rank, rank_o)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    later = np.bincount(src[rank_o[g.col] > rank_o[src]], minlength=g.n)
+    assert np.array_equal(outd, later)
+    assert info["degeneracy"] == (int(core_o.max()) if g.n else 0)
+    assert info["max_degree"] == (int(g.degrees().max()) if g.n else 0)
+
+
+@pytest.mark.parametrize("blocks,donate,wl", [(1, 1, 1), (2, 1, 1), (3, 2, 1), (5, 10, 1), (4, 1, 0)])
+def test_worker_list_interleavings(blocks, donate, wl):
+    # tiny grids force phase 2 early and many donations; results and the
+    # tree itself (node counts per root) must not change
+    g = gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5)
+    r, o = check_against_oracle(g, blocks=blocks, donate_min_p=donate, worker_list=wl)
+    if wl == 0:
+        assert r.donations == 0
+
+
+def test_worker_list_donates():
+    g = gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5)
+    r = run(g, blocks=2, donate_min_p=1)
+    assert r.donations > 0
+
+
+def _complete_minus_matching(n, t):
+    e = [(i, j) for i in range(n) for j in range(i + 1, n)]
+    missing = {(2 * k, 2 * k + 1) for k in range(t)}
+    g = gen.from_edges(n, [x for x in e if x not in missing])
+    # maximal cliques: one endpoint of every removed edge, plus all other vertices
+    rest = list(range(2 * t, n))
+    cl = []
+    for mask in range(1 << t):
+        cl.append([2 * k + ((mask >> k) & 1) for k in range(t)] + rest)
+    return g, cl
+
+
+@pytest.mark.parametrize("n,t", [(33, 2), (65, 3), (129, 2), (300, 3), (500, 2), (700, 2), (900, 1),
+                                 (1100, 2), (1300, 1), (2300, 1)])
+def test_wide_rows_closed_form(n, t):
+    # |P0| of the first root is n-1: exercises every bitset width class,
+    # including rows kept in global memory
+    g, cl = _complete_minus_matching(n, t)
+    r = run(g)
+    assert r.count == len(cl) == 2 ** t
+    assert r.max_size == n - t
+    assert r.hash == sum(h_clique(c) for c in cl) & M64
+    assert r.hist[n - t] == 2 ** t and int(r.hist.sum()) == 2 ** t
+
+
+def test_complete_graph_node_counts():
+    # K_n: root r walks a chain of n - r calls (pivot restricted to P u X_P)
+    n = 200
+    g = gen.complete(n)
+    r, (rc, rh, rn) = run(g, per_root=True)
+    assert rn.tolist() == [n - i for i in range(n)]
+    assert r.tree_nodes == n * (n + 1) // 2
+
+
+def test_device_pointer_input():
+    g = gen.gnp(400, 0.07, 9)
+    o = oracle.mce(g.row_ptr, g.col)
+    h = mce.mce_create(torch.from_numpy(g.row_ptr).cuda(), torch.from_numpy(g.col).cuda())
+    r = mce.mce_run(h)
+    mce.mce_destroy(h)
+    same(r, o)
+
+
+def test_empty_graph():
+    g = gen.empty(0)
+    r = run(g)
+    assert r.count == 0 and r.max_size == 0
+
+
+@pytest.mark.parametrize("bad", ["unsorted", "asym", "loop", "dup", "range", "rowptr"])
+def test_invalid_graph_rejected(bad):
+    g = gen.gnp(40, 0.3, 1)
+    rp, col = g.row_ptr.copy(), g.col.copy()
+    v = int(np.argmax(np.diff(rp) >= 3))
+    a, b = rp[v], rp[v + 1]
+    if bad == "unsorted":
+        col[a], col[a + 1] = col[a + 1], col[a]
+    elif bad == "asym":
+        col[a] = [x for x in range(40) if x != v and x not in set(col[a:b])][0]
+        col[a:b] = np.sort(col[a:b])
+    elif bad == "loop":
+        col[a] = v
+        col[a:b] = np.sort(col[a:b])
+    elif bad == "dup":
+        col[a + 1] = col[a]
+    elif bad == "range":
+        col[b - 1] = 40
+    elif bad == "rowptr":
+        rp[5] = rp[6] + 1
+    with pytest.raises(mce.MCEError) as ei:
+        mce.mce_create(rp, col)
+    assert ei.value.code == mce.MCE_EINVAL
+
+
+def test_hist_too_short_is_erange():
+    g = gen.complete(6)
+    h = mce.mce_create(g.row_ptr, g.col)
+    with pytest.raises(mce.MCEError) as ei:
+        mce.mce_run(h, hist_len=4)
+    assert ei.value.code == mce.MCE_ERANGE
+    mce.mce_destroy(h)
+
+
+def test_batch_small():
+    parts = [gen.gnp(80, 0.15, 1), gen.moon_moser(4), gen.complete(9), gen.empty(3), gen.gnp(200, 0.05, 2),
+             gen.cycle(10)]
+    u = gen.disjoint_union(parts)
+    h = mce.mce_batch_create(u.graph_ptr, u.row_ptr, u.col)
+    per, hist, tot = mce.mce_run_batch(h)
+    mce.mce_destroy(h)
+    for i, p in enumerate(parts):
+        # hashes use the ids of the concatenated graph
+        a, z = int(u.graph_ptr[i]), int(u.graph_ptr[i + 1])
+        o = oracle.mce(u.row_ptr, u.col, roots=np.arange(a, z, dtype=np.int32))
+        assert (per[i].count, per[i].hash, per[i].max_size) == (o.count, o.hash, o.max_size), i
+        hl = len(o.hist)
+        assert np.array_equal(hist[i, :hl], o.hist) and not hist[i, hl:].any()
+        # counts and histogram do not depend on ids: the part alone agrees
+        op = oracle.mce(p.row_ptr, p.col)
+        assert per[i].count == op.count and np.array_equal(hist[i, :len(op.hist)], op.hist)
+    ou = oracle.mce(u.row_ptr, u.col)
+    assert (tot.count, tot.hash) == (ou.count, ou.hash)
+
+
+def test_batch_generated():
+    b = gen.batch(48, 7, nmin=20, nmax=400, dmin=3, dmax=30, mm_every=8)
+    h = mce.mce_batch_create(b.graph_ptr, b.row_ptr, b.col)
+    per, hist, tot = mce.mce_run_batch(h)
+    mce.mce_destroy(h)
+    for i in range(48):
+        a, z = int(b.graph_ptr[i]), int(b.graph_ptr[i + 1])
+        o = oracle.mce(b.row_ptr, b.col, roots=np.arange(a, z, dtype=np.int32))
+        assert (per[i].count, per[i].hash) == (o.count, o.hash), i
+        if b.mm_sizes[i]:
+            assert np.count_nonzero(hist[i]) >= 1
