@@ -87,8 +87,8 @@ typedef struct {
     int32_t worker_list;   /* 1 = idle workers receive donated subtrees (Sec. III-C), 0 = off */
     int32_t donate_min_p;  /* donate a branch only if its |P| >= this (Sec. III-C: 10) */
     int32_t blocks;        /* persistent blocks per width class; 0 = all that fit on the GPU */
-    int32_t tune;          /* 0 = built-in launch table; 1 = use the table set by mce_set_tuning */
-    int32_t reserved;
+    int32_t tune;          /* reserved, set 0 */
+    int32_t stats;         /* 1 = collect per-phase SM cycle counters (see mce_stats); slows the run */
     int64_t timeout_ms;    /* give-up bound for every device-side wait (default 60000) */
     /* optional DEVICE buffers, indexed by input vertex id, length n: the
      * clique count, hash sum and Bron-Kerbosch call count (tree nodes, root
@@ -171,6 +171,33 @@ int mce_graph_info(const mce_graph *g, int32_t *n, int64_t *m, int32_t *G, int32
  * the degeneracy order, out_degree[v] = |P| of v's root (later neighbours).
  */
 int mce_get_order(const mce_graph *g, int32_t *core, int32_t *rank, int32_t *out_degree);
+
+/* Launch facts and optional counters of the handle's last mce_run / mce_run_batch. */
+#define MCE_STATS_MAX_CLASSES 16
+#define MCE_STATS_PHASES 8
+typedef struct {
+    int32_t struct_size;                         /* sizeof(mce_stats), set by the caller */
+    int32_t n_classes;                           /* width classes launched (entries below) */
+    int32_t class_wp[MCE_STATS_MAX_CLASSES];     /* 32-bit words per bitset row; 0 = roots with |P| = 0 */
+    int32_t class_roots[MCE_STATS_MAX_CLASSES];  /* roots in the class */
+    int32_t class_rows[MCE_STATS_MAX_CLASSES];   /* largest |P| of a root in the class */
+    int32_t class_blocks[MCE_STATS_MAX_CLASSES]; /* persistent blocks launched */
+    int32_t class_groups[MCE_STATS_MAX_CLASSES]; /* cooperating groups (subtree workers) */
+    int32_t class_group_warps[MCE_STATS_MAX_CLASSES];
+    double class_ms[MCE_STATS_MAX_CLASSES];      /* device time of the launch (CUDA events) */
+    uint64_t kernel_launches;                    /* kernels of the last create + run */
+    int64_t peel_rounds;                         /* sub-rounds of the degeneracy peel */
+    /* with opts.stats = 1: SM cycles and event counts summed over groups, per
+     * phase: 0 induced subgraph + excluded rows (count: tasks), 1 pivot
+     * (candidates scored), 2 branch + child sets (tree nodes), 3 leaf
+     * maximality tests (excluded rows tested), 4 excluded-set partition
+     * (rows moved), 5 worker-list donations (donations), 6 idle wait
+     * (subtrees received), 7 unused */
+    uint64_t phase_cycles[MCE_STATS_PHASES];
+    uint64_t phase_counts[MCE_STATS_PHASES];
+} mce_stats;
+
+int mce_get_stats(const mce_graph *g, mce_stats *out);
 
 /* Release the handle and all its device memory. NULL is a no-op. */
 void mce_destroy(mce_graph *g);

@@ -30,6 +30,8 @@ def _load():
         lib.oracle_mce_roots.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                          i32p, ctypes.c_int64, u64p, u64p, u64p, ctypes.c_int32,
                                          i32p, u64p, u64p, u64p]
+        lib.oracle_mce_work.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                        i32p, ctypes.c_int64, u64p, u64p]
         lib.oracle_clique_hash.argtypes = [i32p, ctypes.c_int32]
         lib.oracle_clique_hash.restype = ctypes.c_uint64
         lib.oracle_default_threads.restype = ctypes.c_int32
@@ -118,6 +120,24 @@ def mce(row_ptr, col, mode: int = PIVOT_FULL, threads: int = 0, per_root: bool =
     if per_root:
         res.root_count, res.root_hash, res.root_nodes = rc_arr[:n], rh_arr[:n], rn_arr[:n]
     return res
+
+
+def work(row_ptr, col, mode: int = PIVOT_IP, threads: int = 0, roots=None):
+    """(root_nodes, root_work) uint64 per input vertex id; see oracle_mce_work."""
+    rp, rpp = _i32(row_ptr)
+    c, cp = _i32(col if len(col) else np.zeros(1, np.int32))
+    n = len(rp) - 1
+    rn = np.zeros(max(n, 1), np.uint64)
+    rw = np.zeros(max(n, 1), np.uint64)
+    if roots is None:
+        rop, nr = None, 0
+    else:
+        ro, rop = _i32(roots)
+        nr = len(ro)
+    rc = _load().oracle_mce_work(n, rpp, cp, mode, threads, rop, nr, _u64(rn), _u64(rw))
+    if rc != 0:
+        raise RuntimeError("oracle_mce_work failed: %d" % rc)
+    return rn[:n], rw[:n]
 
 
 def clique_hash(ids) -> int:

@@ -135,6 +135,8 @@ typedef struct {
     int32_t rlen;
     int32_t *ids;      /* scratch for input ids when reporting */
     uint64_t count, hash, nodes;
+    uint64_t work;     /* bitset word operations the GPU formulation needs (see bk) */
+    int32_t words;     /* 32-bit words per bitset row for the current root: ceil(|P0|/32) */
     uint64_t *hist;
     int32_t hist_len, max_size;
 } walk_t;
@@ -193,20 +195,36 @@ static void bk(walk_t *w, int32_t *P, int32_t np, int32_t *XP, int32_t nxp, cons
         memcpy(B, P, (size_t)np * sizeof(int32_t));
         nb = np;
     } else {
-        /* pivot u maximising |P n N(u)|, ties to the smallest rank */
+        /* pivot u maximising |P n N(u)|, ties to the smallest rank. The
+         * candidates are visited in ascending rank; `scanned` counts them up
+         * to the first that reaches the largest possible score (|P| for an
+         * excluded vertex, |P|-1 for a vertex of P), after which no later
+         * candidate can win. It feeds only the work counter. */
         int32_t best = -1, best_u = -1;
         const int32_t *lists[3] = {P, XP, XX};
         int32_t lens[3] = {np, nxp, g->mode == ORACLE_PIVOT_FULL ? nxx : 0};
-        for (int32_t L = 0; L < 3; L++)
-            for (int32_t i = 0; i < lens[L]; i++) {
-                int32_t u = lists[L][i], score = 0;
-                for (int32_t j = 0; j < np; j++) score += adjacent(g, u, P[j]);
-                if (score > best || (score == best && u < best_u)) { best = score; best_u = u; }
-            }
+        int32_t pos[3] = {0, 0, 0};
+        const int32_t bound = (lens[1] + lens[2] > 0) ? np : np - 1;
+        int64_t scanned = 0, total = (int64_t)lens[0] + lens[1] + lens[2];
+        int reached = 0;
+        for (;;) {
+            int32_t L = -1;
+            for (int32_t q = 0; q < 3; q++)
+                if (pos[q] < lens[q] && (L < 0 || lists[q][pos[q]] < lists[L][pos[L]])) L = q;
+            if (L < 0) break;
+            int32_t u = lists[L][pos[L]++], score = 0;
+            for (int32_t j = 0; j < np; j++) score += adjacent(g, u, P[j]);
+            if (!reached) scanned++;
+            if (score == bound) reached = 1;
+            if (score > best || (score == best && u < best_u)) { best = score; best_u = u; }
+        }
+        if (!reached) scanned = total;
+        w->work += (uint64_t)w->words * (uint64_t)(scanned + 1);
         for (int32_t j = 0; j < np; j++)
             if (!adjacent(g, best_u, P[j])) B[nb++] = P[j];
     }
 
+    if (g->mode != ORACLE_NO_PIVOT) w->work += 2ull * (uint64_t)w->words * (uint64_t)nb;
     for (int32_t bi = 0; bi < nb; bi++) {
         int32_t v = B[bi];
         /* child sets: P n N(v), X n N(v) */
@@ -247,6 +265,7 @@ static void first_level(walk_t *w, int32_t r) {
     int32_t *P = (int32_t *)malloc((size_t)(np + 1) * sizeof(int32_t));
     int32_t *XP = (int32_t *)malloc((size_t)(np + 1) * sizeof(int32_t));
     memcpy(P, row + split, (size_t)np * sizeof(int32_t));
+    w->words = (np + 31) / 32;
     w->root = r;
     w->rlen = 0;
     w->R[w->rlen++] = r;
@@ -261,7 +280,7 @@ typedef struct {
     int64_t n_roots;
     atomic_llong next;
     int32_t hist_len, max_deg;
-    uint64_t *root_count, *root_hash, *root_nodes; /* by input id */
+    uint64_t *root_count, *root_hash, *root_nodes, *root_work; /* by input id */
     /* merged results */
     pthread_mutex_t mu;
     uint64_t count, hash;
@@ -290,12 +309,13 @@ static void *worker(void *arg) {
         long long i = atomic_fetch_add(&job->next, 1);
         if (i >= job->n_roots) break;
         int32_t r = job->roots[i];
-        uint64_t c0 = w.count, h0 = w.hash, n0 = w.nodes;
+        uint64_t c0 = w.count, h0 = w.hash, n0 = w.nodes, k0 = w.work;
         first_level(&w, r);
         int32_t id = job->g->order[r];
         if (job->root_count) job->root_count[id] = w.count - c0;
         if (job->root_hash) job->root_hash[id] = w.hash - h0;
         if (job->root_nodes) job->root_nodes[id] = w.nodes - n0;
+        if (job->root_work) job->root_work[id] = w.work - k0;
     }
     pthread_mutex_lock(&job->mu);
     job->count += w.count;
@@ -315,7 +335,7 @@ int32_t oracle_default_threads(void) {
 static int run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode, int32_t nthreads,
                const int32_t *roots_in, int64_t n_roots_in, uint64_t *count, uint64_t *hash,
                uint64_t *hist, int32_t hist_len, int32_t *max_size, uint64_t *root_count,
-               uint64_t *root_hash, uint64_t *root_nodes) {
+               uint64_t *root_hash, uint64_t *root_nodes, uint64_t *root_work) {
     if (oracle_validate(n, row_ptr, col)) return 1;
     if (mode < 0 || mode > 2) return 1;
     int32_t *rank = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
@@ -360,6 +380,7 @@ static int run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mo
     job.root_count = root_count;
     job.root_hash = root_hash;
     job.root_nodes = root_nodes;
+    job.root_work = root_work;
     job.hist = (uint64_t *)calloc((size_t)(job.hist_len > 0 ? job.hist_len : 1), sizeof(uint64_t));
     if (!job.hist) { rc = 2; goto done; }
     pthread_mutex_init(&job.mu, NULL);
@@ -391,7 +412,7 @@ int oracle_mce(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mo
                int32_t hist_len, int32_t *max_size, uint64_t *root_count,
                uint64_t *root_hash, uint64_t *root_nodes) {
     return run(n, row_ptr, col, mode, nthreads, NULL, 0, count, hash, hist, hist_len, max_size,
-               root_count, root_hash, root_nodes);
+               root_count, root_hash, root_nodes, NULL);
 }
 
 int oracle_mce_roots(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode,
@@ -400,5 +421,15 @@ int oracle_mce_roots(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
                      uint64_t *root_count, uint64_t *root_hash, uint64_t *root_nodes) {
     if (!roots || n_roots < 0) return 1;
     return run(n, row_ptr, col, mode, nthreads, roots, n_roots, count, hash, hist, hist_len,
-               max_size, root_count, root_hash, root_nodes);
+               max_size, root_count, root_hash, root_nodes, NULL);
+}
+
+int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode,
+                    int32_t nthreads, const int32_t *roots, int64_t n_roots, uint64_t *root_nodes,
+                    uint64_t *root_work) {
+    uint64_t count, hash;
+    int32_t max_size;
+    int rc = run(n, row_ptr, col, mode, nthreads, roots, roots ? n_roots : 0, &count, &hash, NULL, 0,
+                 &max_size, NULL, NULL, root_nodes, root_work);
+    return rc == 5 ? 0 : rc; /* no histogram was asked for */
 }

@@ -77,6 +77,19 @@ int oracle_mce_roots(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
                      uint64_t *hash, uint64_t *hist, int32_t hist_len, int32_t *max_size,
                      uint64_t *root_count, uint64_t *root_hash, uint64_t *root_nodes);
 
+/*
+ * Per-root tree nodes and bitset word operations of the GPU formulation
+ * (roots = NULL: all vertices). Word operations, with W = ceil(|P0|/32) for
+ * the root's P0: at every call with P non-empty, W per pivot candidate
+ * scanned (candidates in ascending rank, stopping at the first that reaches
+ * the largest possible score), W for the branch set P - N(pivot), and 2W per
+ * branch for the child's P and X_P. Used as the algorithmic work of the
+ * integer-pipe roofline. Returns as oracle_mce (hist not collected).
+ */
+int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode,
+                    int32_t nthreads, const int32_t *roots, int64_t n_roots, uint64_t *root_nodes,
+                    uint64_t *root_work);
+
 /* h(C) for a clique given by input ids (any order) */
 uint64_t oracle_clique_hash(const int32_t *ids, int32_t k);
 

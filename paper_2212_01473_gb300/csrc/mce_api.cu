@@ -12,7 +12,7 @@
 
 namespace mce {
 #define MCE_EXTERN_WP(WP)                                                                             \
-    extern template cudaError_t plan_wp<WP>(int, int, int, int, ClassLaunch *);                       \
+    extern template cudaError_t plan_wp<WP>(int, int, int, int, bool, ClassLaunch *);                       \
     extern template cudaError_t launch_wp<WP>(const ClassLaunch &, const DevGraph &, const DevOut &,  \
                                               const ClassArgs &, int, cudaStream_t);
 MCE_EXTERN_WP(1)
@@ -25,17 +25,17 @@ MCE_EXTERN_WP(36)
 MCE_EXTERN_WP(68)
 MCE_EXTERN_WP(132)
 
-static cudaError_t plan_class_wp(int wp, int rows, int sms, int smem, int req, ClassLaunch *L) {
+static cudaError_t plan_class_wp(int wp, int rows, int sms, int smem, int req, bool bh, ClassLaunch *L) {
     switch (wp) {
-        case 1: return plan_wp<1>(rows, sms, smem, req, L);
-        case 2: return plan_wp<2>(rows, sms, smem, req, L);
-        case 4: return plan_wp<4>(rows, sms, smem, req, L);
-        case 12: return plan_wp<12>(rows, sms, smem, req, L);
-        case 20: return plan_wp<20>(rows, sms, smem, req, L);
-        case 28: return plan_wp<28>(rows, sms, smem, req, L);
-        case 36: return plan_wp<36>(rows, sms, smem, req, L);
-        case 68: return plan_wp<68>(rows, sms, smem, req, L);
-        case 132: return plan_wp<132>(rows, sms, smem, req, L);
+        case 1: return plan_wp<1>(rows, sms, smem, req, bh, L);
+        case 2: return plan_wp<2>(rows, sms, smem, req, bh, L);
+        case 4: return plan_wp<4>(rows, sms, smem, req, bh, L);
+        case 12: return plan_wp<12>(rows, sms, smem, req, bh, L);
+        case 20: return plan_wp<20>(rows, sms, smem, req, bh, L);
+        case 28: return plan_wp<28>(rows, sms, smem, req, bh, L);
+        case 36: return plan_wp<36>(rows, sms, smem, req, bh, L);
+        case 68: return plan_wp<68>(rows, sms, smem, req, bh, L);
+        case 132: return plan_wp<132>(rows, sms, smem, req, bh, L);
     }
     return cudaErrorInvalidValue;
 }
@@ -174,6 +174,8 @@ struct mce_graph {
     size_t scratch_bytes = 0;
     double ms_prep = 0;
     int64_t peel_rounds = 0;
+    uint64_t create_launches = 0;  // kernels launched by create
+    mce_stats last{};              // facts of the last run
 };
 
 static void *dalloc(mce_graph *g, size_t bytes) {
@@ -249,6 +251,7 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
     const int32_t *d_rp = row_ptr, *d_col = col, *d_gptr = nullptr;
     std::vector<int32_t> h_gptr;
     int dev = 0;
+    uint64_t launch_base = launch_counter();
     if (alloc) {
         g->alloc = *alloc;
         g->has_alloc = true;
@@ -276,6 +279,7 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
             if (h_gptr[i] > h_gptr[i + 1]) { rc = fail(MCE_EINVAL, "graph_ptr not non-decreasing"); goto cleanup; }
     }
     CK(cudaEventRecord(ev0, g->stream));
+    launch_base = launch_counter();
     if (!dev_in) {
         int32_t *a = dnew<int32_t>(g, (size_t)n + 1, &tmp);
         int32_t *b = dnew<int32_t>(g, (size_t)2 * m + 1, &tmp);
@@ -313,6 +317,7 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
         CK(cudaMemcpyAsync(gp, h_gptr.data(), ((size_t)G + 1) * 4, cudaMemcpyHostToDevice, g->stream));
         d_gptr = gp;
         k_check_batch<<<(unsigned)std::min<int64_t>(65536, ((int64_t)n + 255) / 256), 256, 0, g->stream>>>(n, d_rp, d_col, gp, G, status);
+        count_launch();
         CK(cudaGetLastError());
     }
     CK(cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, g->stream));
@@ -367,7 +372,9 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
         CK(launch_mix_gid(n, g->order, g->mixid, g->gid, d_gptr, G, g->stream));
         CK(cudaMemsetAsync(small, 0, 64 * 4, g->stream));
         k_last_core<<<1, 1, 0, g->stream>>>(g->order, g->core, n, small);
+        count_launch();
         if (n > 0) k_max_deg<<<(unsigned)std::min<int64_t>(4096, ((int64_t)n + 255) / 256), 256, 0, g->stream>>>(g->outdeg, indeg, n, small + 1);
+        count_launch();
         CK(cudaGetLastError());
         // width classes: small[8..8+K) rows, [24..) x cap, [40..) counts
         int *cls_rows = small + 8, *cls_x = small + 24, *cls_cnt = small + 40;
@@ -396,6 +403,7 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
         float ms = 0;
         CK(cudaEventElapsedTime(&ms, ev0, ev1));
         g->ms_prep = ms;
+        g->create_launches = launch_counter() - launch_base;
     }
 cleanup:
     if (g->stream) cudaStreamSynchronize(g->stream);
@@ -461,8 +469,12 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     int hflags[4] = {0, 0, 0, 0};
     DevGraph dg{};
     DevOut dout{};
-    // outputs: count[G], hash[G], hist[G*HL], nodes, donations | max_size, status
-    const size_t out_words64 = (size_t)2 * G + (size_t)G * HL + 4;
+    // outputs: count[G], hash[G], hist[G*HL], nodes, donations | max_size, status,
+    // phase cycles and counts
+    const size_t out_words64 = (size_t)2 * G + (size_t)G * HL + 4 + 2 * kNumPhases;
+    mce_stats st{};
+    std::vector<cudaEvent_t> cev;
+    uint64_t launches = 0;
     unsigned long long *obuf = (unsigned long long *)dalloc(g, out_words64 * 8 + 64);
     if (!obuf) return fail(MCE_ENOMEM, "device allocation of outputs failed");
     CK(cudaMemsetAsync(obuf, 0, out_words64 * 8 + 64, g->stream));
@@ -488,22 +500,38 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     dout.donations = dout.nodes + 1;
     dout.max_size = (int *)(dout.nodes + 2);
     dout.status = dout.max_size + 1;
+    dout.phase_cycles = dout.nodes + 4;
+    dout.phase_counts = dout.phase_cycles + kNumPhases;
     dout.root_count = (unsigned long long *)opts.root_count;
     dout.root_hash = (unsigned long long *)opts.root_hash;
     dout.root_nodes = (unsigned long long *)opts.root_nodes;
+    st.struct_size = (int32_t)sizeof(mce_stats);
     CK(cudaEventRecord(ev0, g->stream));
     if (g->class_count[kNumClasses] > 0) {
         const int nr = g->class_count[kNumClasses];
-        k_trivial_roots<<<(unsigned)std::min<int64_t>(4096, ((int64_t)nr + 255) / 256), 256, 0, g->stream>>>(
-            dg, dout, g->class_roots[kNumClasses], nr);
+        const unsigned nb = (unsigned)std::min<int64_t>(4096, ((int64_t)nr + 255) / 256);
+        cudaEvent_t a0, a1;
+        CK(cudaEventCreate(&a0));
+        cev.push_back(a0);
+        CK(cudaEventCreate(&a1));
+        cev.push_back(a1);
+        CK(cudaEventRecord(a0, g->stream));
+        k_trivial_roots<<<nb, 256, 0, g->stream>>>(dg, dout, g->class_roots[kNumClasses], nr);
+        count_launch();
         CK(cudaGetLastError());
+        CK(cudaEventRecord(a1, g->stream));
+        launches++;
+        const int k = st.n_classes++;
+        st.class_wp[k] = 0;
+        st.class_roots[k] = nr;
+        st.class_blocks[k] = (int32_t)nb;
     }
     // heaviest width classes first
     for (int c = kNumClasses - 1; c >= 0; c--) {
         if (g->class_count[c] == 0) continue;
         const int rows = g->class_rows[c];
         ClassLaunch L{};
-        CK(plan_class_wp(class_wp(c), rows, g->sm_count, g->smem_optin, opts.blocks, &L));
+        CK(plan_class_wp(class_wp(c), rows, g->sm_count, g->smem_optin, opts.blocks, g->gid == nullptr, &L));
         const int groups = L.blocks * (L.warps_per_block / L.gw);
         const size_t aw = arena_words(L.wp, rows, g->class_x[c], L.a_global, stack_in_smem(L.wp));
         const int mail_words = 4 + 3 * L.wp;
@@ -520,6 +548,7 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         a.worker_list = opts.worker_list ? 1 : 0;
         a.donate_min_p = opts.donate_min_p;
         a.root_chunk = 1;
+        a.stats = opts.stats ? 1 : 0;
         a.timeout_ns = (uint64_t)opts.timeout_ms * 1000000ull;
         a.arena = sw;
         a.arena_words_per_group = aw;
@@ -532,7 +561,22 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         int hctl[CTL_NCTL] = {0};
         hctl[CTL_ACTIVE] = groups;
         CK(cudaMemcpyAsync(a.ctl, hctl, sizeof hctl, cudaMemcpyHostToDevice, g->stream));
+        cudaEvent_t a0, a1;
+        CK(cudaEventCreate(&a0));
+        cev.push_back(a0);
+        CK(cudaEventCreate(&a1));
+        cev.push_back(a1);
+        CK(cudaEventRecord(a0, g->stream));
         CK(launch_class_wp(L, dg, dout, a, rows, g->stream));
+        CK(cudaEventRecord(a1, g->stream));
+        launches++;
+        const int k = st.n_classes++;
+        st.class_wp[k] = L.wp;
+        st.class_roots[k] = g->class_count[c];
+        st.class_rows[k] = rows;
+        st.class_blocks[k] = L.blocks;
+        st.class_groups[k] = groups;
+        st.class_group_warps[k] = L.gw;
     }
     CK(cudaEventRecord(ev1, g->stream));
     CK(cudaMemcpyAsync(hcnt.data(), dout.count, (size_t)G * 8, cudaMemcpyDeviceToHost, g->stream));
@@ -540,7 +584,16 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     CK(cudaMemcpyAsync(hhist.data(), dout.hist, (size_t)G * HL * 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaMemcpyAsync(hmisc, dout.nodes, 2 * 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaMemcpyAsync(hflags, dout.max_size, 2 * 4, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaMemcpyAsync(st.phase_cycles, dout.phase_cycles, 2 * kNumPhases * 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
+    for (int k = 0; k < st.n_classes; k++) {
+        float cms = 0;
+        CK(cudaEventElapsedTime(&cms, cev[2 * k], cev[2 * k + 1]));
+        st.class_ms[k] = cms;
+    }
+    st.kernel_launches = g->create_launches + launches;
+    st.peel_rounds = g->peel_rounds;
+    g->last = st;
     if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms", (long long)opts.timeout_ms); goto cleanup; }
     if (hflags[1] & ST_OVERFLOW) { rc = fail(MCE_ECUDA, "internal capacity exceeded in the traversal"); goto cleanup; }
     {
@@ -582,6 +635,7 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     }
 cleanup:
     if (g->stream) cudaStreamSynchronize(g->stream);
+    for (cudaEvent_t e : cev) cudaEventDestroy(e);
     dfree(g, obuf);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);
@@ -628,6 +682,13 @@ extern "C" int mce_get_order(const mce_graph *g, int32_t *core, int32_t *rank, i
     if (rank) memcpy(rank, hrank.data(), n * 4);
     if (out_degree)
         for (size_t v = 0; v < n; v++) out_degree[v] = hout[(size_t)hrank[v]];
+    return MCE_OK;
+}
+
+extern "C" int mce_get_stats(const mce_graph *g, mce_stats *out) {
+    if (!g || !out) return fail(MCE_EINVAL, "NULL argument");
+    if (out->struct_size != (int32_t)sizeof(mce_stats)) return fail(MCE_EINVAL, "mce_stats.struct_size mismatch");
+    *out = g->last;
     return MCE_OK;
 }
 

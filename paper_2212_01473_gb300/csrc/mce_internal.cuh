@@ -95,6 +95,13 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
     return s_ok != 0;
 }
 
+// Kernel launches made by this host thread (reported by mce_get_stats).
+inline uint64_t &launch_counter() {
+    static thread_local uint64_t c = 0;
+    return c;
+}
+inline void count_launch() { launch_counter()++; }
+
 // ----------------------------------------------------------------- handles
 
 // Everything the traversal needs about the oriented graph (device pointers).
@@ -110,6 +117,18 @@ struct DevGraph {
     const int32_t *gid;       // rank -> graph index (NULL when G == 1)
 };
 
+// Phases of the optional per-group cycle counters (mce_stats.phase_*).
+enum Phase : int {
+    PH_SETUP = 0,      // induced subgraph + X_X rows (+ receiver filter); count = tasks
+    PH_PIVOT = 1,      // candidate list + pivot scan; count = candidates scored
+    PH_BRANCH = 2,     // next branch + child sets; count = tree nodes
+    PH_LEAF = 3,       // maximality test of leaf children; count = X_X rows tested
+    PH_PARTITION = 4,  // X_X partition on descent; count = X_X rows moved
+    PH_DONATE = 5,     // worker-list checks and donations; count = donations
+    PH_IDLE = 6,       // waiting in the worker list; count = subtrees received
+    kNumPhases = 8
+};
+
 // Per-launch traversal outputs (device pointers).
 struct DevOut {
     unsigned long long *count;   // [G]
@@ -123,6 +142,8 @@ struct DevOut {
     unsigned long long *root_hash;
     unsigned long long *root_nodes;
     int *status;
+    unsigned long long *phase_cycles;  // [kNumPhases]
+    unsigned long long *phase_counts;  // [kNumPhases]
 };
 
 // Host-side launch of one width class of the traversal (mce_traverse*.cu).
@@ -144,6 +165,7 @@ struct ClassArgs {
     int32_t worker_list;
     int32_t donate_min_p;
     int32_t root_chunk;     // roots claimed per atomic
+    int32_t stats;          // 1: collect per-phase cycle counters
     uint64_t timeout_ns;
     // scratch (device), sized by the host for groups = blocks * warps_per_block / gw
     uint32_t *arena;        // per-group: stack, X rows, X index lists, (A if a_global)
@@ -156,14 +178,6 @@ struct ClassArgs {
 };
 
 enum CtlSlot { CTL_NEXT_ROOT = 0, CTL_ACTIVE = 1, CTL_IDLE = 2, CTL_NCTL = 8 };
-
-// Number of warps per block and per group, and shared memory, for a width class.
-ClassLaunch plan_class(int wp, int rows_cap, int sm_count, int max_smem_optin, int requested_blocks);
-size_t class_arena_words(const ClassLaunch &L, int rows_cap, int x_cap);
-cudaError_t launch_class(const ClassLaunch &L, const DevGraph &g, const DevOut &o, const ClassArgs &a,
-                         cudaStream_t s);
-cudaError_t launch_trivial(const DevGraph &g, const DevOut &o, const int32_t *roots, int32_t n_roots,
-                           cudaStream_t s);
 
 // Width classes: padded words per row. A row stride w with w/4 odd keeps
 // 128-bit shared loads of 8 consecutive lanes (one phase) on distinct banks.

@@ -334,18 +334,22 @@ __global__ void k_set_total(int32_t *out, int64_t n, const int32_t *in) {
 cudaError_t exclusive_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s) {
     if (n <= 0) {
         k_set_total<<<1, 1, 0, s>>>(out, 0, in);
+        count_launch();
         return cudaGetLastError();
     }
     const int64_t tiles = (n + kScanTile - 1) / kScanTile;
     int32_t *sums = tmp;
     int32_t *offs = tmp + tiles;
     k_scan_tiles<<<(unsigned)tiles, kScanThreads, 0, s>>>(in, out, sums, n);
+    count_launch();
     if (tiles > 1) {
         cudaError_t e = exclusive_scan(sums, offs, tiles, tmp + 2 * tiles + 1, s);
         if (e != cudaSuccess) return e;
         k_scan_add<<<(unsigned)tiles, kScanThreads, 0, s>>>(out, offs, n);
+        count_launch();
     }
     k_set_total<<<1, 1, 0, s>>>(out, n, in);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -511,8 +515,10 @@ cudaError_t launch_validate(int n, const int32_t *rp, const int32_t *col, int64_
                             cudaStream_t s, bool cols) {
     if (!cols) {
         k_check_rowptr<<<grid_for((int64_t)n + 1, 256), 256, 0, s>>>(n, rp, m2, status);
+        count_launch();
     } else if (n > 0) {
         k_check_cols<<<grid_for((int64_t)n * 32, 256, 65536), 256, 0, s>>>(n, rp, col, status);
+        count_launch();
     }
     return cudaGetLastError();
 }
@@ -529,6 +535,7 @@ cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &
                     (void *)&b.rank,   (void *)&b.core,   (void *)&b.order,   (void *)&b.remA,
                     (void *)&b.remB,   (void *)&b.SA,     (void *)&b.SB,      (void *)&b.bitmap,
                     (void *)&b.blocksums, (void *)&b.ctl, (void *)&b.status, (void *)&timeout_ns};
+    count_launch();
     return cudaLaunchCooperativeKernel((void *)k_peel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
 }
 
@@ -549,6 +556,7 @@ __global__ void k_peel_init(PeelCtl *ctl, int n) {
 
 cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s) {
     k_peel_init<<<1, 1, 0, s>>>(ctl, n);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -563,13 +571,17 @@ cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const in
     }
     const unsigned gw = grid_for((int64_t)n * 32, 256, 65536);
     k_count_split<<<gw, 256, 0, s>>>(n, rp, col, order, rank, outdeg, indeg);
+    count_launch();
     cudaError_t e = exclusive_scan(outdeg, out_ptr, n, scan_tmp, s);
     if (e != cudaSuccess) return e;
     e = exclusive_scan(indeg, in_ptr, n, scan_tmp, s);
     if (e != cudaSuccess) return e;
     k_fill_split<<<gw, 256, 0, s>>>(n, rp, col, order, rank, out_ptr, out_col, in_ptr, in_col);
+    count_launch();
     k_sort_rows_warp<<<gw, 256, 0, s>>>(n, out_ptr, out_col);
+    count_launch();
     k_sort_rows_block<<<grid_for(n, 1, 4096), 1024, 0, s>>>(n, out_ptr, out_col);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -577,6 +589,7 @@ cudaError_t launch_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t
                            const int32_t *graph_ptr, int G, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_mix_gid<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, order, mixid, gid, graph_ptr, G);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -584,6 +597,7 @@ cudaError_t launch_classify(int n, const int32_t *outdeg, const int32_t *indeg, 
                             int *cls_x, int *cls_count, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_class_stats<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, outdeg, indeg, cls_rows, cls_x, cls_count);
+    count_launch();
     return cudaGetLastError();
 }
 
@@ -591,9 +605,11 @@ cudaError_t launch_class_list(int n, const int32_t *outdeg, int c, int32_t *flag
                               int32_t *scan_tmp, int32_t *out, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_class_flags<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, outdeg, c, flags);
+    count_launch();
     cudaError_t e = exclusive_scan(flags, pos, n, scan_tmp, s);
     if (e != cudaSuccess) return e;
     k_scatter_flagged<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, flags, pos, out);
+    count_launch();
     return cudaGetLastError();
 }
 

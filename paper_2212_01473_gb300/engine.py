@@ -42,7 +42,7 @@ class mce_allocator(ctypes.Structure):
 class mce_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("pivot", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("worker_list", ctypes.c_int32), ("donate_min_p", ctypes.c_int32),
-                ("blocks", ctypes.c_int32), ("tune", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("tune", ctypes.c_int32), ("stats", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int64), ("root_count", ctypes.c_void_p),
                 ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
                 ("root_priority", ctypes.c_void_p)]
@@ -54,6 +54,18 @@ class mce_result(ctypes.Structure):
                 ("donations", ctypes.c_uint64), ("ms_prep", ctypes.c_double),
                 ("ms_traverse", ctypes.c_double)]
 
+
+class mce_stats(ctypes.Structure):
+    _fields_ = [("struct_size", ctypes.c_int32), ("n_classes", ctypes.c_int32),
+                ("class_wp", ctypes.c_int32 * 16), ("class_roots", ctypes.c_int32 * 16),
+                ("class_rows", ctypes.c_int32 * 16), ("class_blocks", ctypes.c_int32 * 16),
+                ("class_groups", ctypes.c_int32 * 16), ("class_group_warps", ctypes.c_int32 * 16),
+                ("class_ms", ctypes.c_double * 16), ("kernel_launches", ctypes.c_uint64),
+                ("peel_rounds", ctypes.c_int64), ("phase_cycles", ctypes.c_uint64 * 8),
+                ("phase_counts", ctypes.c_uint64 * 8)]
+
+
+PHASES = ["setup", "pivot", "branch", "leaf", "partition", "donate", "idle", "unused"]
 
 _lib = None
 
@@ -79,6 +91,7 @@ def library():
                                       ctypes.POINTER(mce_result)]
         lib.mce_graph_info.argtypes = [vp, i32p, ctypes.POINTER(ctypes.c_int64), i32p, i32p, i32p]
         lib.mce_get_order.argtypes = [vp, i32p, i32p, i32p]
+        lib.mce_get_stats.argtypes = [vp, ctypes.POINTER(mce_stats)]
         lib.mce_destroy.argtypes = [vp]
         lib.mce_destroy.restype = None
         lib.mce_last_error.argtypes = []
@@ -267,6 +280,23 @@ def mce_get_order(h: Handle):
     _check(library().mce_get_order(h.ptr, core.ctypes.data_as(P), rank.ctypes.data_as(P),
                                    outd.ctypes.data_as(P)))
     return core[:n], rank[:n], outd[:n]
+
+
+def mce_get_stats(h: Handle) -> dict:
+    """Launch facts (per width class) and optional phase counters of the last run."""
+    st = mce_stats()
+    st.struct_size = ctypes.sizeof(mce_stats)
+    _check(library().mce_get_stats(h.ptr, ctypes.byref(st)))
+    k = st.n_classes
+    return {
+        "classes": [{"wp": st.class_wp[i], "roots": st.class_roots[i], "rows": st.class_rows[i],
+                     "blocks": st.class_blocks[i], "groups": st.class_groups[i],
+                     "group_warps": st.class_group_warps[i], "ms": st.class_ms[i]} for i in range(k)],
+        "kernel_launches": int(st.kernel_launches),
+        "peel_rounds": int(st.peel_rounds),
+        "phase_cycles": {PHASES[i]: int(st.phase_cycles[i]) for i in range(7)},
+        "phase_counts": {PHASES[i]: int(st.phase_counts[i]) for i in range(7)},
+    }
 
 
 def mce_destroy(h: Handle):
