@@ -85,7 +85,7 @@ typedef struct {
     int32_t pivot;         /* MCE_PIVOT_* */
     int32_t order;         /* MCE_ORDER_* */
     int32_t worker_list;   /* 1 = idle workers receive donated subtrees (Sec. III-C), 0 = off */
-    int32_t donate_min_p;  /* donate a branch only if its |P| >= this (Sec. III-C: 10) */
+    int32_t donate_min_p;  /* donate a branch only if its |P| >= this (Sec. III-C uses 10; default 20) */
     int32_t blocks;        /* persistent blocks per width class; 0 = all that fit on the GPU */
     int32_t tune;          /* reserved, set 0 */
     int32_t stats;         /* 1 = collect per-phase SM cycle counters (see mce_stats); slows the run */
@@ -98,6 +98,12 @@ typedef struct {
     uint64_t *root_nodes;
     /* DEVICE float[n] by input vertex id; read when order == MCE_ORDER_PRIORITY */
     const float *root_priority;
+    /* optional DEVICE int32[n_roots] of distinct input vertex ids: only these
+     * vertices' first-level subtrees (Algorithm 3) are enumerated, and every
+     * result (count, hash, histogram, per-root arrays) covers only them.
+     * NULL = all vertices. An id outside [0, n) fails with MCE_EINVAL. */
+    const int32_t *roots;
+    int64_t n_roots;
 } mce_opts;
 
 typedef struct {
@@ -112,7 +118,7 @@ typedef struct {
 } mce_result;
 
 /* Fill *opts with defaults (IP/IPX auto, plain order, worker list on,
- * donate_min_p 10, timeout 60 s). */
+ * donate_min_p 20, timeout 60 s). */
 void mce_default_opts(mce_opts *opts);
 
 /*

@@ -220,7 +220,7 @@ extern "C" void mce_default_opts(mce_opts *o) {
     o->pivot = MCE_PIVOT_AUTO;
     o->order = MCE_ORDER_PLAIN;
     o->worker_list = 1;
-    o->donate_min_p = 10;
+    o->donate_min_p = 20;
     o->timeout_ms = 60000;
 }
 
@@ -475,6 +475,15 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     mce_stats st{};
     std::vector<cudaEvent_t> cev;
     uint64_t launches = 0;
+    const uint64_t launch_base = launch_counter();
+    // roots to enumerate per width class (all, or the subset opts.roots selects)
+    const int32_t *lists[kNumClasses + 1];
+    int32_t counts[kNumClasses + 1];
+    for (int c = 0; c <= kNumClasses; c++) {
+        lists[c] = g->class_roots[c];
+        counts[c] = g->class_count[c];
+    }
+    std::vector<void *> run_tmp;
     unsigned long long *obuf = (unsigned long long *)dalloc(g, out_words64 * 8 + 64);
     if (!obuf) return fail(MCE_ENOMEM, "device allocation of outputs failed");
     CK(cudaMemsetAsync(obuf, 0, out_words64 * 8 + 64, g->stream));
@@ -506,9 +515,38 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     dout.root_hash = (unsigned long long *)opts.root_hash;
     dout.root_nodes = (unsigned long long *)opts.root_nodes;
     st.struct_size = (int32_t)sizeof(mce_stats);
+    if (opts.roots && opts.n_roots < 0) { rc = fail(MCE_EINVAL, "opts.n_roots < 0"); goto cleanup; }
+    if (opts.roots && g->n > 0) {
+        int maxc = 1;
+        for (int c = 0; c <= kNumClasses; c++) maxc = std::max(maxc, g->class_count[c]);
+        int32_t *mask = (int32_t *)dalloc(g, (size_t)g->n * 4);
+        int32_t *flags = (int32_t *)dalloc(g, (size_t)maxc * 4);
+        int32_t *pos = (int32_t *)dalloc(g, ((size_t)maxc + 1) * 4);
+        int32_t *stmp = (int32_t *)dalloc(g, (size_t)scan_tmp_words(maxc + 1) * 4);
+        for (void *q : {(void *)mask, (void *)flags, (void *)pos, (void *)stmp}) run_tmp.push_back(q);
+        if (!mask || !flags || !pos || !stmp) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+        CK(cudaMemsetAsync(mask, 0, (size_t)g->n * 4, g->stream));
+        CK(launch_mark_roots(opts.roots, opts.n_roots, g->rank, g->n, mask, dout.status, g->stream));
+        int hst = 0;
+        CK(cudaMemcpyAsync(&hst, dout.status, 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        if (hst) { rc = fail(MCE_EINVAL, "opts.roots holds an id outside [0, n)"); goto cleanup; }
+        for (int c = 0; c <= kNumClasses; c++) {
+            if (counts[c] == 0) continue;
+            int32_t *out = (int32_t *)dalloc(g, (size_t)counts[c] * 4);
+            run_tmp.push_back(out);
+            if (!out) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+            CK(launch_subset(lists[c], counts[c], mask, flags, pos, stmp, out, g->stream));
+            int kept = 0;
+            CK(cudaMemcpyAsync(&kept, pos + counts[c], 4, cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaStreamSynchronize(g->stream));
+            lists[c] = out;
+            counts[c] = kept;
+        }
+    }
     CK(cudaEventRecord(ev0, g->stream));
-    if (g->class_count[kNumClasses] > 0) {
-        const int nr = g->class_count[kNumClasses];
+    if (counts[kNumClasses] > 0) {
+        const int nr = counts[kNumClasses];
         const unsigned nb = (unsigned)std::min<int64_t>(4096, ((int64_t)nr + 255) / 256);
         cudaEvent_t a0, a1;
         CK(cudaEventCreate(&a0));
@@ -516,7 +554,7 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         CK(cudaEventCreate(&a1));
         cev.push_back(a1);
         CK(cudaEventRecord(a0, g->stream));
-        k_trivial_roots<<<nb, 256, 0, g->stream>>>(dg, dout, g->class_roots[kNumClasses], nr);
+        k_trivial_roots<<<nb, 256, 0, g->stream>>>(dg, dout, lists[kNumClasses], nr);
         count_launch();
         CK(cudaGetLastError());
         CK(cudaEventRecord(a1, g->stream));
@@ -528,7 +566,7 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     }
     // heaviest width classes first
     for (int c = kNumClasses - 1; c >= 0; c--) {
-        if (g->class_count[c] == 0) continue;
+        if (counts[c] == 0) continue;
         const int rows = g->class_rows[c];
         ClassLaunch L{};
         CK(plan_class_wp(class_wp(c), rows, g->sm_count, g->smem_optin, opts.blocks, g->gid == nullptr, &L));
@@ -536,12 +574,13 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         const size_t aw = arena_words(L.wp, rows, g->class_x[c], L.a_global, stack_in_smem(L.wp));
         const int mail_words = 4 + 3 * L.wp;
         const size_t ctl_words = CTL_NCTL, idle_words = ((size_t)groups + 31) / 32;
-        const size_t total_words = aw * groups + ctl_words + idle_words + groups + (size_t)groups * mail_words + 64;
+        const size_t flag_words = (size_t)groups * kMailFlagStride;
+        const size_t total_words = aw * groups + ctl_words + idle_words + flag_words + (size_t)groups * mail_words + 64;
         if ((rc = grow_scratch(g, total_words * 4)) != MCE_OK) goto cleanup;
         uint32_t *sw = (uint32_t *)g->scratch;
         ClassArgs a{};
-        a.roots = g->class_roots[c];
-        a.n_roots = g->class_count[c];
+        a.roots = lists[c];
+        a.n_roots = counts[c];
         a.rows_cap = rows;
         a.x_cap = g->class_x[c];
         a.pivot_ipx = 0;
@@ -555,9 +594,9 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         a.ctl = (int *)(sw + aw * groups);
         a.idle_bits = (unsigned *)(a.ctl + ctl_words);
         a.mail_flag = (int *)(a.idle_bits + idle_words);
-        a.mail = (uint32_t *)(a.mail_flag + groups);
+        a.mail = (uint32_t *)(a.mail_flag + flag_words);
         a.mail_words = mail_words;
-        CK(cudaMemsetAsync(a.ctl, 0, (ctl_words + idle_words + groups) * 4, g->stream));
+        CK(cudaMemsetAsync(a.ctl, 0, (ctl_words + idle_words + flag_words) * 4, g->stream));
         int hctl[CTL_NCTL] = {0};
         hctl[CTL_ACTIVE] = groups;
         CK(cudaMemcpyAsync(a.ctl, hctl, sizeof hctl, cudaMemcpyHostToDevice, g->stream));
@@ -572,7 +611,7 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         launches++;
         const int k = st.n_classes++;
         st.class_wp[k] = L.wp;
-        st.class_roots[k] = g->class_count[c];
+        st.class_roots[k] = counts[c];
         st.class_rows[k] = rows;
         st.class_blocks[k] = L.blocks;
         st.class_groups[k] = groups;
@@ -591,7 +630,7 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         CK(cudaEventElapsedTime(&cms, cev[2 * k], cev[2 * k + 1]));
         st.class_ms[k] = cms;
     }
-    st.kernel_launches = g->create_launches + launches;
+    st.kernel_launches = g->create_launches + (launch_counter() - launch_base) + launches;
     st.peel_rounds = g->peel_rounds;
     g->last = st;
     if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms", (long long)opts.timeout_ms); goto cleanup; }
@@ -636,6 +675,7 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
 cleanup:
     if (g->stream) cudaStreamSynchronize(g->stream);
     for (cudaEvent_t e : cev) cudaEventDestroy(e);
+    for (void *q : run_tmp) dfree(g, q);
     dfree(g, obuf);
     if (ev0) cudaEventDestroy(ev0);
     if (ev1) cudaEventDestroy(ev1);

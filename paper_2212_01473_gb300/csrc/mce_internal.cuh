@@ -172,12 +172,15 @@ struct ClassArgs {
     size_t arena_words_per_group;
     int *ctl;               // [8]: root counter, active, idle_count, ...
     unsigned *idle_bits;    // [ceil(groups/32)]
-    int *mail_flag;         // [groups]
+    int *mail_flag;         // [groups * kMailFlagStride]
     uint32_t *mail;         // [groups * mail_words]
     int32_t mail_words;
 };
 
-enum CtlSlot { CTL_NEXT_ROOT = 0, CTL_ACTIVE = 1, CTL_IDLE = 2, CTL_NCTL = 8 };
+// Control words of a traversal launch, each on its own 128-byte line so that
+// polling one does not slow atomics on another.
+enum CtlSlot { CTL_NEXT_ROOT = 0, CTL_ACTIVE = 32, CTL_IDLE = 64, CTL_NCTL = 96 };
+constexpr int kMailFlagStride = 8;  // ints between two groups' mail flags (32 bytes)
 
 // Width classes: padded words per row. A row stride w with w/4 odd keeps
 // 128-bit shared loads of 8 consecutive lanes (one phase) on distinct banks.

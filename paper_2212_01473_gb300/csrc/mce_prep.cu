@@ -502,6 +502,29 @@ __global__ void k_scatter_flagged(int n, const int32_t *flags, const int32_t *po
         if (flags[r]) out[pos[r]] = (int32_t)r;
 }
 
+__global__ void k_mark_roots(const int32_t *ids, int64_t k, const int32_t *rank, int n, int32_t *mask,
+                             int *status) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t v = ids[i];
+        if (v < 0 || v >= n) {
+            atomicOr(status, ST_BADGRAPH);
+            continue;
+        }
+        mask[rank[v]] = 1;
+    }
+}
+
+__global__ void k_subset_flags(const int32_t *list, int cnt, const int32_t *mask, int32_t *flags) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        flags[i] = mask[list[i]] != 0;
+}
+
+__global__ void k_gather_flagged(const int32_t *list, int cnt, const int32_t *flags, const int32_t *pos,
+                                 int32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        if (flags[i]) out[pos[i]] = list[i];
+}
+
 // ------------------------------------------------------------ host side
 
 static unsigned grid_for(int64_t work, int per_block, int cap = 1 << 20) {
@@ -597,6 +620,26 @@ cudaError_t launch_classify(int n, const int32_t *outdeg, const int32_t *indeg, 
                             int *cls_x, int *cls_count, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     k_class_stats<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, outdeg, indeg, cls_rows, cls_x, cls_count);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_mark_roots(const int32_t *ids, int64_t k, const int32_t *rank, int n, int32_t *mask,
+                              int *status, cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    k_mark_roots<<<grid_for(k, 256, 65536), 256, 0, s>>>(ids, k, rank, n, mask, status);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_subset(const int32_t *list, int cnt, const int32_t *mask, int32_t *flags, int32_t *pos,
+                          int32_t *scan_tmp, int32_t *out, cudaStream_t s) {
+    if (cnt <= 0) return cudaSuccess;
+    k_subset_flags<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, mask, flags);
+    count_launch();
+    cudaError_t e = exclusive_scan(flags, pos, cnt, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    k_gather_flagged<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, flags, pos, out);
     count_launch();
     return cudaGetLastError();
 }

@@ -36,4 +36,10 @@ cudaError_t launch_classify(int n, const int32_t *outdeg, const int32_t *indeg, 
 cudaError_t launch_class_list(int n, const int32_t *outdeg, int c, int32_t *flags, int32_t *pos,
                               int32_t *scan_tmp, int32_t *out, cudaStream_t s);
 
+// keep the entries of list[0..cnt) (ranks) whose mask[rank] is set, in order
+cudaError_t launch_mark_roots(const int32_t *ids, int64_t k, const int32_t *rank, int n, int32_t *mask,
+                              int *status, cudaStream_t s);
+cudaError_t launch_subset(const int32_t *list, int cnt, const int32_t *mask, int32_t *flags, int32_t *pos,
+                          int32_t *scan_tmp, int32_t *out, cudaStream_t s);
+
 }  // namespace mce

@@ -78,7 +78,7 @@ __host__ __device__ inline GrpSmem grp_smem_layout(int wp, int gw, int rows, boo
     if (!a_global) off += (size_t)rows * wp * 4;
     off = align_up(off, 16);
     L.cur = off;
-    off += (size_t)wp * 4;
+    off += (size_t)wp * 2 * 4;  // P, then P u X_P, of the node being entered
     off = align_up(off, 16);
     L.p0 = off;
     off += (size_t)rows * 4;
@@ -312,21 +312,25 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     __threadfence();
                     atomicSub(&C.ctl[CTL_ACTIVE], 1);
                     unsigned ns = 64;
-                    for (;;) {
-                        if (ld_acquire(&C.mail_flag[gg])) {
-                            C.mail_flag[gg] = 0;
+                    int* const flag = &C.mail_flag[(size_t)gg * kMailFlagStride];
+                    for (unsigned spin = 1;; spin++) {
+                        if (ld_acquire(flag)) {
+                            *flag = 0;
                             mail = 1;
                             r = (int)C.mail[(size_t)gg * C.mail_words + 0];
                             break;
                         }
-                        if (ld_acquire(&C.ctl[CTL_ACTIVE]) == 0) break;
-                        if (ld_relaxed(O.status) & ST_TIMEOUT) break;
-                        if (globaltimer_ns() > deadline) {
-                            atomicOr(O.status, ST_TIMEOUT);
-                            break;
+                        // the shared termination word and the clock are read less often
+                        if ((spin & 7u) == 0) {
+                            if (ld_acquire(&C.ctl[CTL_ACTIVE]) == 0) break;
+                            if (ld_relaxed(O.status) & ST_TIMEOUT) break;
+                            if (globaltimer_ns() > deadline) {
+                                atomicOr(O.status, ST_TIMEOUT);
+                                break;
+                            }
                         }
                         __nanosleep(ns);
-                        if (ns < 2048) ns <<= 1;
+                        if (ns < 1024) ns <<= 1;
                     }
                     pc.stop(PH_IDLE);
                     pc.count(PH_IDLE, mail);
@@ -448,49 +452,37 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             g.sync();
 
             // -------------------------------------------- initial node
-            uint32_t *lv0 = stk + (size_t)l0 * LS;
+            // The current node's P, X_P and branch set live in registers, one
+            // 32-bit word per thread (thread gl owns word gl < WP); the stack
+            // holds the ancestors (pushed on descent, reloaded on backtrack).
+            const bool own = g.gl < WP;
+            uint32_t p = 0u, xp = 0u, b = 0u;
+            int lpx = nx, npend = 0;
+            uint64_t S = G.mixid[r];
             if (!have_mail) {
-                for (int w = g.gl; w < WP; w += GT) {
-                    uint32_t full = 0;
-                    int lo = w * 32;
-                    if (lo < n0) full = (n0 - lo >= 32) ? 0xffffffffu : ((1u << (n0 - lo)) - 1u);
-                    lv0[Lvl<WP>::P + w] = full;
-                    lv0[Lvl<WP>::XP + w] = 0u;
-                }
-                if (g.gl == 0) {
-                    lv0[Lvl<WP>::LPX] = (uint32_t)nx;
-                    lv0[Lvl<WP>::NPEND] = 0u;
-                    uint64_t S = G.mixid[r];
-                    lv0[Lvl<WP>::SLO] = (uint32_t)S;
-                    lv0[Lvl<WP>::SHI] = (uint32_t)(S >> 32);
+                if (own) {
+                    const int lo = g.gl * 32;
+                    if (lo < n0) p = (n0 - lo >= 32) ? 0xffffffffu : ((1u << (n0 - lo)) - 1u);
                 }
             } else {
-                // receiver: P', X_P' and the path R' come from the mail; the
+                // P', X_P' and the path R' below the root come from the mail; the
                 // X_X rows in the arena are exactly the donor's survivors
                 const uint32_t *mR = mb + 4, *mP = mb + 4 + WP, *mX = mb + 4 + 2 * WP;
-                const int keep_n = nx;
-                for (int w = g.gl; w < WP; w += GT) {
-                    lv0[Lvl<WP>::P + w] = mP[w];
-                    lv0[Lvl<WP>::XP + w] = mX[w];
+                if (own) {
+                    p = mP[g.gl];
+                    xp = mX[g.gl];
                 }
-                if (g.gl == 0) {
-                    uint64_t S = G.mixid[r];
-                    int lv = 0;
-                    for (int w = 0; w < W; w++) {
-                        uint32_t bits = mR[w];
-                        while (bits) {
-                            int b = __ffs(bits) - 1;
-                            bits &= bits - 1;
-                            S += G.mixid[p0[w * 32 + b]];
-                            // record the path R' so deeper donations can rebuild it
-                            stk[(size_t)lv * LS + Lvl<WP>::VSEL] = (uint32_t)(w * 32 + b);
-                            lv++;
-                        }
+                int lv = 0;
+                for (int w = 0; w < W; w++) {
+                    uint32_t bits = mR[w];
+                    while (bits) {
+                        const int bb = __ffs(bits) - 1;
+                        bits &= bits - 1;
+                        S += G.mixid[p0[w * 32 + bb]];
+                        // the path, so that deeper donations can rebuild R
+                        if (g.gl == 0) stk[(size_t)lv * LS + Lvl<WP>::VSEL] = (uint32_t)(w * 32 + bb);
+                        lv++;
                     }
-                    lv0[Lvl<WP>::LPX] = (uint32_t)keep_n;
-                    lv0[Lvl<WP>::NPEND] = 0u;
-                    lv0[Lvl<WP>::SLO] = (uint32_t)S;
-                    lv0[Lvl<WP>::SHI] = (uint32_t)(S >> 32);
                 }
             }
             __threadfence_block();
@@ -498,6 +490,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             pc.stop(PH_SETUP);
 
             // ------------------------------------------------- DFS (Algorithm 2)
+            uint32_t *curP = cur, *curPX = cur + WP;
             int l = l0;
             bool enter = true;
             bool timed_out = false;
@@ -509,31 +502,30 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         break;
                     }
                 }
-                uint32_t *lv = stk + (size_t)l * LS;
                 if (enter) {
                     t_nodes++;
-                    // copy P to cur; candidate list P u X_P in ascending index
-                    for (int w = g.gl; w < WP; w += GT) cur[w] = lv[Lvl<WP>::P + w];
+                    if (own) {
+                        curP[g.gl] = p;
+                        curPX[g.gl] = p | xp;
+                    }
+                    const int np = grp_sum(g, red, __popc(p));
+                    const int xany = grp_or(g, red, xp != 0u);
+                    g.sync();
+                    // candidate list P u X_P in ascending index
                     if (g.warp == 0) {
-                        int nc = 0, np = 0;
-                        uint32_t xany = 0;
+                        int nc = 0;
                         for (int w = 0; w < W; w++) {
-                            const uint32_t pw = lv[Lvl<WP>::P + w], xw = lv[Lvl<WP>::XP + w];
-                            const uint32_t bits = pw | xw;
+                            const uint32_t bits = curPX[w];
                             if ((bits >> g.lane) & 1u)
                                 cand[nc + __popc(bits & ((1u << g.lane) - 1u))] = w * 32 + g.lane;
                             nc += __popc(bits);
-                            np += __popc(pw);
-                            xany |= xw;
                         }
-                        if (g.lane == 0) {
-                            misc[2] = nc;
-                            misc[6] = xany ? np : np - 1;  // best score any candidate can reach
-                        }
+                        if (g.lane == 0) misc[2] = nc;
                     }
                     g.sync();
                     const int nc = misc[2];
-                    const unsigned bound = (unsigned)misc[6];
+                    // best score any candidate can reach: |P| for an excluded vertex, |P|-1 in P
+                    const unsigned bound = (unsigned)(xany ? np : np - 1);
                     unsigned best = 0;
                     int scanned = 0;
                     for (int j0 = 0; j0 < nc; j0 += GT) {
@@ -542,85 +534,62 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         if (j < nc) {
                             const int c = cand[j];
                             const uint32_t *arow = Arow + (size_t)c * WP;
-                            int s = 0;
+                            int sc = 0;
                             if (WP % 4 == 0) {
                                 const uint4 *a4 = reinterpret_cast<const uint4 *>(arow);
-                                const uint4 *p4 = reinterpret_cast<const uint4 *>(cur);
+                                const uint4 *p4 = reinterpret_cast<const uint4 *>(curP);
                                 for (int qq = 0; qq < (W + 3) / 4; qq++) {
-                                    uint4 a = a4[qq], p = p4[qq];
-                                    s += __popc(a.x & p.x) + __popc(a.y & p.y) + __popc(a.z & p.z) +
-                                         __popc(a.w & p.w);
+                                    const uint4 a = a4[qq], pw = p4[qq];
+                                    sc += __popc(a.x & pw.x) + __popc(a.y & pw.y) + __popc(a.z & pw.z) +
+                                          __popc(a.w & pw.w);
                                 }
                             } else {
-                                for (int w = 0; w < W; w++) s += __popc(arow[w] & cur[w]);
+                                for (int w = 0; w < W; w++) sc += __popc(arow[w] & curP[w]);
                             }
-                            key = ((unsigned)s << 16) | (unsigned)(0xffff - c);
+                            key = ((unsigned)sc << 16) | (unsigned)(0xffff - c);
                         }
                         best = max(best, grp_max(g, red, key));
                         scanned = min(nc, j0 + GT);
                         if ((best >> 16) >= bound) break;
                     }
                     const int piv = 0xffff - (int)(best & 0xffffu);
-                    for (int w = g.gl; w < WP; w += GT)
-                        lv[Lvl<WP>::B + w] = cur[w] & ~Arow[(size_t)piv * WP + w];
-                    __threadfence_block();
-                    g.sync();
+                    b = own ? (p & ~Arow[(size_t)piv * WP + g.gl]) : 0u;
                     enter = false;
                     pc.stop(PH_PIVOT);
                     pc.count(PH_PIVOT, (unsigned long long)scanned);
                 }
-                // --------------------------------------- next branch at level l
-                if (g.warp == 0) {
-                    int v = -1;
-                    for (int w0 = 0; w0 < W; w0 += 32) {
-                        int w = w0 + g.lane;
-                        uint32_t bits = (w < W) ? lv[Lvl<WP>::B + w] : 0u;
-                        unsigned nz = __ballot_sync(0xffffffffu, bits != 0u);
-                        if (nz) {
-                            int src = __ffs(nz) - 1;
-                            uint32_t bw = __shfl_sync(0xffffffffu, bits, src);
-                            v = (w0 + src) * 32 + (__ffs(bw) - 1);
-                            break;
-                        }
-                    }
-                    if (g.lane == 0) misc[3] = v;
-                }
-                g.sync();
-                const int v = misc[3];
-                g.sync();
-                if (v < 0) {
+                // --------------------------------------- next branch: lowest bit of B
+                const unsigned bkey = b ? ~(unsigned)(g.gl * 32 + __ffs(b) - 1) : 0u;
+                const unsigned bsel = grp_max(g, red, bkey);
+                if (bsel == 0u) {
                     // all branches done: backtrack
                     pc.stop(PH_BRANCH);
                     if (l == l0) break;
                     l--;
+                    const uint32_t *lv = stk + (size_t)l * LS;
+                    if (own) {
+                        p = lv[Lvl<WP>::P + g.gl];
+                        xp = lv[Lvl<WP>::XP + g.gl];
+                        b = lv[Lvl<WP>::B + g.gl];
+                    }
+                    lpx = (int)lv[Lvl<WP>::LPX];
+                    npend = (int)lv[Lvl<WP>::NPEND];
+                    S = (uint64_t)lv[Lvl<WP>::SLO] | ((uint64_t)lv[Lvl<WP>::SHI] << 32);
                     continue;
                 }
+                const int v = (int)(~bsel);
                 const int vw = v >> 5;
                 const uint32_t vb = 1u << (v & 31);
-                // child sets P n N(v), X_P n N(v) (into level l+1), then P -= v, X_P += v
-                uint32_t *nv = lv + LS;
-                int pcnt = 0, xa = 0;
-                for (int w = g.gl; w < WP; w += GT) {
-                    uint32_t av = Arow[(size_t)v * WP + w];
-                    uint32_t cp = lv[Lvl<WP>::P + w] & av;
-                    uint32_t cx = lv[Lvl<WP>::XP + w] & av;
-                    nv[Lvl<WP>::P + w] = cp;
-                    nv[Lvl<WP>::XP + w] = cx;
-                    pcnt += __popc(cp);
-                    xa |= (cx != 0u);
+                // child sets P n N(v), X_P n N(v); then P -= v, X_P += v, B -= v
+                const uint32_t av = own ? Arow[(size_t)v * WP + g.gl] : 0u;
+                const uint32_t cp = p & av, cx = xp & av;
+                if (g.gl == vw) {
+                    b &= ~vb;
+                    p &= ~vb;
+                    xp |= vb;
                 }
-                pcnt = grp_sum(g, red, pcnt);
-                xa = grp_or(g, red, xa);
-                if (g.gl == 0) {
-                    lv[Lvl<WP>::B + vw] &= ~vb;
-                    lv[Lvl<WP>::P + vw] &= ~vb;
-                    lv[Lvl<WP>::XP + vw] |= vb;
-                    lv[Lvl<WP>::VSEL] = (uint32_t)v;
-                }
-                __threadfence_block();
-                g.sync();
-                const int lpx = (int)lv[Lvl<WP>::LPX];
-                const uint64_t S = (uint64_t)lv[Lvl<WP>::SLO] | ((uint64_t)lv[Lvl<WP>::SHI] << 32);
+                const int pcnt = grp_sum(g, red, __popc(cp));
+                const int xa = grp_or(g, red, cx != 0u);
                 pc.stop(PH_BRANCH);
                 if (pcnt == 0) {
                     // the child is a leaf: R u {v} is maximal iff X_P' and X_X' are empty
@@ -628,7 +597,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     if (!xa) {
                         int found = 0, it = 0;
                         for (; it < lpx && !found; it += GT) {
-                            int idx = it + g.gl;
+                            const int idx = it + g.gl;
                             int hit = 0;
                             if (idx < lpx) hit = (xrows[(size_t)xidx[idx] * WP + vw] & vb) != 0u;
                             found = grp_or(g, red, hit);
@@ -646,135 +615,140 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     pc.stop(PH_LEAF);
                     continue;
                 }
+                const int others_here = grp_or(g, red, b != 0u);
                 // ------------------------------ donation (Sec. III-C)
-                if (C.worker_list && pcnt >= C.donate_min_p) {
-                    int others_here = 0;
-                    for (int w = g.gl; w < W; w += GT) others_here |= (lv[Lvl<WP>::B + w] != 0u);
-                    others_here = grp_or(g, red, others_here);
-                    const int npend = (int)lv[Lvl<WP>::NPEND];
-                    if (others_here && npend >= 1) {
-                        if (g.gl == 0) {
-                            int claimed = -1;
-                            if (ld_relaxed(&C.ctl[CTL_IDLE]) > 0) {
-                                const int nwords = (ngroups + 31) >> 5;
-                                for (int qd = 0; qd < nwords && claimed < 0; qd++) {
-                                    int wi = (gg / 32 + 1 + qd) % nwords;
-                                    unsigned bits = *((volatile unsigned *)&C.idle_bits[wi]);
-                                    while (bits) {
-                                        int b = __ffs(bits) - 1;
-                                        unsigned old = atomicAnd(&C.idle_bits[wi], ~(1u << b));
-                                        if (old & (1u << b)) {
-                                            claimed = wi * 32 + b;
-                                            break;
-                                        }
-                                        bits &= bits - 1;
+                if (C.worker_list && pcnt >= C.donate_min_p && others_here && npend >= 1) {
+                    if (g.gl == 0) {
+                        int claimed = -1;
+                        if (ld_relaxed(&C.ctl[CTL_IDLE]) > 0) {
+                            const int nwords = (ngroups + 31) >> 5;
+                            for (int qd = 0; qd < nwords && claimed < 0; qd++) {
+                                const int wi = (gg / 32 + 1 + qd) % nwords;
+                                unsigned bits = *((volatile unsigned *)&C.idle_bits[wi]);
+                                while (bits) {
+                                    const int bb = __ffs(bits) - 1;
+                                    const unsigned old = atomicAnd(&C.idle_bits[wi], ~(1u << bb));
+                                    if (old & (1u << bb)) {
+                                        claimed = wi * 32 + bb;
+                                        break;
                                     }
-                                }
-                                if (claimed >= 0) {
-                                    atomicSub(&C.ctl[CTL_IDLE], 1);
-                                    atomicAdd(&C.ctl[CTL_ACTIVE], 1);
+                                    bits &= bits - 1;
                                 }
                             }
-                            misc[4] = claimed;
+                            if (claimed >= 0) {
+                                atomicSub(&C.ctl[CTL_IDLE], 1);
+                                atomicAdd(&C.ctl[CTL_ACTIVE], 1);
+                            }
+                        }
+                        misc[4] = claimed;
+                    }
+                    g.sync();
+                    const int recv = misc[4];
+                    g.sync();
+                    if (recv >= 0) {
+                        // X_X of the child = rows of this level's prefix with bit v
+                        int out = 0;
+                        for (int it = 0; it < lpx; it += GT) {
+                            const int idx = it + g.gl;
+                            const bool valid = idx < lpx;
+                            const uint32_t e = valid ? xidx[idx] : 0u;
+                            const bool surv = valid && (xrows[(size_t)e * WP + vw] & vb) != 0u;
+                            int ts;
+                            const int ps = grp_prefix(g, red, surv, &ts);
+                            if (surv) xscr[out + ps] = e;
+                            out += ts;
+                        }
+                        __threadfence_block();
+                        g.sync();
+                        // push A and the surviving rows into the receiver's arena
+                        const ArenaPtrs ra = arena_at(C.arena + (size_t)recv * C.arena_words_per_group, WP,
+                                                      rows_cap, C.x_cap, stack_smem != 0);
+                        if (WP % 4 == 0) {
+                            const uint4 *src = reinterpret_cast<const uint4 *>(Arow);
+                            uint4 *dst = reinterpret_cast<uint4 *>(ra.A);
+                            for (int i = g.gl; i < n0 * WP / 4; i += GT) dst[i] = src[i];
+                        } else {
+                            for (int i = g.gl; i < n0 * WP; i += GT) ra.A[i] = Arow[i];
+                        }
+                        for (int i = g.gl; i < out * WP; i += GT) {
+                            const int k = i / WP, w = i - k * WP;
+                            ra.xrows[i] = xrows[(size_t)xscr[k] * WP + w];
+                        }
+                        for (int k = g.gl; k < out; k += GT) ra.xidx[k] = (uint32_t)k;
+                        uint32_t *m = C.mail + (size_t)recv * C.mail_words;
+                        if (own) {
+                            m[4 + g.gl] = 0u;
+                            m[4 + WP + g.gl] = cp;
+                            m[4 + 2 * WP + g.gl] = cx;
                         }
                         g.sync();
-                        const int recv = misc[4];
-                        g.sync();
-                        if (recv >= 0) {
-                            // X_X of the child = rows of the level-l prefix with bit v
-                            int out = 0;
-                            for (int it = 0; it < lpx; it += GT) {
-                                int idx = it + g.gl;
-                                bool valid = idx < lpx;
-                                uint32_t e = valid ? xidx[idx] : 0u;
-                                bool surv = valid && (xrows[(size_t)e * WP + vw] & vb) != 0u;
-                                int ts;
-                                int ps = grp_prefix(g, red, surv, &ts);
-                                if (surv) xscr[out + ps] = e;
-                                out += ts;
+                        if (g.gl == 0) {
+                            // R' = the path below the root at levels [0, l), plus v
+                            for (int qd = 0; qd < l; qd++) {
+                                const int u = (int)stk[(size_t)qd * LS + Lvl<WP>::VSEL];
+                                m[4 + (u >> 5)] |= 1u << (u & 31);
                             }
-                            __threadfence_block();
-                            g.sync();
-                            const ArenaPtrs ra = arena_at(C.arena + (size_t)recv * C.arena_words_per_group, WP,
-                                                          rows_cap, C.x_cap, stack_smem != 0);
-                            {
-                                const uint4 *src = reinterpret_cast<const uint4 *>(Arow);
-                                uint4 *dst = reinterpret_cast<uint4 *>(ra.A);
-                                if (WP % 4 == 0) {
-                                    for (int i = g.gl; i < n0 * WP / 4; i += GT) dst[i] = src[i];
-                                } else {
-                                    for (int i = g.gl; i < n0 * WP; i += GT) ra.A[i] = Arow[i];
-                                }
-                            }
-                            for (int i = g.gl; i < out * WP; i += GT) {
-                                const int k = i / WP, w = i - k * WP;
-                                ra.xrows[i] = xrows[(size_t)xscr[k] * WP + w];
-                            }
-                            for (int k = g.gl; k < out; k += GT) ra.xidx[k] = (uint32_t)k;
-                            uint32_t *m = C.mail + (size_t)recv * C.mail_words;
-                            for (int w = g.gl; w < WP; w += GT) {
-                                m[4 + w] = 0u;
-                                m[4 + WP + w] = nv[Lvl<WP>::P + w];
-                                m[4 + 2 * WP + w] = nv[Lvl<WP>::XP + w];
-                            }
-                            g.sync();
-                            if (g.gl == 0) {
-                                // R' = the path below the root at levels [0, l), plus v
-                                for (int qd = 0; qd < l; qd++) {
-                                    int u = (int)stk[(size_t)qd * LS + Lvl<WP>::VSEL];
-                                    m[4 + (u >> 5)] |= 1u << (u & 31);
-                                }
-                                m[4 + vw] |= vb;
-                                m[0] = (uint32_t)r;
-                                m[1] = (uint32_t)(l + 1);
-                                m[2] = (uint32_t)out;
-                            }
-                            __threadfence();
-                            g.sync();
-                            if (g.gl == 0) {
-                                st_release(&C.mail_flag[recv], 1);
-                                acc_don++;
-                            }
-                            g.sync();
-                            pc.stop(PH_DONATE);
-                            pc.count(PH_DONATE, 1);
-                            continue;
+                            m[4 + vw] |= vb;
+                            m[0] = (uint32_t)r;
+                            m[1] = (uint32_t)(l + 1);
+                            m[2] = (uint32_t)out;
                         }
+                        __threadfence();
+                        g.sync();
+                        if (g.gl == 0) {
+                            st_release(&C.mail_flag[(size_t)recv * kMailFlagStride], 1);
+                            acc_don++;
+                        }
+                        g.sync();
+                        pc.stop(PH_DONATE);
+                        pc.count(PH_DONATE, 1);
+                        continue;
                     }
                     pc.stop(PH_DONATE);
                 }
-                // ------------------------------ descend: partition X_X by v
+                // ------------------------------ descend: push this level, partition X_X by v
                 {
+                    uint32_t *lv = stk + (size_t)l * LS;
+                    if (own) {
+                        lv[Lvl<WP>::P + g.gl] = p;
+                        lv[Lvl<WP>::XP + g.gl] = xp;
+                        lv[Lvl<WP>::B + g.gl] = b;
+                    }
+                    if (g.gl == 0) {
+                        lv[Lvl<WP>::LPX] = (uint32_t)lpx;
+                        lv[Lvl<WP>::NPEND] = (uint32_t)npend;
+                        lv[Lvl<WP>::VSEL] = (uint32_t)v;
+                        lv[Lvl<WP>::SLO] = (uint32_t)S;
+                        lv[Lvl<WP>::SHI] = (uint32_t)(S >> 32);
+                    }
                     int out = 0, nout = 0;
                     for (int it = 0; it < lpx; it += GT) {
-                        int idx = it + g.gl;
-                        bool valid = idx < lpx;
-                        uint32_t e = valid ? xidx[idx] : 0u;
-                        bool surv = valid && (xrows[(size_t)e * WP + vw] & vb) != 0u;
+                        const int idx = it + g.gl;
+                        const bool valid = idx < lpx;
+                        const uint32_t e = valid ? xidx[idx] : 0u;
+                        const bool surv = valid && (xrows[(size_t)e * WP + vw] & vb) != 0u;
                         int ts, tn;
-                        int ps = grp_prefix(g, red, surv, &ts);
-                        int pn = grp_prefix(g, red, valid && !surv, &tn);
+                        const int ps = grp_prefix(g, red, surv, &ts);
+                        const int pn = grp_prefix(g, red, valid && !surv, &tn);
                         if (surv) xidx[out + ps] = e;
                         else if (valid) xscr[nout + pn] = e;
                         out += ts;
                         nout += tn;
                     }
-                    __threadfence_block();
-                    g.sync();
-                    for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
-                    if (g.gl == 0) {
-                        nv[Lvl<WP>::LPX] = (uint32_t)out;
-                        int others = 0;
-                        for (int w = 0; w < W; w++) others |= (lv[Lvl<WP>::B + w] != 0u);
-                        nv[Lvl<WP>::NPEND] = lv[Lvl<WP>::NPEND] + (others ? 1u : 0u);
-                        uint64_t S2 = S + G.mixid[p0[v]];
-                        nv[Lvl<WP>::SLO] = (uint32_t)S2;
-                        nv[Lvl<WP>::SHI] = (uint32_t)(S2 >> 32);
+                    if (nout > 0) {
+                        __threadfence_block();
+                        g.sync();
+                        for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
                     }
                     __threadfence_block();
                     g.sync();
                     pc.stop(PH_PARTITION);
                     pc.count(PH_PARTITION, (unsigned long long)lpx);
+                    p = cp;
+                    xp = cx;
+                    lpx = out;
+                    npend += others_here ? 1 : 0;
+                    S += G.mixid[p0[v]];
                 }
                 l++;
                 enter = true;

@@ -45,7 +45,8 @@ class mce_opts(ctypes.Structure):
                 ("blocks", ctypes.c_int32), ("tune", ctypes.c_int32), ("stats", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int64), ("root_count", ctypes.c_void_p),
                 ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
-                ("root_priority", ctypes.c_void_p)]
+                ("root_priority", ctypes.c_void_p), ("roots", ctypes.c_void_p),
+                ("n_roots", ctypes.c_int64)]
 
 
 class mce_result(ctypes.Structure):
@@ -305,14 +306,20 @@ def mce_destroy(h: Handle):
         h.ptr = ctypes.c_void_p()
 
 
-def enumerate_maximal_cliques(row_ptr, col, per_root: bool = False, **opt_fields):
+def enumerate_maximal_cliques(row_ptr, col, per_root: bool = False, roots=None, **opt_fields):
     """One-shot convenience: create, run, destroy. With per_root, also returns
-    per-vertex subtree (count, hash, nodes) as numpy uint64 arrays."""
+    per-vertex subtree (count, hash, nodes) as numpy uint64 arrays. `roots`
+    (input vertex ids) restricts the enumeration to those first-level subtrees."""
     import torch
     h = mce_create(row_ptr, col)
     try:
         opts = mce_default_opts(**opt_fields)
         keep = []
+        if roots is not None:
+            rt = torch.as_tensor(np.ascontiguousarray(roots, dtype=np.int32)).cuda()
+            keep_roots = rt
+            opts.roots = rt.data_ptr() if len(rt) else torch.zeros(1, dtype=torch.int32, device="cuda").data_ptr()
+            opts.n_roots = len(rt)
         if per_root:
             n = max(h.n, 1)
             for name in ("root_count", "root_hash", "root_nodes"):

@@ -31,11 +31,17 @@ def test_library_builds_and_exports_every_declared_symbol():
         assert hasattr(lib, name), name
 
 
+def ctypes_sizeof_opts():
+    import ctypes
+    from paper_2212_01473_gb300 import engine
+    return ctypes.sizeof(engine.mce_opts)
+
+
 def test_default_opts_without_gpu():
     import paper_2212_01473_gb300 as mce
     o = mce.mce_default_opts()
-    assert o.donate_min_p == 10 and o.worker_list == 1 and o.timeout_ms == 60000
-    assert o.struct_size == 72
+    assert o.donate_min_p == 20 and o.worker_list == 1 and o.timeout_ms == 60000
+    assert o.struct_size == ctypes_sizeof_opts()
 
 
 def test_null_handle_errors_without_gpu():

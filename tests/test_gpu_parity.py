@@ -217,3 +217,22 @@ def test_batch_generated():
         assert (per[i].count, per[i].hash) == (o.count, o.hash), i
         if b.mm_sizes[i]:
             assert np.count_nonzero(hist[i]) >= 1
+
+
+def test_root_subset():
+    g = gen.gnp(600, 0.06, 12)
+    roots = np.random.default_rng(3).choice(g.n, 150, replace=False).astype(np.int32)
+    o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, roots=roots, per_root=True)
+    r, (rc, rh, rn) = run(g, per_root=True, roots=roots)
+    same(r, o)
+    assert np.array_equal(rc, o.root_count) and np.array_equal(rh, o.root_hash)
+    assert np.array_equal(rn, o.root_nodes)
+
+
+def test_root_subset_empty_and_bad():
+    g = gen.gnp(100, 0.1, 1)
+    r = run(g, roots=np.zeros(0, np.int32))
+    assert r.count == 0 and r.tree_nodes == 0
+    with pytest.raises(mce.MCEError) as ei:
+        run(g, roots=np.array([5, g.n], np.int32))
+    assert ei.value.code == mce.MCE_EINVAL
