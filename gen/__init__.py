@@ -12,6 +12,8 @@ max-degree/degeneracy 12-3,814):
 * ``er_2000``       G(n=2000, m=20000), seed 0
 * ``chunglu_1m``    Chung-Lu n=1e6, mean degree 16, exponent 2.1, weight cap
                     20,000, 50 planted cliques of size U[20,40], seed 1
+* ``chunglu_200k``  the same family at n=200,000, cap 4,000, 10 planted cliques
+                    (a small case for kernel profiles), seed 1
 * ``rmat_22``       R-MAT scale 22, edge factor 16, (0.57,0.19,0.19,0.05), seed 2
 * ``batch_4096``    4096 G(n,p) graphs, n power-law on [50,5000] (density
                     proportional to n^-2), mean degree U[5,60], one in eight
@@ -152,6 +154,8 @@ def workload(name: str, seed: Optional[int] = None) -> Graph:
         return er(2000, 20000, 0 if seed is None else seed)
     if name == "chunglu_1m":
         return chung_lu(1_000_000, 16.0, 2.1, 20000.0, 50, 20, 40, 1 if seed is None else seed)
+    if name == "chunglu_200k":  # a small case of the same family, for profiling
+        return chung_lu(200_000, 16.0, 2.1, 4000.0, 10, 20, 40, 1 if seed is None else seed)
     if name == "rmat_22":
         return rmat(22, 16, 0.57, 0.19, 0.19, 2 if seed is None else seed)
     if name == "batch_4096":

@@ -62,6 +62,12 @@ extern "C" {
 #define MCE_PIVOT_IP 1   /* pivot from P u X_P (partial induced subgraph) */
 #define MCE_PIVOT_IPX 2  /* pivot from P u X_P u X_X (full induced subgraph) */
 
+/* donation policy: a busy group may hand the child it is about to enter to an
+ * idle group when the child's |P| >= donate_min_p and ... */
+#define MCE_DONATE_PAPER 0 /* ... branches remain at this level AND at a shallower one (Sec. III-C) */
+#define MCE_DONATE_EITHER 1 /* ... branches remain at this level OR at a shallower one */
+#define MCE_DONATE_ANY 2   /* ... always (the donor may become idle right after) */
+
 /* root ordering */
 #define MCE_ORDER_PLAIN 0   /* roots in degeneracy order within each width class */
 #define MCE_ORDER_PRIORITY 1/* roots by descending opts.root_priority (e.g. learned work estimate) */
@@ -85,9 +91,10 @@ typedef struct {
     int32_t pivot;         /* MCE_PIVOT_* */
     int32_t order;         /* MCE_ORDER_* */
     int32_t worker_list;   /* 1 = idle workers receive donated subtrees (Sec. III-C), 0 = off */
-    int32_t donate_min_p;  /* donate a branch only if its |P| >= this (Sec. III-C uses 10; default 20) */
+    int32_t donate_min_p;  /* donate a child only if its |P| >= this (Sec. III-C uses 10); 0 = automatic:
+                            max(10, largest |P0| of the width class / 8) */
     int32_t blocks;        /* persistent blocks per width class; 0 = all that fit on the GPU */
-    int32_t tune;          /* reserved, set 0 */
+    int32_t donate_policy; /* which busy groups may donate a child (Sec. III-C): MCE_DONATE_* */
     int32_t stats;         /* 1 = collect per-phase SM cycle counters (see mce_stats); slows the run */
     int64_t timeout_ms;    /* give-up bound for every device-side wait (default 60000) */
     /* optional DEVICE buffers, indexed by input vertex id, length n: the
@@ -118,7 +125,7 @@ typedef struct {
 } mce_result;
 
 /* Fill *opts with defaults (IP/IPX auto, plain order, worker list on,
- * donate_min_p 20, timeout 60 s). */
+ * donate_min_p 0 = automatic, donate_policy MCE_DONATE_EITHER, timeout 60 s). */
 void mce_default_opts(mce_opts *opts);
 
 /*

@@ -220,7 +220,8 @@ extern "C" void mce_default_opts(mce_opts *o) {
     o->pivot = MCE_PIVOT_AUTO;
     o->order = MCE_ORDER_PLAIN;
     o->worker_list = 1;
-    o->donate_min_p = 20;
+    o->donate_min_p = 0;
+    o->donate_policy = MCE_DONATE_EITHER;
     o->timeout_ms = 60000;
 }
 
@@ -454,10 +455,12 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         opts = *opts_in;
     }
     if (opts.pivot < 0 || opts.pivot > 2) return fail(MCE_EINVAL, "bad opts.pivot");
-    if (opts.order == MCE_ORDER_PRIORITY) return fail(MCE_EINVAL, "priority order is not available in this build");
-    if (opts.order != MCE_ORDER_PLAIN) return fail(MCE_EINVAL, "bad opts.order");
+    if (opts.order != MCE_ORDER_PLAIN && opts.order != MCE_ORDER_PRIORITY) return fail(MCE_EINVAL, "bad opts.order");
+    if (opts.order == MCE_ORDER_PRIORITY && !opts.root_priority)
+        return fail(MCE_EINVAL, "MCE_ORDER_PRIORITY needs opts.root_priority");
     if (opts.pivot == MCE_PIVOT_IPX) return fail(MCE_EINVAL, "IPX pivoting is not available in this build");
-    if (opts.donate_min_p < 1) opts.donate_min_p = 1;
+    if (opts.donate_min_p < 0) return fail(MCE_EINVAL, "opts.donate_min_p < 0");
+    if (opts.donate_policy < 0 || opts.donate_policy > 2) return fail(MCE_EINVAL, "bad opts.donate_policy");
     if (opts.timeout_ms <= 0) opts.timeout_ms = 60000;
     if (hist && hist_len < 0) return fail(MCE_EINVAL, "hist_len < 0");
     const int G = g->G;
@@ -544,6 +547,19 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
             counts[c] = kept;
         }
     }
+    if (opts.order == MCE_ORDER_PRIORITY && g->n > 0) {
+        int *hb = (int *)dalloc(g, 256 * sizeof(int));
+        run_tmp.push_back(hb);
+        if (!hb) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+        for (int c = 0; c < kNumClasses; c++) {
+            if (counts[c] == 0) continue;
+            int32_t *out = (int32_t *)dalloc(g, (size_t)counts[c] * 4);
+            run_tmp.push_back(out);
+            if (!out) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+            CK(launch_priority_order(lists[c], counts[c], g->order, opts.root_priority, hb, out, g->stream));
+            lists[c] = out;
+        }
+    }
     CK(cudaEventRecord(ev0, g->stream));
     if (counts[kNumClasses] > 0) {
         const int nr = counts[kNumClasses];
@@ -585,7 +601,10 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         a.x_cap = g->class_x[c];
         a.pivot_ipx = 0;
         a.worker_list = opts.worker_list ? 1 : 0;
-        a.donate_min_p = opts.donate_min_p;
+        // 0 = automatic: a donated child must have at least 1/8 of the
+        // class's widest root set, and never fewer than 10 candidates (Sec. III-C)
+        a.donate_min_p = opts.donate_min_p > 0 ? opts.donate_min_p : std::max(10, rows / 8);
+        a.donate_policy = opts.donate_policy;
         a.root_chunk = 1;
         a.stats = opts.stats ? 1 : 0;
         a.timeout_ns = (uint64_t)opts.timeout_ms * 1000000ull;

@@ -164,6 +164,7 @@ struct ClassArgs {
     int32_t pivot_ipx;      // 1: pivot candidates include X_X
     int32_t worker_list;
     int32_t donate_min_p;
+    int32_t donate_policy;  // MCE_DONATE_*
     int32_t root_chunk;     // roots claimed per atomic
     int32_t stats;          // 1: collect per-phase cycle counters
     uint64_t timeout_ns;

@@ -525,6 +525,40 @@ __global__ void k_gather_flagged(const int32_t *list, int cnt, const int32_t *fl
         if (flags[i]) out[pos[i]] = list[i];
 }
 
+// -------------------------------------------------- priority order (buckets)
+
+constexpr int kPrioBuckets = 256;
+
+__device__ __forceinline__ int prio_bucket(float p) {
+    // descending priority first; quarter-unit buckets (priorities are log2 work)
+    if (!(p > 0.f)) p = 0.f;  // NaN and negatives land in the last bucket
+    int b = (int)(p * 4.f);
+    b = b > kPrioBuckets - 1 ? kPrioBuckets - 1 : b;
+    return kPrioBuckets - 1 - b;
+}
+
+__global__ void k_prio_hist(const int32_t *list, int cnt, const int32_t *order, const float *prio, int *hist) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
+        atomicAdd(&hist[prio_bucket(prio[order[list[i]]])], 1);
+}
+
+__global__ void k_prio_offsets(int *hist) {
+    // exclusive scan of kPrioBuckets counts in place (one block of kPrioBuckets threads)
+    __shared__ int sh[32];
+    int tot;
+    const int x = hist[threadIdx.x];
+    const int pre = block_scan_excl<kPrioBuckets>(x, sh, &tot);
+    hist[threadIdx.x] = pre;
+}
+
+__global__ void k_prio_scatter(const int32_t *list, int cnt, const int32_t *order, const float *prio, int *cursor,
+                               int32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = list[i];
+        out[atomicAdd(&cursor[prio_bucket(prio[order[r]])], 1)] = r;
+    }
+}
+
 // ------------------------------------------------------------ host side
 
 static unsigned grid_for(int64_t work, int per_block, int cap = 1 << 20) {
@@ -640,6 +674,20 @@ cudaError_t launch_subset(const int32_t *list, int cnt, const int32_t *mask, int
     cudaError_t e = exclusive_scan(flags, pos, cnt, scan_tmp, s);
     if (e != cudaSuccess) return e;
     k_gather_flagged<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, flags, pos, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
+cudaError_t launch_priority_order(const int32_t *list, int cnt, const int32_t *order, const float *prio,
+                                  int *hist, int32_t *out, cudaStream_t s) {
+    if (cnt <= 0) return cudaSuccess;
+    cudaError_t e = cudaMemsetAsync(hist, 0, kPrioBuckets * sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_prio_hist<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, order, prio, hist);
+    count_launch();
+    k_prio_offsets<<<1, kPrioBuckets, 0, s>>>(hist);
+    count_launch();
+    k_prio_scatter<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, order, prio, hist, out);
     count_launch();
     return cudaGetLastError();
 }

@@ -42,4 +42,9 @@ cudaError_t launch_mark_roots(const int32_t *ids, int64_t k, const int32_t *rank
 cudaError_t launch_subset(const int32_t *list, int cnt, const int32_t *mask, int32_t *flags, int32_t *pos,
                           int32_t *scan_tmp, int32_t *out, cudaStream_t s);
 
+// roots of list[0..cnt) by descending prio[order[r]] (quarter-unit buckets,
+// any order inside a bucket); hist: 256 ints of scratch
+cudaError_t launch_priority_order(const int32_t *list, int cnt, const int32_t *order, const float *prio,
+                                  int *hist, int32_t *out, cudaStream_t s);
+
 }  // namespace mce

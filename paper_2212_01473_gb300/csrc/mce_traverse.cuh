@@ -617,7 +617,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 }
                 const int others_here = grp_or(g, red, b != 0u);
                 // ------------------------------ donation (Sec. III-C)
-                if (C.worker_list && pcnt >= C.donate_min_p && others_here && npend >= 1) {
+                const bool may_donate = C.donate_policy == MCE_DONATE_ANY ||
+                                        (C.donate_policy == MCE_DONATE_EITHER ? (others_here || npend >= 1)
+                                                                              : (others_here && npend >= 1));
+                if (C.worker_list && pcnt >= C.donate_min_p && may_donate) {
                     if (g.gl == 0) {
                         int claimed = -1;
                         if (ld_relaxed(&C.ctl[CTL_IDLE]) > 0) {

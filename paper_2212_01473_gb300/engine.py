@@ -19,6 +19,7 @@ MCE_OK, MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETIMEOUT, MCE_ERANGE, MCE_EUNSUPP
 MCE_FLAG_DEVICE_PTRS = 1
 MCE_PIVOT_AUTO, MCE_PIVOT_IP, MCE_PIVOT_IPX = 0, 1, 2
 MCE_ORDER_PLAIN, MCE_ORDER_PRIORITY = 0, 1
+MCE_DONATE_PAPER, MCE_DONATE_EITHER, MCE_DONATE_ANY = 0, 1, 2
 MCE_MAX_DEGENERACY = 4096
 
 _NAMES = {MCE_EINVAL: "MCE_EINVAL", MCE_ENOMEM: "MCE_ENOMEM", MCE_ECUDA: "MCE_ECUDA",
@@ -42,7 +43,7 @@ class mce_allocator(ctypes.Structure):
 class mce_opts(ctypes.Structure):
     _fields_ = [("struct_size", ctypes.c_int32), ("pivot", ctypes.c_int32), ("order", ctypes.c_int32),
                 ("worker_list", ctypes.c_int32), ("donate_min_p", ctypes.c_int32),
-                ("blocks", ctypes.c_int32), ("tune", ctypes.c_int32), ("stats", ctypes.c_int32),
+                ("blocks", ctypes.c_int32), ("donate_policy", ctypes.c_int32), ("stats", ctypes.c_int32),
                 ("timeout_ms", ctypes.c_int64), ("root_count", ctypes.c_void_p),
                 ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
                 ("root_priority", ctypes.c_void_p), ("roots", ctypes.c_void_p),

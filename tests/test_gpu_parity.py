@@ -236,3 +236,17 @@ def test_root_subset_empty_and_bad():
     with pytest.raises(mce.MCEError) as ei:
         run(g, roots=np.array([5, g.n], np.int32))
     assert ei.value.code == mce.MCE_EINVAL
+
+
+def test_timeout_is_reported_and_context_survives():
+    # every device wait is bounded: a 1 ms bound on a run that needs more makes
+    # the kernels give up and return MCE_ETIMEOUT; the next run is unaffected
+    g = gen.chung_lu(20000, 16.0, 2.1, 2000.0, 5, 25, 40, 3)
+    h = mce.mce_create(g.row_ptr, g.col)
+    with pytest.raises(mce.MCEError) as ei:
+        mce.mce_run(h, mce.mce_default_opts(timeout_ms=1, blocks=1))
+    assert ei.value.code == mce.MCE_ETIMEOUT
+    r = mce.mce_run(h)
+    mce.mce_destroy(h)
+    o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP)
+    same(r, o)
