@@ -212,6 +212,38 @@ typedef struct {
 
 int mce_get_stats(const mce_graph *g, mce_stats *out);
 
+/*
+ * mce_peel_noalloc -- the degeneracy peel of mce_create (core numbers and
+ * order), for callers that must not allocate device memory. The paper has no
+ * counterpart; it is a deployment variant of the same kernel.
+ *
+ * Who needs it: code whose device memory is budgeted by someone else -- a
+ * serving process whose pool reserves the whole GPU up front, a plug-in
+ * running inside another framework's allocator, or a stage that must not call
+ * cudaMalloc because cudaMalloc can synchronise the device and is not allowed
+ * while a stream is being captured into a CUDA graph.
+ *
+ * It allocates nothing: its scratch is one file-scope static device array of
+ * (5 * MCE_NOALLOC_MAX_VERTICES + MCE_NOALLOC_MAX_VERTICES / 32 + 1184) 32-bit
+ * words (about 21 MB), which every GPU that loads the library holds until the
+ * process exits. Graphs with n > MCE_NOALLOC_MAX_VERTICES are rejected with
+ * MCE_EUNSUPPORTED.
+ *   row_ptr, col  DEVICE CSR (canonical, as for mce_create); n vertices, m edges
+ *   core, rank    DEVICE int32[n], by input id: core number, position in the order
+ *   order         DEVICE int32[n]: order[r] = the vertex of rank r
+ *   stream        cudaStream_t (NULL = default stream); synchronous on return
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture. Every call on a device shares the same array and
+ * the call clears what must start at zero, so calls that overlap on the GPU
+ * (two streams, two threads) race and must be serialised by the caller.
+ * Results equal mce_create's order (mce_get_order). Errors: MCE_EINVAL,
+ * MCE_EUNSUPPORTED, MCE_ETIMEOUT, MCE_ECUDA; message in mce_last_error().
+ */
+#define MCE_NOALLOC_MAX_VERTICES (1 << 20)
+int mce_peel_noalloc(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t m, int32_t *core,
+                     int32_t *rank, int32_t *order, void *stream);
+
 /* Release the handle and all its device memory. NULL is a no-op. */
 void mce_destroy(mce_graph *g);
 

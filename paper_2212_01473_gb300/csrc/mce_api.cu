@@ -143,6 +143,11 @@ static int fail(int code, const char *fmt, ...) {
     return code;
 }
 
+int mce::set_last_error(int code, const char *msg) {
+    g_err = msg;
+    return code;
+}
+
 #define CK(call)                                                                             \
     do {                                                                                     \
         cudaError_t _e = (call);                                                             \

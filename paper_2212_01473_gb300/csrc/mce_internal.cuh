@@ -95,6 +95,9 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
     return s_ok != 0;
 }
 
+// Record a message for mce_last_error() on this thread; returns code.
+int set_last_error(int code, const char *msg);
+
 // Kernel launches made by this host thread (reported by mce_get_stats).
 inline uint64_t &launch_counter() {
     static thread_local uint64_t c = 0;

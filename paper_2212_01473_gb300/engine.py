@@ -94,6 +94,7 @@ def library():
         lib.mce_graph_info.argtypes = [vp, i32p, ctypes.POINTER(ctypes.c_int64), i32p, i32p, i32p]
         lib.mce_get_order.argtypes = [vp, i32p, i32p, i32p]
         lib.mce_get_stats.argtypes = [vp, ctypes.POINTER(mce_stats)]
+        lib.mce_peel_noalloc.argtypes = [vp, vp, i32, i64, vp, vp, vp, vp]
         lib.mce_destroy.argtypes = [vp]
         lib.mce_destroy.restype = None
         lib.mce_last_error.argtypes = []
@@ -299,6 +300,23 @@ def mce_get_stats(h: Handle) -> dict:
         "phase_cycles": {PHASES[i]: int(st.phase_cycles[i]) for i in range(7)},
         "phase_counts": {PHASES[i]: int(st.phase_counts[i]) for i in range(7)},
     }
+
+
+def mce_peel_noalloc(row_ptr, col, core, rank, order, stream: Optional[int] = None):
+    """Degeneracy peel into caller-owned CUDA int32 tensors, allocating nothing
+    (see include/mce.h): core and rank by input id, order[r] = vertex of rank r."""
+    import torch
+    for t in (row_ptr, col, core, rank, order):
+        if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.int32 and t.is_contiguous()):
+            raise TypeError("mce_peel_noalloc takes contiguous CUDA int32 tensors")
+    n = row_ptr.numel() - 1
+    if min(core.numel(), rank.numel(), order.numel()) < n:
+        raise ValueError("output tensors shorter than n")
+    s = stream if stream is not None else torch.cuda.current_stream().cuda_stream
+    _check(library().mce_peel_noalloc(ctypes.c_void_p(row_ptr.data_ptr()), ctypes.c_void_p(col.data_ptr()),
+                                      n, col.numel() // 2, ctypes.c_void_p(core.data_ptr()),
+                                      ctypes.c_void_p(rank.data_ptr()), ctypes.c_void_p(order.data_ptr()),
+                                      ctypes.c_void_p(s)))
 
 
 def mce_destroy(h: Handle):
