@@ -371,10 +371,11 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
         g->mixid = dnew<uint64_t>(g, nn, nullptr);
         if (G > 1) g->gid = dnew<int32_t>(g, nn, nullptr);
         int *small = dnew<int>(g, 64, &tmp);
+        int *long_rows = dnew<int>(g, nn + 1, &tmp);
         if (!g->outdeg || !indeg || !g->out_ptr || !g->in_ptr || !g->out_col || !g->in_col || !scan_tmp ||
-            !g->mixid || (G > 1 && !g->gid) || !small) { rc = fail(MCE_ENOMEM, "device allocation for orientation failed"); goto cleanup; }
+            !g->mixid || (G > 1 && !g->gid) || !small || !long_rows) { rc = fail(MCE_ENOMEM, "device allocation for orientation failed"); goto cleanup; }
         CK(launch_orient(n, d_rp, d_col, g->order, g->rank, g->outdeg, indeg, g->out_ptr, g->out_col,
-                         g->in_ptr, g->in_col, scan_tmp, g->stream));
+                         g->in_ptr, g->in_col, scan_tmp, long_rows, g->stream));
         CK(launch_mix_gid(n, g->order, g->mixid, g->gid, d_gptr, G, g->stream));
         CK(cudaMemsetAsync(small, 0, 64 * 4, g->stream));
         k_last_core<<<1, 1, 0, g->stream>>>(g->order, g->core, n, small);

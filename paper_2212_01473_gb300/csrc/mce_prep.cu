@@ -141,6 +141,11 @@ __device__ void block_bitonic(int *a, int len) {
     }
 }
 
+// Once at most this many vertices remain at a level start, block 0 finishes
+// the peel alone (block barriers instead of grid barriers); the other blocks
+// return. The rounds, ranks and core numbers are the same either way.
+constexpr int kSoloRemaining = 16384;
+
 __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp, const int32_t *col,
                                                        int32_t *deg, int32_t *rank, int32_t *core,
                                                        int32_t *order, int32_t *remA, int32_t *remB,
@@ -150,24 +155,44 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     __shared__ int sh[64];
     __shared__ int ssort[kSmallSort];
     const uint64_t deadline = globaltimer_ns() + timeout_ns;
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    const int64_t gwarp = tid >> 5, nwarps = nth >> 5;
-    GridBar *bar = &ctl->bar;
+    int64_t gwarp = tid >> 5, nwarps = nth >> 5;
+    int nblocks = gridDim.x, bid = blockIdx.x;
+    bool solo = false;
+    GridBar *gbar = &ctl->bar;
+    auto barrier = [&]() -> bool {
+        if (solo) {
+            __syncthreads();
+            return true;
+        }
+        return grid_barrier(gbar, status, deadline);
+    };
 
     for (int64_t v = tid; v < n; v += nth) {
         deg[v] = rp[v + 1] - rp[v];
         rank[v] = -1;
         remA[v] = (int32_t)v;
     }
-    if (!grid_barrier(bar, status, deadline)) return;
+    if (!barrier()) return;
 
     for (;;) {
         if (vload(&ctl->next) >= n) break;
+        const int nrem = vload(&ctl->nrem);
+        if (!solo && nrem <= kSoloRemaining) {
+            // every block read the same nrem after the last grid barrier
+            if (blockIdx.x != 0) return;
+            solo = true;
+            tid = threadIdx.x;
+            nth = blockDim.x;
+            gwarp = tid >> 5;
+            nwarps = nth >> 5;
+            nblocks = 1;
+            bid = 0;
+        }
         int32_t *rem = vload(&ctl->remsel) ? remB : remA;
         int32_t *rem2 = vload(&ctl->remsel) ? remA : remB;
-        const int nrem = vload(&ctl->nrem);
         // level start: k = max(k, min remaining degree)
         int lmin = INT_MAX;
         for (int64_t i = tid; i < nrem; i += nth) {
@@ -176,7 +201,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         }
         lmin = block_reduce_min<kPeelThreads>(lmin, sh);
         if (threadIdx.x == 0 && lmin != INT_MAX) atomicMin(&ctl->minval, lmin);
-        if (!grid_barrier(bar, status, deadline)) return;
+        if (!barrier()) return;
         const int k = max(vload(&ctl->k), vload(&ctl->minval));
         {
             int32_t *S = vload(&ctl->sel) ? SB : SA;
@@ -195,15 +220,15 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 if (live && !inS) rem2[pk] = v;
             }
         }
-        if (!grid_barrier(bar, status, deadline)) return;
-        if (blockIdx.x == 0 && threadIdx.x == 0) {
+        if (!barrier()) return;
+        if (bid == 0 && threadIdx.x == 0) {
             ctl->k = k;
             ctl->minval = INT_MAX;
             ctl->remsel ^= 1;
             ctl->nrem = ctl->nrem2;
             ctl->nrem2 = 0;
         }
-        if (!grid_barrier(bar, status, deadline)) return;
+        if (!barrier()) return;
 
         // sub-rounds at level k: S_t = remaining vertices with degree <= k
         for (;;) {
@@ -213,7 +238,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             int32_t *S2 = vload(&ctl->sel) ? SA : SB;
             // ranks inside a sub-round follow ascending vertex id
             if (ns <= kSmallSort) {
-                if (blockIdx.x == 0) {
+                if (bid == 0) {
                     for (int i = threadIdx.x; i < ns; i += blockDim.x) ssort[i] = S[i];
                     __syncthreads();
                     block_bitonic(ssort, ns);
@@ -224,17 +249,17 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     int v = S[i];
                     atomicOr(&bitmap[v >> 5], 1u << (v & 31));
                 }
-                if (!grid_barrier(bar, status, deadline)) return;
+                if (!barrier()) return;
                 const int nw = (n + 31) >> 5;
-                const int chunk = (nw + gridDim.x - 1) / gridDim.x;
-                const int w_lo = min(nw, (int)blockIdx.x * chunk), w_hi = min(nw, w_lo + chunk);
+                const int chunk = (nw + nblocks - 1) / nblocks;
+                const int w_lo = min(nw, bid * chunk), w_hi = min(nw, w_lo + chunk);
                 int c = 0;
                 for (int w = w_lo + threadIdx.x; w < w_hi; w += blockDim.x) c += __popc(bitmap[w]);
                 c = block_reduce_sum<kPeelThreads>(c, sh);
-                if (threadIdx.x == 0) blocksums[blockIdx.x] = c;
-                if (!grid_barrier(bar, status, deadline)) return;
+                if (threadIdx.x == 0) blocksums[bid] = c;
+                if (!barrier()) return;
                 int off = 0;
-                for (int b = threadIdx.x; b < (int)blockIdx.x; b += blockDim.x) off += blocksums[b];
+                for (int b = threadIdx.x; b < bid; b += blockDim.x) off += blocksums[b];
                 off = block_reduce_sum<kPeelThreads>(off, sh);
                 for (int t0 = w_lo; t0 < w_hi; t0 += blockDim.x) {
                     int w = t0 + threadIdx.x;
@@ -251,7 +276,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     off += tot;
                 }
             }
-            if (!grid_barrier(bar, status, deadline)) return;
+            if (!barrier()) return;
             const int base = vload(&ctl->next);
             for (int64_t i = tid; i < ns; i += nth) {
                 int v = S[i];
@@ -259,7 +284,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 core[v] = k;
                 order[base + i] = v;
             }
-            if (!grid_barrier(bar, status, deadline)) return;
+            if (!barrier()) return;
             for (int64_t i = gwarp; i < ns; i += nwarps) {
                 const int v = S[i];
                 const int b = rp[v], e = rp[v + 1];
@@ -278,15 +303,15 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     if (push) S2[p] = u;
                 }
             }
-            if (!grid_barrier(bar, status, deadline)) return;
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
+            if (!barrier()) return;
+            if (bid == 0 && threadIdx.x == 0) {
                 ctl->next += ns;
                 ctl->ns = ctl->ns2;
                 ctl->ns2 = 0;
                 ctl->sel ^= 1;
                 ctl->rounds++;
             }
-            if (!grid_barrier(bar, status, deadline)) return;
+            if (!barrier()) return;
         }
     }
 }
@@ -415,8 +440,9 @@ __global__ void k_fill_split(int n, const int32_t *rp, const int32_t *col, const
 constexpr int kRowSortWarpCap = 1024;
 constexpr int kRowSortBlockCap = 4096;
 
-// rows of length <= kRowSortWarpCap: one warp per row, bitonic in shared memory
-__global__ void __launch_bounds__(256) k_sort_rows_warp(int n, const int32_t *ptr, int32_t *colv) {
+// rows of length <= kRowSortWarpCap: one warp per row, bitonic in shared
+// memory; longer rows are listed for k_sort_rows_block
+__global__ void __launch_bounds__(256) k_sort_rows_warp(int n, const int32_t *ptr, int32_t *colv, int *long_rows) {
     __shared__ int buf[8][kRowSortWarpCap];
     const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
     int *a = buf[wib];
@@ -424,7 +450,11 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(int n, const int32_t *pt
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     for (int64_t r = w0; r < n; r += nw) {
         const int b = ptr[r], len = ptr[r + 1] - b;
-        if (len <= 1 || len > kRowSortWarpCap) continue;
+        if (len > kRowSortWarpCap) {
+            if (lane == 0) long_rows[1 + atomicAdd(&long_rows[0], 1)] = (int)r;
+            continue;
+        }
+        if (len <= 1) continue;
         int m = 1;
         while (m < len) m <<= 1;
         for (int i = lane; i < m; i += 32) a[i] = i < len ? colv[b + i] : INT_MAX;
@@ -446,12 +476,14 @@ __global__ void __launch_bounds__(256) k_sort_rows_warp(int n, const int32_t *pt
     }
 }
 
-// rows longer than kRowSortWarpCap (at most the degeneracy): one block per row
-__global__ void __launch_bounds__(1024) k_sort_rows_block(int n, const int32_t *ptr, int32_t *colv) {
+// the listed rows longer than kRowSortWarpCap (at most the degeneracy): one block per row
+__global__ void __launch_bounds__(1024) k_sort_rows_block(const int *long_rows, const int32_t *ptr, int32_t *colv) {
     __shared__ int a[kRowSortBlockCap];
-    for (int64_t r = blockIdx.x; r < n; r += gridDim.x) {
+    const int cnt = long_rows[0];
+    for (int i = blockIdx.x; i < cnt; i += gridDim.x) {
+        const int r = long_rows[1 + i];
         const int b = ptr[r], len = ptr[r + 1] - b;
-        if (len <= kRowSortWarpCap || len > kRowSortBlockCap) continue;
+        if (len > kRowSortBlockCap) continue;
         for (int i = threadIdx.x; i < len; i += blockDim.x) a[i] = colv[b + i];
         __syncthreads();
         block_bitonic(a, len);
@@ -479,13 +511,26 @@ __global__ void k_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t 
 // class statistics and per-class flags
 __global__ void k_class_stats(int n, const int32_t *outdeg, const int32_t *indeg, int *cls_rows,
                               int *cls_x, int *cls_count) {
+    __shared__ int srows[kNumClasses + 1], sx[kNumClasses + 1], scnt[kNumClasses + 1];
+    if (threadIdx.x <= kNumClasses) {
+        srows[threadIdx.x] = 0;
+        sx[threadIdx.x] = 0;
+        scnt[threadIdx.x] = 0;
+    }
+    __syncthreads();
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
         const int n0 = outdeg[r];
         const int c = n0 == 0 ? kNumClasses : class_of(n0);
         if (c < 0) continue;
-        atomicMax(&cls_rows[c], n0);
-        atomicMax(&cls_x[c], indeg[r]);
-        atomicAdd(&cls_count[c], 1);
+        atomicMax(&srows[c], n0);
+        atomicMax(&sx[c], indeg[r]);
+        atomicAdd(&scnt[c], 1);
+    }
+    __syncthreads();
+    if (threadIdx.x <= kNumClasses && scnt[threadIdx.x]) {
+        atomicMax(&cls_rows[threadIdx.x], srows[threadIdx.x]);
+        atomicMax(&cls_x[threadIdx.x], sx[threadIdx.x]);
+        atomicAdd(&cls_count[threadIdx.x], scnt[threadIdx.x]);
     }
 }
 
@@ -620,7 +665,7 @@ cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s) {
 cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const int32_t *order,
                           const int32_t *rank, int32_t *outdeg, int32_t *indeg, int32_t *out_ptr,
                           int32_t *out_col, int32_t *in_ptr, int32_t *in_col, int32_t *scan_tmp,
-                          cudaStream_t s) {
+                          int *long_rows, cudaStream_t s) {
     if (n == 0) {
         cudaError_t e = exclusive_scan(outdeg, out_ptr, 0, scan_tmp, s);
         if (e != cudaSuccess) return e;
@@ -635,9 +680,12 @@ cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const in
     if (e != cudaSuccess) return e;
     k_fill_split<<<gw, 256, 0, s>>>(n, rp, col, order, rank, out_ptr, out_col, in_ptr, in_col);
     count_launch();
-    k_sort_rows_warp<<<gw, 256, 0, s>>>(n, out_ptr, out_col);
+    // long_rows[0] = count, then the rows longer than a warp sorts
+    e = cudaMemsetAsync(long_rows, 0, sizeof(int), s);
+    if (e != cudaSuccess) return e;
+    k_sort_rows_warp<<<gw, 256, 0, s>>>(n, out_ptr, out_col, long_rows);
     count_launch();
-    k_sort_rows_block<<<grid_for(n, 1, 4096), 1024, 0, s>>>(n, out_ptr, out_col);
+    k_sort_rows_block<<<152, 1024, 0, s>>>(long_rows, out_ptr, out_col);
     count_launch();
     return cudaGetLastError();
 }

@@ -28,7 +28,7 @@ int64_t scan_tmp_words(int64_t n);
 cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const int32_t *order,
                           const int32_t *rank, int32_t *outdeg, int32_t *indeg, int32_t *out_ptr,
                           int32_t *out_col, int32_t *in_ptr, int32_t *in_col, int32_t *scan_tmp,
-                          cudaStream_t s);
+                          int *long_rows /* n + 1 ints */, cudaStream_t s);
 cudaError_t launch_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t *gid,
                            const int32_t *graph_ptr, int G, cudaStream_t s);
 cudaError_t launch_classify(int n, const int32_t *outdeg, const int32_t *indeg, int *cls_rows,
