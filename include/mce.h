@@ -244,6 +244,49 @@ int mce_get_stats(const mce_graph *g, mce_stats *out);
 int mce_peel_noalloc(const int32_t *row_ptr, const int32_t *col, int32_t n, int64_t m, int32_t *core,
                      int32_t *rank, int32_t *order, void *stream);
 
+/* ------------------------------------------- learned work estimator
+ * Not in the paper: a small network predicts log2 of each root's subtree
+ * size (Bron-Kerbosch calls) from 16 root features; the prediction is only
+ * used to order roots (opts.order = MCE_ORDER_PRIORITY), so results never
+ * change. Features (int32, saturating at INT32_MAX), for a root v with
+ * P0 = later and X0 = earlier neighbours in the degeneracy order:
+ *   0 deg(v)             1 core(v)             2 |P0|              3 |X0|
+ *   4 e(P0) + e(P0,X0)   5 e(P0)               6 e(P0,X0)          7 floor(2^16 e(P0) / C(|P0|,2))
+ *   8 sum of deg(u), u in N(v)                 9 max / 10 min over u in P0 of |N(u) n P0|
+ *  11 #u in P0 adjacent to all other P0        12 max / 13 sum of core(u) over u in P0
+ *  14 max over x in X0 of |N(x) n P0|          15 C(|P0|,2) - e(P0)
+ * The network input is log2(1 + feature), standardised with per-feature
+ * mean/std stored in the model. Layers: 16 -> 64 (ReLU) -> 64 (ReLU) -> 1,
+ * weights rounded to BF16 (nearest even) in every use, biases and all
+ * accumulation in FP32. Training minimises the mean squared error with Adam
+ * (beta1 0.9, beta2 0.999, eps 1e-8) on FP32 master weights. */
+#define MCE_NUM_FEATURES 16
+#define MCE_MODEL_HIDDEN 64
+/* parameter vector: W1[64][16] b1[64] W2[64][64] b2[64] W3[64] b3 mean[16] std[16] */
+#define MCE_MODEL_PARAMS (64 * 16 + 64 + 64 * 64 + 64 + 64 + 1 + 16 + 16)
+
+typedef struct mce_model mce_model;
+
+/* Root features of a single-graph or batched handle into DEVICE buffers of
+ * n * 16 elements indexed [input id][feature]: raw int32 values and/or
+ * log2(1 + value) as float (either may be NULL). */
+int mce_root_features(mce_graph *g, int32_t *raw, float *feat);
+
+/* New model from a HOST parameter vector (MCE_MODEL_PARAMS floats, every std > 0). */
+int mce_model_create(const float *params, const mce_allocator *alloc, void *stream, mce_model **out);
+int mce_model_get_params(const mce_model *m, float *params);
+/* DEVICE feat[n][16] (log2 features) -> DEVICE out[n] predicted log2 subtree size */
+int mce_model_predict(mce_model *m, const float *feat, int64_t n, float *out);
+/* Gradient of the batch's mean squared error with respect to every trained
+ * parameter (standardisation entries get 0), HOST grad[MCE_MODEL_PARAMS];
+ * *loss = the mean squared error. DEVICE feat[batch][16], label[batch]. */
+int mce_model_gradient(mce_model *m, const float *feat, const float *label, int32_t batch, float *grad,
+                       float *loss);
+/* One Adam step on the batch; *loss (HOST, may be NULL) = its mean squared error before the step. */
+int mce_model_train_step(mce_model *m, const float *feat, const float *label, int32_t batch, float lr,
+                         float *loss);
+void mce_model_destroy(mce_model *m);
+
 /* Release the handle and all its device memory. NULL is a no-op. */
 void mce_destroy(mce_graph *g);
 

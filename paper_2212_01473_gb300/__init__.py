@@ -8,7 +8,8 @@ from .engine import (MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ERANGE, MCE_ETIMEOUT
                      MCE_FLAG_DEVICE_PTRS, MCE_OK, MCE_ORDER_PLAIN, MCE_ORDER_PRIORITY, MCE_PIVOT_AUTO,
                      MCE_PIVOT_IP, MCE_PIVOT_IPX, MCEError, Result, enumerate_maximal_cliques, library,
                      mce_batch_create, mce_create, mce_default_opts, mce_destroy, mce_get_order,
-                     mce_get_stats, mce_graph_info, mce_peel_noalloc, mce_run, mce_run_batch)
+                     mce_get_stats, mce_graph_info, mce_peel_noalloc, mce_root_features, mce_run, mce_run_batch,
+                     Model, MCE_MODEL_PARAMS, MCE_NUM_FEATURES)
 
 __all__ = [name for name in dir() if name.startswith(("mce_", "MCE"))] + [
-    "Result", "enumerate_maximal_cliques", "library"]
+    "Model", "Result", "enumerate_maximal_cliques", "library"]

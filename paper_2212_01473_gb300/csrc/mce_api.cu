@@ -7,6 +7,7 @@
 #include <string>
 #include <vector>
 
+#include "mce_learn.cuh"
 #include "mce_prep.cuh"
 #include "mce_trav_inst.cuh"
 
@@ -748,6 +749,25 @@ extern "C" int mce_get_order(const mce_graph *g, int32_t *core, int32_t *rank, i
     if (out_degree)
         for (size_t v = 0; v < n; v++) out_degree[v] = hout[(size_t)hrank[v]];
     return MCE_OK;
+}
+
+extern "C" int mce_root_features(mce_graph *g, int32_t *raw, float *feat) {
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    if (g->n == 0 || (!raw && !feat)) return MCE_OK;
+    const int threads = 256;
+    const int blocks = std::min<int64_t>((int64_t)g->sm_count * 16, ((int64_t)g->n * 32 + threads - 1) / threads);
+    const int warps = blocks * (threads / 32);
+    const int stride = g->d + 1;
+    int rc = MCE_OK;
+    int32_t *scratch = (int32_t *)dalloc(g, (size_t)warps * stride * sizeof(int32_t));
+    if (!scratch) return fail(MCE_ENOMEM, "device allocation failed");
+    CK(launch_root_features(g->n, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->core, scratch, stride,
+                            warps, raw, feat, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+cleanup:
+    dfree(g, scratch);
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    return rc;
 }
 
 extern "C" int mce_get_stats(const mce_graph *g, mce_stats *out) {

@@ -95,6 +95,15 @@ def library():
         lib.mce_get_order.argtypes = [vp, i32p, i32p, i32p]
         lib.mce_get_stats.argtypes = [vp, ctypes.POINTER(mce_stats)]
         lib.mce_peel_noalloc.argtypes = [vp, vp, i32, i64, vp, vp, vp, vp]
+        f32p = ctypes.POINTER(ctypes.c_float)
+        lib.mce_root_features.argtypes = [vp, vp, vp]
+        lib.mce_model_create.argtypes = [f32p, ctypes.POINTER(mce_allocator), vp, ctypes.POINTER(vp)]
+        lib.mce_model_get_params.argtypes = [vp, f32p]
+        lib.mce_model_predict.argtypes = [vp, vp, i64, vp]
+        lib.mce_model_gradient.argtypes = [vp, vp, vp, i32, f32p, f32p]
+        lib.mce_model_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, f32p]
+        lib.mce_model_destroy.argtypes = [vp]
+        lib.mce_model_destroy.restype = None
         lib.mce_destroy.argtypes = [vp]
         lib.mce_destroy.restype = None
         lib.mce_last_error.argtypes = []
@@ -317,6 +326,80 @@ def mce_peel_noalloc(row_ptr, col, core, rank, order, stream: Optional[int] = No
                                       n, col.numel() // 2, ctypes.c_void_p(core.data_ptr()),
                                       ctypes.c_void_p(rank.data_ptr()), ctypes.c_void_p(order.data_ptr()),
                                       ctypes.c_void_p(s)))
+
+
+MCE_NUM_FEATURES = 16
+MCE_MODEL_PARAMS = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1 + 16 + 16
+
+
+def mce_root_features(h: Handle, raw: bool = False):
+    """Root features as CUDA tensors [n, 16] indexed by input id: float32
+    log2(1 + value), or int32 raw values with raw=True."""
+    import torch
+    n = max(h.n, 1)
+    if raw:
+        t = torch.empty((n, MCE_NUM_FEATURES), dtype=torch.int32, device="cuda")
+        _check(library().mce_root_features(h.ptr, ctypes.c_void_p(t.data_ptr()), None))
+    else:
+        t = torch.empty((n, MCE_NUM_FEATURES), dtype=torch.float32, device="cuda")
+        _check(library().mce_root_features(h.ptr, None, ctypes.c_void_p(t.data_ptr())))
+    return t[: h.n]
+
+
+class Model:
+    """mce_model: the work estimator's parameters (FP32 master, BF16 in use) and Adam state."""
+
+    def __init__(self, params, stream: Optional[int] = None, use_torch_allocator: bool = True):
+        import torch
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (MCE_MODEL_PARAMS,):
+            raise ValueError("need %d parameters" % MCE_MODEL_PARAMS)
+        s, dev = (stream, torch.cuda.current_device()) if stream is not None else _current_stream()
+        self._alloc = _TorchAllocator(dev, s) if use_torch_allocator else None
+        self.ptr = ctypes.c_void_p()
+        _check(library().mce_model_create(p.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                          ctypes.byref(self._alloc.struct) if self._alloc else None,
+                                          ctypes.c_void_p(s), ctypes.byref(self.ptr)))
+
+    def params(self) -> np.ndarray:
+        out = np.zeros(MCE_MODEL_PARAMS, np.float32)
+        _check(library().mce_model_get_params(self.ptr, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float))))
+        return out
+
+    def predict(self, feat):
+        import torch
+        feat = feat.contiguous()
+        out = torch.empty(feat.shape[0], dtype=torch.float32, device="cuda")
+        _check(library().mce_model_predict(self.ptr, ctypes.c_void_p(feat.data_ptr()), feat.shape[0],
+                                           ctypes.c_void_p(out.data_ptr())))
+        return out
+
+    def gradient(self, feat, label):
+        g = np.zeros(MCE_MODEL_PARAMS, np.float32)
+        loss = ctypes.c_float()
+        feat, label = feat.contiguous(), label.contiguous()
+        _check(library().mce_model_gradient(self.ptr, ctypes.c_void_p(feat.data_ptr()),
+                                            ctypes.c_void_p(label.data_ptr()), feat.shape[0],
+                                            g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)), ctypes.byref(loss)))
+        return g, float(loss.value)
+
+    def train_step(self, feat, label, lr: float, want_loss: bool = False):
+        loss = ctypes.c_float()
+        _check(library().mce_model_train_step(self.ptr, ctypes.c_void_p(feat.data_ptr()),
+                                              ctypes.c_void_p(label.data_ptr()), feat.shape[0], lr,
+                                              ctypes.byref(loss) if want_loss else None))
+        return float(loss.value) if want_loss else None
+
+    def close(self):
+        if self.ptr:
+            library().mce_model_destroy(self.ptr)
+            self.ptr = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def mce_destroy(h: Handle):

@@ -1,0 +1,105 @@
+"""The work estimator's kernels against the CPU references (oracle/features.py,
+oracle/mlp.py), and the learned order's effect on results (none) and time.
+
+Tolerances. Features are integers: bit-exact. The network runs in float32
+with BF16 weights; the reference in float64 with the same BF16 weights, so
+the only difference is float32 rounding of ~5,000 multiply-adds per sample:
+outputs of magnitude <= ~40 agree to 1e-3 absolute, and gradients (sums over
+the batch of products of such values) to 1e-3 relative of the largest
+gradient entry.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import gen
+from oracle import features as ofeat
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("needs a CUDA device", allow_module_level=True)
+
+import paper_2212_01473_gb300 as mce  # noqa: E402
+from paper_2212_01473_gb300 import learn  # noqa: E402
+
+GRAPHS = [gen.complete(9), gen.moon_moser(5), gen.worked_example(), gen.gnp(300, 0.08, 2),
+          gen.chung_lu(3000, 12.0, 2.1, 300.0, 3, 10, 20, 4), gen.random_forest(200, 3)]
+
+
+@pytest.mark.parametrize("g", GRAPHS, ids=[g.name or "g" for g in GRAPHS])
+def test_features_match_definition(g):
+    h = mce.mce_create(g.row_ptr, g.col)
+    raw = mce.mce_root_features(h, raw=True).cpu().numpy()
+    flt = mce.mce_root_features(h).cpu().numpy()
+    mce.mce_destroy(h)
+    want = ofeat.root_features(g.row_ptr, g.col)
+    assert np.array_equal(raw.astype(np.int64), want)
+    assert np.allclose(flt, np.log2(1.0 + want.astype(np.float64)), rtol=1e-6, atol=1e-6)
+
+
+def _params(seed):
+    rs = np.random.default_rng(seed)
+    x = rs.normal(2.0, 1.5, (300, 16)).astype(np.float32)
+    p = learn.init_params(x.mean(0), x.std(0), seed)
+    p[omlp.OB1:omlp.OW2] = rs.normal(0, 0.1, 64)
+    p[omlp.OB2:omlp.OW3] = rs.normal(0, 0.1, 64)
+    p[omlp.OB3] = 1.5
+    return p, x, rs.normal(4.0, 2.0, 300).astype(np.float32)
+
+
+def test_predict_matches_reference():
+    p, x, _ = _params(1)
+    m = mce.Model(p)
+    got = m.predict(torch.from_numpy(x).cuda()).cpu().numpy()
+    m.close()
+    want, _ = omlp.forward(p.astype(np.float64), x.astype(np.float64))
+    assert np.allclose(got, want, rtol=0, atol=1e-3)
+
+
+def test_gradient_matches_reference():
+    p, x, t = _params(2)
+    m = mce.Model(p)
+    g, loss = m.gradient(torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda())
+    m.close()
+    lw, gw = omlp.loss_and_grad(p.astype(np.float64), x.astype(np.float64), t.astype(np.float64))
+    assert abs(loss - lw) <= 1e-4 * max(1.0, lw)
+    assert np.all(g[omlp.OMEAN:] == 0)
+    assert np.allclose(g, gw, rtol=0, atol=1e-3 * np.abs(gw).max())
+
+
+def test_training_reduces_loss_and_keeps_results():
+    g = gen.chung_lu(20000, 16.0, 2.1, 1500.0, 4, 20, 30, 21)
+    feat, label = learn.collect(g, light_keep=4000)
+    model, hist = learn.train(feat, label, epochs=6, batch=512, lr=3e-3, log=lambda *a: None)
+    p0 = learn.init_params(feat.double().mean(0).cpu().numpy(), feat.double().std(0).cpu().numpy(), 0)
+    m0 = mce.Model(p0)
+    _, loss0 = m0.gradient(feat, label)
+    m0.close()
+    _, loss1 = model.gradient(feat, label)
+    assert loss1 < 0.5 * loss0
+    # the learned order changes the schedule only
+    h = mce.mce_create(g.row_ptr, g.col)
+    plain = mce.mce_run(h)
+    o = mce.mce_default_opts(order=mce.MCE_ORDER_PRIORITY)
+    pr = learn.priority(model, h)
+    o.root_priority = pr.data_ptr()
+    lrn = mce.mce_run(h, o)
+    mce.mce_destroy(h)
+    model.close()
+    assert (lrn.count, lrn.hash, lrn.tree_nodes) == (plain.count, plain.hash, plain.tree_nodes)
+    assert np.array_equal(lrn.hist, plain.hist)
+
+
+@pytest.mark.skipif(not os.path.exists(learn.DEFAULT_MODEL), reason="no trained model file")
+def test_trained_model_on_held_out_seed():
+    model, meta = learn.load()
+    rows = learn.evaluate(model, families=("chunglu_1m",), seeds=(101,), repeats=2, log=lambda *a: None)
+    model.close()
+    r = rows[0]
+    assert r["spearman"] > 0.5
+    # the learned order must not lose to the plain order by more than noise
+    assert r["ms_learned"] <= 1.10 * r["ms_plain"]

@@ -294,3 +294,57 @@ def test_validate_rejects(bad):
         rp[5] = rp[6] + 1
     assert oracle.validate(g.row_ptr, g.col)
     assert not oracle.validate(rp, col)
+
+
+# ------------------------------------------------ work-estimator references
+
+def test_features_complete_graph_closed_form():
+    from oracle.features import root_features
+    n = 9
+    g = gen.complete(n)
+    f = root_features(g.row_ptr, g.col)
+    for r in range(n):  # K_n: one peel round, rank = id; P0 = later ids, X0 = earlier ids
+        k, x = n - 1 - r, r
+        pairs = k * (k - 1) // 2
+        want = [n - 1, n - 1, k, x, pairs + k * x, pairs, k * x, 65536 if k >= 2 else 0,
+                (n - 1) * (n - 1), k - 1 if k else 0, k - 1 if k else 0, k, n - 1 if k else 0,
+                (n - 1) * k, k if x else 0, 0]
+        assert f[r].tolist() == want, r
+
+
+def test_features_star_and_path():
+    from oracle.features import root_features
+    g = gen.from_edges(6, [(0, i) for i in range(1, 6)])  # star: leaves peel first, centre last
+    f = root_features(g.row_ptr, g.col)
+    assert f[0].tolist()[:4] == [5, 1, 0, 5] and f[0, 8] == 5
+    for leaf in range(1, 6):
+        assert f[leaf].tolist()[:4] == [1, 1, 1, 0] and f[leaf, 8] == 5 and f[leaf, 15] == 0
+
+
+def test_mlp_reference_gradient_matches_finite_differences():
+    from oracle import mlp
+    rs = np.random.default_rng(0)
+    p = rs.normal(0, 0.3, mlp.NPARAMS)
+    p[mlp.OSTD:] = rs.uniform(0.5, 2.0, 16)
+    x = rs.normal(1.0, 1.0, (7, 16))
+    t = rs.normal(3.0, 1.0, 7)
+    loss, g = mlp.loss_and_grad(p, x, t, rounded=False)
+    eps = 1e-6
+    for i in list(range(0, mlp.OMEAN, 97)) + [mlp.OB3, mlp.OW3 + 5, mlp.OB1 + 3]:
+        q = p.copy()
+        q[i] += eps
+        lp = mlp.loss_and_grad(q, x, t, rounded=False)[0]
+        q[i] -= 2 * eps
+        lm = mlp.loss_and_grad(q, x, t, rounded=False)[0]
+        assert abs((lp - lm) / (2 * eps) - g[i]) <= 1e-6 * max(1.0, abs(g[i])), i
+    assert np.all(g[mlp.OMEAN:] == 0)
+
+
+def test_bf16_rounding_reference():
+    from oracle.mlp import bf16_round
+    # exactly representable values stay; halfway cases go to the even neighbour
+    assert bf16_round(np.float32(1.0)) == 1.0
+    assert bf16_round(np.float32(1.0 + 2 ** -8)) == 1.0                  # halfway, even is 1.0
+    assert bf16_round(np.float32(1.0 + 3 * 2 ** -8)) == 1.0 + 2 ** -6    # halfway, even is up
+    assert bf16_round(np.float32(-2.5)) == -2.5
+    assert bf16_round(np.float32(1.0 + 2 ** -7 + 2 ** -9)) == 1.0 + 2 ** -7
