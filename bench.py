@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.05,
                     help="fraction of roots (seeded) the CPU oracle runs for its baseline")
+    ap.add_argument("--no-forms", action="store_true",
+                    help="skip the learned-order and batched comparisons")
     return ap.parse_args()
 
 
@@ -149,6 +151,100 @@ def run_reference(args):
             "e2e": {"value": value, "unit": "cliques/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
     return 0
+
+
+def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf):
+    """Learned root order on the same workload, and the 4096-graph batch run
+    batched (one set of persistent launches, replayed from a CUDA graph) versus
+    graph by graph, all on this GPU."""
+    import numpy as np
+    import torch
+    import gen
+    import paper_2212_01473_gb300 as mce
+    from paper_2212_01473_gb300 import learn
+    forms = {"plain": {"value": value_plain, "unit": "cliques/s"}}
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        ms = []
+        for _ in range(reps):
+            flush_buf.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            out = fn()
+            e1.record(stream)
+            e1.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        return ms, out
+
+    # learned order: features + network + traversal in the step
+    model, meta = learn.load()
+
+    def learned_step():
+        h = mce.mce_create(rp_d, col_d)
+        pr = learn.priority(model, h)
+        o = mce.mce_default_opts(order=mce.MCE_ORDER_PRIORITY)
+        o.root_priority = pr.data_ptr()
+        r = mce.mce_run(h, o)
+        mce.mce_destroy(h)
+        return r
+
+    timed(learned_step, 1)
+    ms, r = timed(learned_step, args.steps)
+    assert r.count == count
+    forms["learned"] = {"value": count * args.steps / (sum(ms) / 1e3), "unit": "cliques/s",
+                        "ms_per_step": sum(ms) / len(ms), "vs_plain": count * args.steps / (sum(ms) / 1e3) / value_plain,
+                        "model": "paper_2212_01473_gb300/work_model.json (%s)" % meta.get("train", "")}
+    model.close()
+
+    # batched versus graph by graph
+    b = gen.workload("batch_4096")
+    gp, rp, col = (torch.from_numpy(x).cuda() for x in (b.graph_ptr, b.row_ptr, b.col))
+
+    def batched_step():
+        h = mce.mce_batch_create(gp, rp, col)
+        per, hist, tot = mce.mce_run_batch(h)
+        mce.mce_destroy(h)
+        return tot
+
+    timed(batched_step, 1)
+    ms_b, tot = timed(batched_step, 2)
+    hb = mce.mce_batch_create(gp, rp, col)
+    tune = mce.mce_autotune(hb, budget_ms=8000.0)
+    mce.mce_prepare(hb, mce.mce_default_opts(tuned=1))
+    mce.mce_run_prepared(hb)
+    ms_r, rr = timed(lambda: mce.mce_run_prepared(hb)[2], 2)
+    assert rr.count == tot.count and rr.hash == tot.hash
+    mce.mce_destroy(hb)
+    parts = []
+    for i in range(len(b.graph_ptr) - 1):
+        a, z = int(b.graph_ptr[i]), int(b.graph_ptr[i + 1])
+        sub_rp = torch.from_numpy((b.row_ptr[a:z + 1] - b.row_ptr[a]).astype(np.int32)).cuda()
+        sub_col = torch.from_numpy((b.col[b.row_ptr[a]:b.row_ptr[z]] - a).astype(np.int32)).cuda()
+        parts.append((sub_rp, sub_col))
+
+    def one_by_one():
+        c = 0
+        for sub_rp, sub_col in parts:
+            h = mce.mce_create(sub_rp, sub_col)
+            c += mce.mce_run(h).count
+            mce.mce_destroy(h)
+        return c
+
+    ms_1, c1 = timed(one_by_one, 1)
+    assert c1 == tot.count
+    v_b = tot.count * len(ms_b) / (sum(ms_b) / 1e3)
+    v_r = tot.count * len(ms_r) / (sum(ms_r) / 1e3)
+    v_1 = c1 / (ms_1[0] / 1e3)
+    forms["batched"] = {"workload": "batch_4096", "maximal_cliques": tot.count,
+                        "value": v_b, "unit": "cliques/s", "ms_per_step": sum(ms_b) / len(ms_b),
+                        "step": "mce_batch_create + mce_run_batch over all 4096 graphs",
+                        "replay_value": v_r, "replay_ms": sum(ms_r) / len(ms_r),
+                        "replay": "autotuned launch settings, run captured once and replayed as one CUDA graph",
+                        "tuning": tune,
+                        "one_by_one_value": v_1, "one_by_one_ms": ms_1[0],
+                        "vs_one_by_one": v_b / v_1}
+    return forms
 
 
 def run_ours(args):
@@ -278,6 +374,8 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e, "roofline": roofline}
     if golden:
         line["config"]["oracle_match"] = golden.get("count") == count and golden.get("hash") == "0x%016x" % results[-1].hash
+    if rank == 0 and world == 1 and not args.no_forms:
+        line["forms"] = measure_forms(args, rp_d, col_d, count, value, flush_buf)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_sample)
     if rank == 0:

@@ -111,6 +111,8 @@ typedef struct {
      * NULL = all vertices. An id outside [0, n) fails with MCE_EINVAL. */
     const int32_t *roots;
     int64_t n_roots;
+    int32_t tuned;         /* 1 = use the per-width-class settings mce_autotune chose for this handle */
+    int32_t reserved;
 } mce_opts;
 
 typedef struct {
@@ -173,6 +175,29 @@ int mce_run(mce_graph *g, const mce_opts *opts, mce_result *out, uint64_t *hist,
  */
 int mce_run_batch(mce_graph *g, const mce_opts *opts, mce_result *per_graph, uint64_t *hist,
                   int32_t hist_len, mce_result *total);
+
+/*
+ * Autotuner: for every width class, times the whole class with a few launch
+ * settings (donation threshold |P0|max/16, /8, /4; donation rule EITHER,
+ * PAPER, ANY; full or one-block-per-SM grid) within about budget_ms of device
+ * time, and keeps the fastest per class in the handle. Runs with
+ * opts.tuned = 1 then use them. Results are never affected.
+ */
+int mce_autotune(mce_graph *g, const mce_opts *base, double budget_ms);
+/* The chosen settings, HOST arrays of 9 width classes (0 / -1 = default). */
+int mce_get_tuning(const mce_graph *g, int32_t *donate_min_p, int32_t *donate_policy, int32_t *blocks);
+
+/*
+ * Capture one complete run (every memset and kernel of mce_run / mce_run_batch
+ * with these opts: roots of |P0| = 0, then each width class, heaviest first)
+ * into a CUDA graph kept by the handle; mce_run_prepared replays it with one
+ * graph launch and one read-back. The opts' device buffers (per-root outputs,
+ * priorities, subsets) must stay valid while the capture is kept. A new
+ * mce_prepare or mce_destroy releases it.
+ */
+int mce_prepare(mce_graph *g, const mce_opts *opts);
+int mce_run_prepared(mce_graph *g, mce_result *per_graph, uint64_t *hist, int32_t hist_len,
+                     mce_result *total);
 
 /* Handle facts (host values): n, m, G, degeneracy, max degree. Any may be NULL. */
 int mce_graph_info(const mce_graph *g, int32_t *n, int64_t *m, int32_t *G, int32_t *degeneracy,
@@ -286,6 +311,12 @@ int mce_model_gradient(mce_model *m, const float *feat, const float *label, int3
 int mce_model_train_step(mce_model *m, const float *feat, const float *label, int32_t batch, float lr,
                          float *loss);
 void mce_model_destroy(mce_model *m);
+
+/* The learned order's input in one call, on the handle's stream: features and
+ * predictions for the roots with |P0| >= min_p only (the others are cheap and
+ * get -1, the lowest priority), written to DEVICE priority[n] by input id,
+ * ready for opts.root_priority with MCE_ORDER_PRIORITY. */
+int mce_predict_priority(mce_graph *g, mce_model *m, int32_t min_p, float *priority);
 
 /* Release the handle and all its device memory. NULL is a no-op. */
 void mce_destroy(mce_graph *g);

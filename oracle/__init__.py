@@ -32,6 +32,7 @@ def _load():
                                          i32p, u64p, u64p, u64p]
         lib.oracle_mce_work.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                         i32p, ctypes.c_int64, u64p, u64p]
+        lib.oracle_multipartite.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, u64p, u64p]
         lib.oracle_clique_hash.argtypes = [i32p, ctypes.c_int32]
         lib.oracle_clique_hash.restype = ctypes.c_uint64
         lib.oracle_default_threads.restype = ctypes.c_int32
@@ -138,6 +139,14 @@ def work(row_ptr, col, mode: int = PIVOT_IP, threads: int = 0, roots=None):
     if rc != 0:
         raise RuntimeError("oracle_mce_work failed: %d" % rc)
     return rn[:n], rw[:n]
+
+
+def multipartite(first: int, parts: int, part_size: int):
+    """(count, hash) of the maximal cliques of a complete multipartite graph."""
+    c, h = ctypes.c_uint64(), ctypes.c_uint64()
+    if _load().oracle_multipartite(first, parts, part_size, ctypes.byref(c), ctypes.byref(h)) != 0:
+        raise ValueError("bad multipartite arguments")
+    return int(c.value), int(h.value)
 
 
 def clique_hash(ids) -> int:

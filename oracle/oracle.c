@@ -433,3 +433,37 @@ int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32
                  &max_size, NULL, NULL, root_nodes, root_work);
     return rc == 5 ? 0 : rc; /* no histogram was asked for */
 }
+
+/*
+ * Maximal cliques of a complete multipartite graph whose parts are the
+ * consecutive id ranges [first + i*part_size, first + (i+1)*part_size),
+ * i < parts: exactly the sets holding one vertex of every part (every
+ * transversal is a clique; any other clique misses a part and extends by a
+ * vertex of it). Enumerates all part_size^parts of them and sums h(C).
+ */
+int oracle_multipartite(int32_t first, int32_t parts, int32_t part_size, uint64_t *count, uint64_t *hash) {
+    if (parts < 0 || part_size < 1 || parts > 64) return 1;
+    int32_t choice[64];
+    uint64_t prefix[65];
+    uint64_t c = 0, h = 0;
+    if (parts == 0) { *count = 0; *hash = 0; return 0; }
+    for (int32_t i = 0; i < parts; i++) choice[i] = 0;
+    prefix[0] = 0;
+    for (int32_t i = 0; i < parts; i++)
+        prefix[i + 1] = prefix[i] + mix64((uint64_t)(int64_t)(first + i * part_size) + 1ull);
+    for (;;) {
+        c++;
+        h += mix64(prefix[parts] + (uint64_t)parts * 0x9E3779B97F4A7C15ull);
+        /* odometer: advance the last part first */
+        int32_t i = parts - 1;
+        while (i >= 0 && choice[i] == part_size - 1) i--;
+        if (i < 0) break;
+        choice[i]++;
+        for (int32_t j = i + 1; j < parts; j++) choice[j] = 0;
+        for (int32_t j = i; j < parts; j++)
+            prefix[j + 1] = prefix[j] + mix64((uint64_t)(int64_t)(first + j * part_size + choice[j]) + 1ull);
+    }
+    *count = c;
+    *hash = h;
+    return 0;
+}

@@ -90,6 +90,11 @@ int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32
                     int32_t nthreads, const int32_t *roots, int64_t n_roots, uint64_t *root_nodes,
                     uint64_t *root_work);
 
+/* count and hash of the maximal cliques of a complete multipartite graph with
+ * `parts` parts of `part_size` consecutive ids starting at `first` (Moon-Moser
+ * graphs have part_size 3): the transversals, enumerated directly. */
+int oracle_multipartite(int32_t first, int32_t parts, int32_t part_size, uint64_t *count, uint64_t *hash);
+
 /* h(C) for a clique given by input ids (any order) */
 uint64_t oracle_clique_hash(const int32_t *ids, int32_t k);
 

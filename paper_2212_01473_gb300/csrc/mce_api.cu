@@ -159,6 +159,16 @@ int mce::set_last_error(int code, const char *msg) {
         }                                                                                    \
     } while (0)
 
+// Launch settings of one width class chosen by mce_autotune (0 / -1 = default).
+struct Tuned {
+    int dmp = 0;
+    int policy = -1;
+    int blocks = 0;
+};
+
+struct RunPlan;
+static void free_plan(mce_graph *g, RunPlan *P);
+
 struct mce_graph {
     int32_t n = 0;
     int64_t m = 0;
@@ -182,6 +192,10 @@ struct mce_graph {
     int64_t peel_rounds = 0;
     uint64_t create_launches = 0;  // kernels launched by create
     mce_stats last{};              // facts of the last run
+    Tuned tuned[kNumClasses];      // per width class, from mce_autotune
+    bool tuned_valid = false;
+    struct RunPlan *prepared = nullptr;  // mce_prepare
+    cudaGraphExec_t prepared_exec = nullptr;
 };
 
 static void *dalloc(mce_graph *g, size_t bytes) {
@@ -209,7 +223,10 @@ static T *dnew(mce_graph *g, size_t count, std::vector<void *> *track) {
     return p;
 }
 
+static void release_prepared(mce_graph *g);
+
 static void release(mce_graph *g) {
+    release_prepared(g);
     void *ps[] = {g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->rank,
                   g->core,    g->outdeg,  g->gid,    g->mixid,  g->scratch};
     for (void *p : ps) dfree(g, p);
@@ -451,57 +468,90 @@ static int grow_scratch(mce_graph *g, size_t bytes) {
     return MCE_OK;
 }
 
-// Shared implementation of mce_run / mce_run_batch.
-static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph, uint64_t *hist,
-                    int32_t hist_len, mce_result *total) {
-    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
-    mce_opts opts;
-    mce_default_opts(&opts);
-    if (opts_in) {
-        if (opts_in->struct_size != (int32_t)sizeof(mce_opts)) return fail(MCE_EINVAL, "opts.struct_size mismatch");
-        opts = *opts_in;
-    }
-    if (opts.pivot < 0 || opts.pivot > 2) return fail(MCE_EINVAL, "bad opts.pivot");
-    if (opts.order != MCE_ORDER_PLAIN && opts.order != MCE_ORDER_PRIORITY) return fail(MCE_EINVAL, "bad opts.order");
-    if (opts.order == MCE_ORDER_PRIORITY && !opts.root_priority)
-        return fail(MCE_EINVAL, "MCE_ORDER_PRIORITY needs opts.root_priority");
-    if (opts.pivot == MCE_PIVOT_IPX) return fail(MCE_EINVAL, "IPX pivoting is not available in this build");
-    if (opts.donate_min_p < 0) return fail(MCE_EINVAL, "opts.donate_min_p < 0");
-    if (opts.donate_policy < 0 || opts.donate_policy > 2) return fail(MCE_EINVAL, "bad opts.donate_policy");
-    if (opts.timeout_ms <= 0) opts.timeout_ms = 60000;
-    if (hist && hist_len < 0) return fail(MCE_EINVAL, "hist_len < 0");
-    const int G = g->G;
-    const int HL = g->d + 2;  // every maximal clique has at most d + 1 vertices
-    int rc = MCE_OK;
-    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
-    std::vector<unsigned long long> hcnt(G), hhash(G), hhist((size_t)G * HL);
-    unsigned long long hmisc[4] = {0, 0, 0, 0};
-    int hflags[4] = {0, 0, 0, 0};
+// ------------------------------------------------------------------ runs
+//
+// A run is planned (root lists, launch shapes, scratch, outputs), enqueued
+// (device work only: memsets and kernels, so it can be captured into a CUDA
+// graph), then collected (results copied back and checked).
+
+__global__ void k_init_ctl(int *ctl, int groups) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) ctl[CTL_ACTIVE] = groups;
+}
+
+struct RunPlan {
+    mce_opts opts{};
+    int G = 1, HL = 2;
+    unsigned long long *obuf = nullptr;
+    size_t obuf_bytes = 0;
     DevGraph dg{};
     DevOut dout{};
-    // outputs: count[G], hash[G], hist[G*HL], nodes, donations | max_size, status,
-    // phase cycles and counts
-    const size_t out_words64 = (size_t)2 * G + (size_t)G * HL + 4 + 2 * kNumPhases;
-    mce_stats st{};
-    std::vector<cudaEvent_t> cev;
-    uint64_t launches = 0;
-    const uint64_t launch_base = launch_counter();
-    // roots to enumerate per width class (all, or the subset opts.roots selects)
-    const int32_t *lists[kNumClasses + 1];
-    int32_t counts[kNumClasses + 1];
-    for (int c = 0; c <= kNumClasses; c++) {
-        lists[c] = g->class_roots[c];
-        counts[c] = g->class_count[c];
+    const int32_t *lists[kNumClasses + 1] = {};
+    int32_t counts[kNumClasses + 1] = {};
+    struct Cls {
+        int c = 0, rows = 0, groups = 0;
+        ClassLaunch L{};
+        ClassArgs a{};
+    } cls[kNumClasses];
+    int ncls = 0;
+    unsigned trivial_blocks = 0;
+    std::vector<void *> tmp;
+    std::vector<cudaEvent_t> ev;  // [0] start, [1] end, then one pair per launch
+    uint64_t launch_base = 0;
+    uint64_t plan_launches = 0;  // kernels run while planning (subsets, priority order)
+    uint64_t run_launches = 0;   // kernels of one enqueued run
+    bool replay = false;         // collected after a CUDA graph replay
+    bool capturing = false;      // enqueued inside a stream capture
+};
+
+// Timing events: inside a capture they must be external record nodes to stay
+// in the graph; outside a capture the plain record is the valid form.
+static cudaError_t record(cudaEvent_t e, cudaStream_t s, bool capturing) {
+    return capturing ? cudaEventRecordWithFlags(e, s, cudaEventRecordExternal) : cudaEventRecord(e, s);
+}
+
+static void free_plan(mce_graph *g, RunPlan *P) {
+    if (!P) return;
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (cudaEvent_t e : P->ev) cudaEventDestroy(e);
+    for (void *q : P->tmp) dfree(g, q);
+    dfree(g, P->obuf);
+    delete P;
+}
+
+// class_mask: bit c set = launch width class c (bit kNumClasses: roots with |P0| = 0)
+static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, const Tuned *tune_override,
+                    RunPlan **out) {
+    *out = nullptr;
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    RunPlan *P = new RunPlan();
+    mce_opts &opts = P->opts;
+    mce_default_opts(&opts);
+    int rc = MCE_OK;
+    if (opts_in) {
+        if (opts_in->struct_size != (int32_t)sizeof(mce_opts)) { delete P; return fail(MCE_EINVAL, "opts.struct_size mismatch"); }
+        opts = *opts_in;
     }
-    std::vector<void *> run_tmp;
-    unsigned long long *obuf = (unsigned long long *)dalloc(g, out_words64 * 8 + 64);
-    if (!obuf) return fail(MCE_ENOMEM, "device allocation of outputs failed");
-    CK(cudaMemsetAsync(obuf, 0, out_words64 * 8 + 64, g->stream));
-    if (opts.root_count) CK(cudaMemsetAsync(opts.root_count, 0, (size_t)g->n * 8, g->stream));
-    if (opts.root_hash) CK(cudaMemsetAsync(opts.root_hash, 0, (size_t)g->n * 8, g->stream));
-    if (opts.root_nodes) CK(cudaMemsetAsync(opts.root_nodes, 0, (size_t)g->n * 8, g->stream));
-    CK(cudaEventCreate(&ev0));
-    CK(cudaEventCreate(&ev1));
+    if (opts.pivot < 0 || opts.pivot > 2) rc = fail(MCE_EINVAL, "bad opts.pivot");
+    else if (opts.order != MCE_ORDER_PLAIN && opts.order != MCE_ORDER_PRIORITY) rc = fail(MCE_EINVAL, "bad opts.order");
+    else if (opts.order == MCE_ORDER_PRIORITY && !opts.root_priority) rc = fail(MCE_EINVAL, "MCE_ORDER_PRIORITY needs opts.root_priority");
+    else if (opts.pivot == MCE_PIVOT_IPX) rc = fail(MCE_EINVAL, "IPX pivoting is not available in this build");
+    else if (opts.donate_min_p < 0) rc = fail(MCE_EINVAL, "opts.donate_min_p < 0");
+    else if (opts.donate_policy < 0 || opts.donate_policy > 2) rc = fail(MCE_EINVAL, "bad opts.donate_policy");
+    else if (opts.roots && opts.n_roots < 0) rc = fail(MCE_EINVAL, "opts.n_roots < 0");
+    else if (opts.tuned && !g->tuned_valid) rc = fail(MCE_EINVAL, "opts.tuned set but mce_autotune has not run on this handle");
+    if (rc != MCE_OK) { delete P; return rc; }
+    if (opts.timeout_ms <= 0) opts.timeout_ms = 60000;
+    const int G = g->G;
+    P->G = G;
+    P->HL = g->d + 2;  // every maximal clique has at most d + 1 vertices
+    P->launch_base = launch_counter();
+    // outputs: count[G], hash[G], hist[G*HL], nodes, donations | max_size, status, phase counters
+    const size_t out_words64 = (size_t)2 * G + (size_t)G * P->HL + 4 + 2 * kNumPhases;
+    P->obuf_bytes = out_words64 * 8 + 64;
+    P->obuf = (unsigned long long *)dalloc(g, P->obuf_bytes);
+    if (!P->obuf) { free_plan(g, P); return fail(MCE_ENOMEM, "device allocation of outputs failed"); }
+    DevGraph &dg = P->dg;
+    DevOut &dout = P->dout;
     dg.n = g->n;
     dg.G = G;
     dg.out_ptr = g->out_ptr;
@@ -511,11 +561,11 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     dg.order = g->order;
     dg.mixid = g->mixid;
     dg.gid = g->gid;
-    dout.count = obuf;
-    dout.hash = obuf + G;
-    dout.hist = obuf + 2 * G;
-    dout.hist_len = HL;
-    dout.nodes = obuf + 2 * G + (size_t)G * HL;
+    dout.count = P->obuf;
+    dout.hash = P->obuf + G;
+    dout.hist = P->obuf + 2 * G;
+    dout.hist_len = P->HL;
+    dout.nodes = P->obuf + 2 * G + (size_t)G * P->HL;
     dout.donations = dout.nodes + 1;
     dout.max_size = (int *)(dout.nodes + 2);
     dout.status = dout.max_size + 1;
@@ -524,8 +574,12 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     dout.root_count = (unsigned long long *)opts.root_count;
     dout.root_hash = (unsigned long long *)opts.root_hash;
     dout.root_nodes = (unsigned long long *)opts.root_nodes;
-    st.struct_size = (int32_t)sizeof(mce_stats);
-    if (opts.roots && opts.n_roots < 0) { rc = fail(MCE_EINVAL, "opts.n_roots < 0"); goto cleanup; }
+    for (int c = 0; c <= kNumClasses; c++) {
+        const bool on = (class_mask >> c) & 1u;
+        P->lists[c] = g->class_roots[c];
+        P->counts[c] = on ? g->class_count[c] : 0;
+    }
+    size_t need_words = 0;
     if (opts.roots && g->n > 0) {
         int maxc = 1;
         for (int c = 0; c <= kNumClasses; c++) maxc = std::max(maxc, g->class_count[c]);
@@ -533,8 +587,9 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         int32_t *flags = (int32_t *)dalloc(g, (size_t)maxc * 4);
         int32_t *pos = (int32_t *)dalloc(g, ((size_t)maxc + 1) * 4);
         int32_t *stmp = (int32_t *)dalloc(g, (size_t)scan_tmp_words(maxc + 1) * 4);
-        for (void *q : {(void *)mask, (void *)flags, (void *)pos, (void *)stmp}) run_tmp.push_back(q);
+        for (void *q : {(void *)mask, (void *)flags, (void *)pos, (void *)stmp}) P->tmp.push_back(q);
         if (!mask || !flags || !pos || !stmp) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+        CK(cudaMemsetAsync(dout.status, 0, 4, g->stream));
         CK(cudaMemsetAsync(mask, 0, (size_t)g->n * 4, g->stream));
         CK(launch_mark_roots(opts.roots, opts.n_roots, g->rank, g->n, mask, dout.status, g->stream));
         int hst = 0;
@@ -542,108 +597,144 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         CK(cudaStreamSynchronize(g->stream));
         if (hst) { rc = fail(MCE_EINVAL, "opts.roots holds an id outside [0, n)"); goto cleanup; }
         for (int c = 0; c <= kNumClasses; c++) {
-            if (counts[c] == 0) continue;
-            int32_t *out = (int32_t *)dalloc(g, (size_t)counts[c] * 4);
-            run_tmp.push_back(out);
-            if (!out) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
-            CK(launch_subset(lists[c], counts[c], mask, flags, pos, stmp, out, g->stream));
+            if (P->counts[c] == 0) continue;
+            int32_t *o = (int32_t *)dalloc(g, (size_t)P->counts[c] * 4);
+            P->tmp.push_back(o);
+            if (!o) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+            CK(launch_subset(P->lists[c], P->counts[c], mask, flags, pos, stmp, o, g->stream));
             int kept = 0;
-            CK(cudaMemcpyAsync(&kept, pos + counts[c], 4, cudaMemcpyDeviceToHost, g->stream));
+            CK(cudaMemcpyAsync(&kept, pos + P->counts[c], 4, cudaMemcpyDeviceToHost, g->stream));
             CK(cudaStreamSynchronize(g->stream));
-            lists[c] = out;
-            counts[c] = kept;
+            P->lists[c] = o;
+            P->counts[c] = kept;
         }
     }
     if (opts.order == MCE_ORDER_PRIORITY && g->n > 0) {
         int *hb = (int *)dalloc(g, 256 * sizeof(int));
-        run_tmp.push_back(hb);
+        P->tmp.push_back(hb);
         if (!hb) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
         for (int c = 0; c < kNumClasses; c++) {
-            if (counts[c] == 0) continue;
-            int32_t *out = (int32_t *)dalloc(g, (size_t)counts[c] * 4);
-            run_tmp.push_back(out);
-            if (!out) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
-            CK(launch_priority_order(lists[c], counts[c], g->order, opts.root_priority, hb, out, g->stream));
-            lists[c] = out;
+            if (P->counts[c] == 0) continue;
+            int32_t *o = (int32_t *)dalloc(g, (size_t)P->counts[c] * 4);
+            P->tmp.push_back(o);
+            if (!o) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+            CK(launch_priority_order(P->lists[c], P->counts[c], g->order, opts.root_priority, hb, o, g->stream));
+            P->lists[c] = o;
         }
     }
-    CK(cudaEventRecord(ev0, g->stream));
-    if (counts[kNumClasses] > 0) {
-        const int nr = counts[kNumClasses];
-        const unsigned nb = (unsigned)std::min<int64_t>(4096, ((int64_t)nr + 255) / 256);
-        cudaEvent_t a0, a1;
-        CK(cudaEventCreate(&a0));
-        cev.push_back(a0);
-        CK(cudaEventCreate(&a1));
-        cev.push_back(a1);
-        CK(cudaEventRecord(a0, g->stream));
-        k_trivial_roots<<<nb, 256, 0, g->stream>>>(dg, dout, lists[kNumClasses], nr);
-        count_launch();
-        CK(cudaGetLastError());
-        CK(cudaEventRecord(a1, g->stream));
-        launches++;
-        const int k = st.n_classes++;
-        st.class_wp[k] = 0;
-        st.class_roots[k] = nr;
-        st.class_blocks[k] = (int32_t)nb;
-    }
-    // heaviest width classes first
+    if (P->counts[kNumClasses] > 0)
+        P->trivial_blocks = (unsigned)std::min<int64_t>(4096, ((int64_t)P->counts[kNumClasses] + 255) / 256);
+    // width classes, heaviest first: launch shapes, then one scratch for all
     for (int c = kNumClasses - 1; c >= 0; c--) {
-        if (counts[c] == 0) continue;
-        const int rows = g->class_rows[c];
-        ClassLaunch L{};
-        CK(plan_class_wp(class_wp(c), rows, g->sm_count, g->smem_optin, opts.blocks, g->gid == nullptr, &L));
-        const int groups = L.blocks * (L.warps_per_block / L.gw);
-        const size_t aw = arena_words(L.wp, rows, g->class_x[c], L.a_global, stack_in_smem(L.wp));
-        const int mail_words = 4 + 3 * L.wp;
-        const size_t ctl_words = CTL_NCTL, idle_words = ((size_t)groups + 31) / 32;
-        const size_t flag_words = (size_t)groups * kMailFlagStride;
-        const size_t total_words = aw * groups + ctl_words + idle_words + flag_words + (size_t)groups * mail_words + 64;
-        if ((rc = grow_scratch(g, total_words * 4)) != MCE_OK) goto cleanup;
-        uint32_t *sw = (uint32_t *)g->scratch;
-        ClassArgs a{};
-        a.roots = lists[c];
-        a.n_roots = counts[c];
-        a.rows_cap = rows;
+        if (P->counts[c] == 0) continue;
+        RunPlan::Cls &k = P->cls[P->ncls++];
+        const Tuned *t = tune_override ? &tune_override[c] : (opts.tuned ? &g->tuned[c] : nullptr);
+        k.c = c;
+        k.rows = g->class_rows[c];
+        const int blocks = (t && t->blocks > 0) ? t->blocks : opts.blocks;
+        CK(plan_class_wp(class_wp(c), k.rows, g->sm_count, g->smem_optin, blocks, g->gid == nullptr, &k.L));
+        k.groups = k.L.blocks * (k.L.warps_per_block / k.L.gw);
+        const size_t aw = arena_words(k.L.wp, k.rows, g->class_x[c], k.L.a_global, stack_in_smem(k.L.wp));
+        const size_t idle_words = ((size_t)k.groups + 31) / 32;
+        const size_t flag_words = (size_t)k.groups * kMailFlagStride;
+        const int mail_words = 4 + 3 * k.L.wp;
+        const size_t words = aw * k.groups + CTL_NCTL + idle_words + flag_words + (size_t)k.groups * mail_words + 64;
+        need_words = std::max(need_words, words);
+        ClassArgs &a = k.a;
+        a.roots = P->lists[c];
+        a.n_roots = P->counts[c];
+        a.rows_cap = k.rows;
         a.x_cap = g->class_x[c];
         a.pivot_ipx = 0;
         a.worker_list = opts.worker_list ? 1 : 0;
         // 0 = automatic: a donated child must have at least 1/8 of the
         // class's widest root set, and never fewer than 10 candidates (Sec. III-C)
-        a.donate_min_p = opts.donate_min_p > 0 ? opts.donate_min_p : std::max(10, rows / 8);
-        a.donate_policy = opts.donate_policy;
+        const int dmp = (t && t->dmp > 0) ? t->dmp : opts.donate_min_p;
+        a.donate_min_p = dmp > 0 ? dmp : std::max(10, k.rows / 8);
+        a.donate_policy = (t && t->policy >= 0) ? t->policy : opts.donate_policy;
         a.root_chunk = 1;
         a.stats = opts.stats ? 1 : 0;
         a.timeout_ns = (uint64_t)opts.timeout_ms * 1000000ull;
-        a.arena = sw;
         a.arena_words_per_group = aw;
-        a.ctl = (int *)(sw + aw * groups);
-        a.idle_bits = (unsigned *)(a.ctl + ctl_words);
-        a.mail_flag = (int *)(a.idle_bits + idle_words);
-        a.mail = (uint32_t *)(a.mail_flag + flag_words);
         a.mail_words = mail_words;
-        CK(cudaMemsetAsync(a.ctl, 0, (ctl_words + idle_words + flag_words) * 4, g->stream));
-        int hctl[CTL_NCTL] = {0};
-        hctl[CTL_ACTIVE] = groups;
-        CK(cudaMemcpyAsync(a.ctl, hctl, sizeof hctl, cudaMemcpyHostToDevice, g->stream));
-        cudaEvent_t a0, a1;
-        CK(cudaEventCreate(&a0));
-        cev.push_back(a0);
-        CK(cudaEventCreate(&a1));
-        cev.push_back(a1);
-        CK(cudaEventRecord(a0, g->stream));
-        CK(launch_class_wp(L, dg, dout, a, rows, g->stream));
-        CK(cudaEventRecord(a1, g->stream));
-        launches++;
-        const int k = st.n_classes++;
-        st.class_wp[k] = L.wp;
-        st.class_roots[k] = counts[c];
-        st.class_rows[k] = rows;
-        st.class_blocks[k] = L.blocks;
-        st.class_groups[k] = groups;
-        st.class_group_warps[k] = L.gw;
     }
-    CK(cudaEventRecord(ev1, g->stream));
+    if ((rc = grow_scratch(g, need_words * 4)) != MCE_OK) goto cleanup;
+    for (int i = 0; i < P->ncls; i++) {
+        RunPlan::Cls &k = P->cls[i];
+        uint32_t *sw = (uint32_t *)g->scratch;
+        const size_t idle_words = ((size_t)k.groups + 31) / 32;
+        const size_t flag_words = (size_t)k.groups * kMailFlagStride;
+        k.a.arena = sw;
+        k.a.ctl = (int *)(sw + k.a.arena_words_per_group * k.groups);
+        k.a.idle_bits = (unsigned *)(k.a.ctl + CTL_NCTL);
+        k.a.mail_flag = (int *)(k.a.idle_bits + idle_words);
+        k.a.mail = (uint32_t *)(k.a.mail_flag + flag_words);
+    }
+    {
+        const int nev = 2 + 2 * (P->ncls + (P->trivial_blocks ? 1 : 0));
+        for (int i = 0; i < nev; i++) {
+            cudaEvent_t e;
+            CK(cudaEventCreate(&e));
+            P->ev.push_back(e);
+        }
+    }
+    P->plan_launches = launch_counter() - P->launch_base;
+    *out = P;
+    return MCE_OK;
+cleanup:
+    free_plan(g, P);
+    return rc;
+}
+
+// Device work of a planned run; no host synchronisation (capturable).
+static int enqueue_run(mce_graph *g, RunPlan *P) {
+    int rc = MCE_OK;
+    const uint64_t base = launch_counter();
+    const mce_opts &opts = P->opts;
+    cudaStream_t s = g->stream;
+    int e = 2;
+    CK(cudaMemsetAsync(P->obuf, 0, P->obuf_bytes, s));
+    if (opts.root_count) CK(cudaMemsetAsync(opts.root_count, 0, (size_t)g->n * 8, s));
+    if (opts.root_hash) CK(cudaMemsetAsync(opts.root_hash, 0, (size_t)g->n * 8, s));
+    if (opts.root_nodes) CK(cudaMemsetAsync(opts.root_nodes, 0, (size_t)g->n * 8, s));
+    CK(record(P->ev[0], s, P->capturing));
+    if (P->trivial_blocks) {
+        CK(record(P->ev[e++], s, P->capturing));
+        k_trivial_roots<<<P->trivial_blocks, 256, 0, s>>>(P->dg, P->dout, P->lists[kNumClasses],
+                                                          P->counts[kNumClasses]);
+        count_launch();
+        CK(cudaGetLastError());
+        CK(record(P->ev[e++], s, P->capturing));
+    }
+    for (int i = 0; i < P->ncls; i++) {
+        RunPlan::Cls &k = P->cls[i];
+        const size_t idle_words = ((size_t)k.groups + 31) / 32;
+        const size_t flag_words = (size_t)k.groups * kMailFlagStride;
+        CK(cudaMemsetAsync(k.a.ctl, 0, (CTL_NCTL + idle_words + flag_words) * 4, s));
+        k_init_ctl<<<1, 32, 0, s>>>(k.a.ctl, k.groups);
+        count_launch();
+        CK(record(P->ev[e++], s, P->capturing));
+        CK(launch_class_wp(k.L, P->dg, P->dout, k.a, k.rows, s));
+        count_launch();
+        CK(record(P->ev[e++], s, P->capturing));
+    }
+    CK(record(P->ev[1], s, P->capturing));
+    P->run_launches = launch_counter() - base;
+cleanup:
+    return rc;
+}
+
+// Copy results back, check the device status, fill the caller's outputs.
+static int collect_run(mce_graph *g, RunPlan *P, mce_result *per_graph, uint64_t *hist, int32_t hist_len,
+                       mce_result *total) {
+    int rc = MCE_OK;
+    const int G = P->G, HL = P->HL;
+    const DevOut &dout = P->dout;
+    std::vector<unsigned long long> hcnt(G), hhash(G), hhist((size_t)G * HL);
+    unsigned long long hmisc[2] = {0, 0};
+    int hflags[2] = {0, 0};
+    mce_stats st{};
+    st.struct_size = (int32_t)sizeof(mce_stats);
     CK(cudaMemcpyAsync(hcnt.data(), dout.count, (size_t)G * 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaMemcpyAsync(hhash.data(), dout.hash, (size_t)G * 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaMemcpyAsync(hhist.data(), dout.hist, (size_t)G * HL * 8, cudaMemcpyDeviceToHost, g->stream));
@@ -651,27 +742,49 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
     CK(cudaMemcpyAsync(hflags, dout.max_size, 2 * 4, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaMemcpyAsync(st.phase_cycles, dout.phase_cycles, 2 * kNumPhases * 8, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
-    for (int k = 0; k < st.n_classes; k++) {
-        float cms = 0;
-        CK(cudaEventElapsedTime(&cms, cev[2 * k], cev[2 * k + 1]));
-        st.class_ms[k] = cms;
+    {
+        int e = 2;
+        if (P->trivial_blocks) {
+            const int k = st.n_classes++;
+            float cms = 0;
+            CK(cudaEventElapsedTime(&cms, P->ev[e], P->ev[e + 1]));
+            e += 2;
+            st.class_wp[k] = 0;
+            st.class_roots[k] = P->counts[kNumClasses];
+            st.class_blocks[k] = (int32_t)P->trivial_blocks;
+            st.class_ms[k] = cms;
+        }
+        for (int i = 0; i < P->ncls; i++) {
+            const RunPlan::Cls &c = P->cls[i];
+            const int k = st.n_classes++;
+            float cms = 0;
+            CK(cudaEventElapsedTime(&cms, P->ev[e], P->ev[e + 1]));
+            e += 2;
+            st.class_wp[k] = c.L.wp;
+            st.class_roots[k] = P->counts[c.c];
+            st.class_rows[k] = c.rows;
+            st.class_blocks[k] = c.L.blocks;
+            st.class_groups[k] = c.groups;
+            st.class_group_warps[k] = c.L.gw;
+            st.class_ms[k] = cms;
+        }
     }
-    st.kernel_launches = g->create_launches + (launch_counter() - launch_base) + launches;
+    st.kernel_launches = g->create_launches + (P->replay ? 0 : P->plan_launches) + P->run_launches;
     st.peel_rounds = g->peel_rounds;
     g->last = st;
-    if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms", (long long)opts.timeout_ms); goto cleanup; }
+    if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms", (long long)P->opts.timeout_ms); goto cleanup; }
     if (hflags[1] & ST_OVERFLOW) { rc = fail(MCE_ECUDA, "internal capacity exceeded in the traversal"); goto cleanup; }
     {
         float ms = 0;
-        CK(cudaEventElapsedTime(&ms, ev0, ev1));
+        CK(cudaEventElapsedTime(&ms, P->ev[0], P->ev[1]));
         mce_result tot{};
         for (int gi = 0; gi < G; gi++) {
             mce_result r{};
             r.count = hcnt[gi];
             r.hash = hhash[gi];
             int mx = 0;
-            for (int s = HL - 1; s > 0; s--)
-                if (hhist[(size_t)gi * HL + s]) { mx = s; break; }
+            for (int sz = HL - 1; sz > 0; sz--)
+                if (hhist[(size_t)gi * HL + sz]) { mx = sz; break; }
             r.max_size = mx;
             r.degeneracy = g->d;
             r.ms_prep = g->ms_prep;
@@ -693,19 +806,134 @@ static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph
         if (total) *total = tot;
         if (hist && hist_len > 0) {
             for (int gi = 0; gi < G; gi++)
-                for (int s = 0; s < hist_len; s++)
-                    hist[(size_t)gi * hist_len + s] = s < HL ? hhist[(size_t)gi * HL + s] : 0ull;
+                for (int sz = 0; sz < hist_len; sz++)
+                    hist[(size_t)gi * hist_len + sz] = sz < HL ? hhist[(size_t)gi * HL + sz] : 0ull;
         }
         if (hist && hist_len <= tot.max_size) rc = fail(MCE_ERANGE, "hist_len %d <= max clique size %d", hist_len, tot.max_size);
     }
 cleanup:
-    if (g->stream) cudaStreamSynchronize(g->stream);
-    for (cudaEvent_t e : cev) cudaEventDestroy(e);
-    for (void *q : run_tmp) dfree(g, q);
-    dfree(g, obuf);
-    if (ev0) cudaEventDestroy(ev0);
-    if (ev1) cudaEventDestroy(ev1);
     return rc;
+}
+
+constexpr unsigned kAllClasses = (1u << (kNumClasses + 1)) - 1u;
+
+static int run_impl(mce_graph *g, const mce_opts *opts_in, mce_result *per_graph, uint64_t *hist,
+                    int32_t hist_len, mce_result *total) {
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    if (hist && hist_len < 0) return fail(MCE_EINVAL, "hist_len < 0");
+    RunPlan *P = nullptr;
+    int rc = plan_run(g, opts_in, kAllClasses, nullptr, &P);
+    if (rc != MCE_OK) return rc;
+    rc = enqueue_run(g, P);
+    if (rc == MCE_OK) rc = collect_run(g, P, per_graph, hist, hist_len, total);
+    free_plan(g, P);
+    return rc;
+}
+
+static void release_prepared(mce_graph *g) {
+    if (g->prepared_exec) cudaGraphExecDestroy(g->prepared_exec);
+    if (g->prepared) free_plan(g, g->prepared);
+    g->prepared = nullptr;
+    g->prepared_exec = nullptr;
+}
+
+extern "C" int mce_prepare(mce_graph *g, const mce_opts *opts) {
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    release_prepared(g);
+    RunPlan *P = nullptr;
+    int rc = plan_run(g, opts, kAllClasses, nullptr, &P);
+    if (rc != MCE_OK) return rc;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(g->stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) {
+        free_plan(g, P);
+        return fail(MCE_ECUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(e));
+    }
+    P->capturing = true;
+    rc = enqueue_run(g, P);
+    P->capturing = false;
+    e = cudaStreamEndCapture(g->stream, &graph);
+    if (rc == MCE_OK && e != cudaSuccess) rc = fail(MCE_ECUDA, "cudaStreamEndCapture: %s", cudaGetErrorString(e));
+    if (rc == MCE_OK && (e = cudaGraphInstantiate(&exec, graph, 0)) != cudaSuccess)
+        rc = fail(MCE_ECUDA, "cudaGraphInstantiate: %s", cudaGetErrorString(e));
+    if (graph) cudaGraphDestroy(graph);
+    if (rc != MCE_OK) {
+        free_plan(g, P);
+        return rc;
+    }
+    g->prepared = P;
+    g->prepared_exec = exec;
+    return MCE_OK;
+}
+
+extern "C" int mce_run_prepared(mce_graph *g, mce_result *per_graph, uint64_t *hist, int32_t hist_len,
+                                mce_result *total) {
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    if (!g->prepared) return fail(MCE_EINVAL, "no prepared run: call mce_prepare first");
+    if (!per_graph && !total) return fail(MCE_EINVAL, "per_graph and total are both NULL");
+    if (hist && hist_len < 0) return fail(MCE_EINVAL, "hist_len < 0");
+    g->prepared->replay = true;
+    cudaError_t e = cudaGraphLaunch(g->prepared_exec, g->stream);
+    if (e != cudaSuccess) return fail(MCE_ECUDA, "cudaGraphLaunch: %s", cudaGetErrorString(e));
+    return collect_run(g, g->prepared, per_graph, hist, hist_len, total);
+}
+
+// Try launch settings per width class on the whole class and keep the
+// fastest: donation threshold, donation rule, block count.
+extern "C" int mce_autotune(mce_graph *g, const mce_opts *base, double budget_ms) {
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    Tuned over[kNumClasses];
+    for (int c = 0; c < kNumClasses; c++) {
+        g->tuned[c] = Tuned{};
+        if (g->class_count[c] == 0) continue;
+        const int rows = g->class_rows[c];
+        const int A = std::max(10, rows / 8);
+        const Tuned cands[] = {{A, MCE_DONATE_EITHER, 0},
+                               {std::max(10, rows / 16), MCE_DONATE_EITHER, 0},
+                               {std::max(10, rows / 4), MCE_DONATE_EITHER, 0},
+                               {A, MCE_DONATE_PAPER, 0},
+                               {A, MCE_DONATE_ANY, 0},
+                               {A, MCE_DONATE_EITHER, g->sm_count}};
+        double best_ms = 1e300, spent = 0;
+        const double share = budget_ms > 0 ? budget_ms / kNumClasses : 1e300;
+        for (const Tuned &t : cands) {
+            for (int q = 0; q < kNumClasses; q++) over[q] = Tuned{};
+            over[c] = t;
+            RunPlan *P = nullptr;
+            int rc = plan_run(g, base, 1u << c, over, &P);
+            if (rc != MCE_OK) return rc;
+            rc = enqueue_run(g, P);
+            if (rc == MCE_OK) {
+                mce_result tot{};
+                rc = collect_run(g, P, nullptr, nullptr, 0, &tot);
+                if (rc == MCE_OK) {
+                    const double ms = tot.ms_traverse;
+                    spent += ms;
+                    if (ms < best_ms) {
+                        best_ms = ms;
+                        g->tuned[c] = t;
+                    }
+                }
+            }
+            free_plan(g, P);
+            if (rc != MCE_OK) return rc;
+            if (spent > share) break;
+        }
+    }
+    g->tuned_valid = true;
+    return MCE_OK;
+}
+
+extern "C" int mce_get_tuning(const mce_graph *g, int32_t *donate_min_p, int32_t *donate_policy, int32_t *blocks) {
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    if (!g->tuned_valid) return fail(MCE_EINVAL, "mce_autotune has not run on this handle");
+    for (int c = 0; c < kNumClasses; c++) {
+        if (donate_min_p) donate_min_p[c] = g->tuned[c].dmp;
+        if (donate_policy) donate_policy[c] = g->tuned[c].policy;
+        if (blocks) blocks[c] = g->tuned[c].blocks;
+    }
+    return MCE_OK;
 }
 
 extern "C" int mce_run(mce_graph *g, const mce_opts *opts, mce_result *out, uint64_t *hist, int32_t hist_len) {
@@ -762,11 +990,51 @@ extern "C" int mce_root_features(mce_graph *g, int32_t *raw, float *feat) {
     int32_t *scratch = (int32_t *)dalloc(g, (size_t)warps * stride * sizeof(int32_t));
     if (!scratch) return fail(MCE_ENOMEM, "device allocation failed");
     CK(launch_root_features(g->n, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->core, scratch, stride,
-                            warps, raw, feat, g->stream));
+                            warps, raw, feat, nullptr, g->stream));
     CK(cudaStreamSynchronize(g->stream));
 cleanup:
     dfree(g, scratch);
     if (g->stream) cudaStreamSynchronize(g->stream);
+    return rc;
+}
+
+extern "C" int mce_predict_priority(mce_graph *g, mce_model *m, int32_t min_p, float *priority) {
+    if (!g || !m || !priority) return fail(MCE_EINVAL, "NULL argument");
+    if (g->n == 0) return MCE_OK;
+    const int n = g->n;
+    int rc = MCE_OK;
+    int32_t *flags = (int32_t *)dalloc(g, (size_t)n * 4);
+    int32_t *pos = (int32_t *)dalloc(g, ((size_t)n + 1) * 4);
+    int32_t *stmp = (int32_t *)dalloc(g, (size_t)scan_tmp_words(n + 1) * 4);
+    int32_t *list = nullptr, *scratch = nullptr;
+    float *feat = nullptr, *pred = nullptr;
+    int k = 0;
+    if (!flags || !pos || !stmp) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+    CK(launch_select_roots(n, g->outdeg, min_p, flags, pos, stmp, nullptr, g->stream));  // count only
+    CK(cudaMemcpyAsync(&k, pos + n, 4, cudaMemcpyDeviceToHost, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+    if (k > 0) {
+        const int threads = 256;
+        const int blocks = std::min<int64_t>((int64_t)g->sm_count * 16, ((int64_t)k * 32 + threads - 1) / threads);
+        const int warps = blocks * (threads / 32);
+        const int stride = g->d + 1;
+        list = (int32_t *)dalloc(g, (size_t)k * 4);
+        feat = (float *)dalloc(g, (size_t)k * kNumFeatures * 4);
+        pred = (float *)dalloc(g, (size_t)k * 4);
+        scratch = (int32_t *)dalloc(g, (size_t)warps * stride * 4);
+        if (!list || !feat || !pred || !scratch) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+        CK(launch_select_roots(n, g->outdeg, min_p, flags, pos, stmp, list, g->stream));
+        CK(launch_root_features(k, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->core, scratch, stride,
+                                warps, nullptr, feat, list, g->stream));
+        CK(launch_mlp_predict(model_params(m), feat, k, pred, g->sm_count, g->stream));
+    }
+    // roots below the threshold get the lowest priority
+    CK(launch_fill_and_scatter(n, -1.0f, k, list, g->order, pred, priority, g->stream));
+    CK(cudaStreamSynchronize(g->stream));
+cleanup:
+    if (g->stream) cudaStreamSynchronize(g->stream);
+    for (void *q : {(void *)flags, (void *)pos, (void *)stmp, (void *)list, (void *)feat, (void *)pred, (void *)scratch})
+        dfree(g, q);
     return rc;
 }
 

@@ -9,7 +9,10 @@
 #include <cstring>
 #include <vector>
 
+#include <algorithm>
+
 #include "mce_learn.cuh"
+#include "mce_prep.cuh"
 
 namespace mce {
 
@@ -26,15 +29,19 @@ __device__ __forceinline__ int find_sorted(const int32_t *a, int lo, int hi, int
 
 __device__ __forceinline__ int32_t sat32(long long x) { return x > INT32_MAX ? INT32_MAX : (int32_t)x; }
 
-// One warp per root rank r. scratch: per warp (d + 1) ints.
+// One warp per root. Roots are all ranks 0..n-1 (list == NULL; outputs
+// indexed by input id) or list[0..n) (outputs indexed by list position).
+// scratch: per warp (d + 1) ints.
 __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
                                 const int32_t *in_col, const int32_t *order, const int32_t *core_by_id,
-                                int32_t *scratch, int scratch_stride, int32_t *raw, float *feat) {
+                                int32_t *scratch, int scratch_stride, int32_t *raw, float *feat,
+                                const int32_t *list) {
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
     int32_t *dg = scratch + (size_t)w0 * scratch_stride;
-    for (int64_t r = w0; r < n; r += nw) {
+    for (int64_t it = w0; it < n; it += nw) {
+        const int64_t r = list ? list[it] : it;
         const int32_t *P0 = out_col + out_ptr[r];
         const int n0 = out_ptr[r + 1] - out_ptr[r];
         const int32_t *X0 = in_col + in_ptr[r];
@@ -129,9 +136,9 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
                 case 15: f = pairs - eP; break;                              // missing edges in P0
             }
             const int32_t v = sat32(f);
-            const int id = order[r];
-            if (raw) raw[(size_t)id * kNumFeatures + lane] = v;
-            if (feat) feat[(size_t)id * kNumFeatures + lane] = log2f(1.0f + (float)v);
+            const size_t at = list ? (size_t)it : (size_t)order[r];
+            if (raw) raw[at * kNumFeatures + lane] = v;
+            if (feat) feat[at * kNumFeatures + lane] = log2f(1.0f + (float)v);
         }
         __syncwarp();
     }
@@ -140,13 +147,61 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
 cudaError_t launch_root_features(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
                                  const int32_t *in_col, const int32_t *order, const int32_t *core_by_id,
                                  int32_t *scratch, int scratch_stride, int warps, int32_t *raw, float *feat,
-                                 cudaStream_t s) {
+                                 const int32_t *list, cudaStream_t s) {
     if (n == 0) return cudaSuccess;
     const int threads = 256;
     const int blocks = (warps * 32 + threads - 1) / threads;
     k_root_features<<<blocks, threads, 0, s>>>(n, out_ptr, out_col, in_ptr, in_col, order, core_by_id, scratch,
-                                               scratch_stride, raw, feat);
+                                               scratch_stride, raw, feat, list);
     count_launch();
+    return cudaGetLastError();
+}
+
+// roots whose |P0| >= min_p (ranks, ascending) and the priority fill
+__global__ void k_flag_min_p(int n, const int32_t *outdeg, int min_p, int32_t *flags) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        flags[r] = outdeg[r] >= min_p;
+}
+
+__global__ void k_gather_ranks(int n, const int32_t *flags, const int32_t *pos, int32_t *list) {
+    for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+        if (flags[r]) list[pos[r]] = (int32_t)r;
+}
+
+__global__ void k_fill_f32(float *a, int64_t n, float v) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        a[i] = v;
+}
+
+__global__ void k_scatter_pred(int k, const int32_t *list, const int32_t *order, const float *pred, float *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        out[order[list[i]]] = pred[i];
+}
+
+cudaError_t launch_select_roots(int n, const int32_t *outdeg, int min_p, int32_t *flags, int32_t *pos,
+                                int32_t *scan_tmp, int32_t *list, cudaStream_t s) {
+    if (n == 0) return cudaSuccess;
+    const unsigned b = (unsigned)std::min<int64_t>(65536, ((int64_t)n + 255) / 256);
+    k_flag_min_p<<<b, 256, 0, s>>>(n, outdeg, min_p, flags);
+    count_launch();
+    cudaError_t e = exclusive_scan(flags, pos, n, scan_tmp, s);
+    if (e != cudaSuccess) return e;
+    if (list) {  // NULL: only count (pos[n])
+        k_gather_ranks<<<b, 256, 0, s>>>(n, flags, pos, list);
+        count_launch();
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fill_and_scatter(int64_t n, float fill, int k, const int32_t *list, const int32_t *order,
+                                    const float *pred, float *out, cudaStream_t s) {
+    k_fill_f32<<<(unsigned)std::min<int64_t>(65536, (n + 255) / 256 + 1), 256, 0, s>>>(out, n, fill);
+    count_launch();
+    if (k > 0) {
+        k_scatter_pred<<<(unsigned)std::min<int64_t>(65536, ((int64_t)k + 255) / 256), 256, 0, s>>>(k, list, order,
+                                                                                                    pred, out);
+        count_launch();
+    }
     return cudaGetLastError();
 }
 
@@ -350,6 +405,8 @@ struct mce_model {
 };
 
 using mce::kModelParams;
+
+const float *mce::model_params(const mce_model *m) { return m->params; }
 
 static int model_fail(int code, const char *what, cudaError_t e = cudaSuccess) {
     char buf[256];

@@ -47,7 +47,7 @@ class mce_opts(ctypes.Structure):
                 ("timeout_ms", ctypes.c_int64), ("root_count", ctypes.c_void_p),
                 ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
                 ("root_priority", ctypes.c_void_p), ("roots", ctypes.c_void_p),
-                ("n_roots", ctypes.c_int64)]
+                ("n_roots", ctypes.c_int64), ("tuned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
 class mce_result(ctypes.Structure):
@@ -94,6 +94,10 @@ def library():
         lib.mce_graph_info.argtypes = [vp, i32p, ctypes.POINTER(ctypes.c_int64), i32p, i32p, i32p]
         lib.mce_get_order.argtypes = [vp, i32p, i32p, i32p]
         lib.mce_get_stats.argtypes = [vp, ctypes.POINTER(mce_stats)]
+        lib.mce_autotune.argtypes = [vp, ctypes.POINTER(mce_opts), ctypes.c_double]
+        lib.mce_get_tuning.argtypes = [vp, i32p, i32p, i32p]
+        lib.mce_prepare.argtypes = [vp, ctypes.POINTER(mce_opts)]
+        lib.mce_run_prepared.argtypes = [vp, ctypes.POINTER(mce_result), u64p, i32, ctypes.POINTER(mce_result)]
         lib.mce_peel_noalloc.argtypes = [vp, vp, i32, i64, vp, vp, vp, vp]
         f32p = ctypes.POINTER(ctypes.c_float)
         lib.mce_root_features.argtypes = [vp, vp, vp]
@@ -102,6 +106,7 @@ def library():
         lib.mce_model_predict.argtypes = [vp, vp, i64, vp]
         lib.mce_model_gradient.argtypes = [vp, vp, vp, i32, f32p, f32p]
         lib.mce_model_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, f32p]
+        lib.mce_predict_priority.argtypes = [vp, vp, i32, vp]
         lib.mce_model_destroy.argtypes = [vp]
         lib.mce_model_destroy.restype = None
         lib.mce_destroy.argtypes = [vp]
@@ -274,6 +279,32 @@ def mce_run_batch(h: Handle, opts: Optional[mce_opts] = None, hist_len: Optional
     return [_result(per[i]) for i in range(h.G)], hist, _result(tot)
 
 
+def mce_autotune(h: Handle, opts: Optional[mce_opts] = None, budget_ms: float = 5000.0) -> dict:
+    """Pick launch settings per width class (see include/mce.h); returns them."""
+    _check(library().mce_autotune(h.ptr, ctypes.byref(opts) if opts is not None else None, budget_ms))
+    d, p, b = (ctypes.c_int32 * 9)(), (ctypes.c_int32 * 9)(), (ctypes.c_int32 * 9)()
+    _check(library().mce_get_tuning(h.ptr, d, p, b))
+    return {"donate_min_p": list(d), "donate_policy": list(p), "blocks": list(b)}
+
+
+def mce_prepare(h: Handle, opts: Optional[mce_opts] = None):
+    """Capture one run into a CUDA graph kept by the handle."""
+    h._prepared_opts = opts  # the opts' device buffers must outlive the capture
+    _check(library().mce_prepare(h.ptr, ctypes.byref(opts) if opts is not None else None))
+
+
+def mce_run_prepared(h: Handle, hist_len: Optional[int] = None):
+    """Replay the captured run: (per-graph results, hist [G, hist_len], total)."""
+    if hist_len is None:
+        hist_len = mce_graph_info(h)["degeneracy"] + 2
+    per = (mce_result * h.G)()
+    hist = np.zeros((h.G, max(hist_len, 1)), np.uint64)
+    tot = mce_result()
+    _check(library().mce_run_prepared(h.ptr, per, hist.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64)),
+                                      hist_len, ctypes.byref(tot)))
+    return [_result(per[i]) for i in range(h.G)], hist, _result(tot)
+
+
 def mce_graph_info(h: Handle) -> dict:
     n, G, d, md = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
     m = ctypes.c_int64()
@@ -400,6 +431,15 @@ class Model:
             self.close()
         except Exception:
             pass
+
+
+def mce_predict_priority(h: Handle, model: "Model", min_p: int = 33):
+    """Predicted log2 subtree size per root (CUDA float32 [n] by input id);
+    roots with |P0| < min_p get -1 (see include/mce.h)."""
+    import torch
+    out = torch.empty(max(h.n, 1), dtype=torch.float32, device="cuda")
+    _check(library().mce_predict_priority(h.ptr, model.ptr, min_p, ctypes.c_void_p(out.data_ptr())))
+    return out[: h.n]
 
 
 def mce_destroy(h: Handle):

@@ -136,9 +136,10 @@ def load(path=DEFAULT_MODEL):
     return E.Model(np.array(d["params"], np.float32)), d.get("meta", {})
 
 
-def priority(model, h):
-    """Predicted log2 subtree size per root (CUDA float32 [n], by input id)."""
-    return model.predict(E.mce_root_features(h))
+def priority(model, h, min_p=33):
+    """Predicted log2 subtree size per root (CUDA float32 [n], by input id);
+    roots with fewer than min_p later neighbours are not scored (-1)."""
+    return E.mce_predict_priority(h, model, min_p)
 
 
 def evaluate(model, families=FAMILIES, seeds=EVAL_SEEDS, repeats=3, log=print):
@@ -157,9 +158,10 @@ def evaluate(model, families=FAMILIES, seeds=EVAL_SEEDS, repeats=3, log=print):
             o.root_nodes = nodes.data_ptr()
             base = E.mce_run(h, o)
             truth = torch.log2(nodes[: g.n].clamp(min=1).double()).float().contiguous()
-            pred = priority(model, h)
+            full = model.predict(E.mce_root_features(h))  # every root, for the accuracy figures
+            pred = priority(model, h)                     # what the ordering uses
             torch.cuda.synchronize()
-            t, p = truth.cpu().numpy(), pred.cpu().numpy()
+            t, p = truth.cpu().numpy(), full.cpu().numpy()
             heavy = t > 1.0
             row = {"family": fam, "seed": s, "mse": float(np.mean((p - t) ** 2)),
                    "spearman": spearman(p, t), "spearman_nontrivial": spearman(p[heavy], t[heavy]) if heavy.sum() > 2 else None}

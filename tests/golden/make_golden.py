@@ -7,7 +7,8 @@ same graph on another machine.
 
     python tests/golden/make_golden.py er_2000 chunglu_1m ...
 
-Per workload, <name>.json holds: fingerprint (n, m, sha256 of row_ptr and
+Batched workloads (batch_*) store per-graph count, hash, largest size and
+histogram instead (see make_batch). Per single-graph workload, <name>.json holds: fingerprint (n, m, sha256 of row_ptr and
 col), count, hash, hist, max_size, degeneracy, per-width totals of tree nodes
 and bitset word operations (oracle_mce_work: W = ceil(|P0|/32) words per row;
 the integer-pipe roofline's algorithmic work), the oracle's wall time and
@@ -76,6 +77,58 @@ def make(name, threads=0):
     print(name, out["count"], out["hash"], "%.1fs" % t_mce, flush=True)
 
 
+def make_batch(name, threads=0):
+    """Per-graph results of a batched workload. Each graph is a G(n,p) part
+    plus, for some, a disjoint Moon-Moser block; the parts are separate
+    components, so per-graph results are the sums of the parts':
+      * G(n,p) part: count and hash from one oracle run over all such roots
+        (per-root results summed per graph, hashes on the batch's ids), and
+        the histogram from the part alone (sizes do not depend on ids);
+      * Moon-Moser block: oracle_multipartite (all transversals enumerated).
+    """
+    b = gen.workload(name)
+    gp, mm = b.graph_ptr, b.mm_sizes
+    G = len(gp) - 1
+    gnp_roots = np.concatenate([np.arange(gp[i], gp[i + 1] - mm[i], dtype=np.int32) for i in range(G)])
+    t0 = time.time()
+    r = oracle.mce(b.row_ptr, b.col, mode=oracle.PIVOT_IP, threads=threads, roots=gnp_roots, per_root=True)
+    graphs = []
+    total_c, total_h = 0, 0
+    for i in range(G):
+        a, z = int(gp[i]), int(gp[i + 1])
+        ng = z - a - int(mm[i])
+        cnt = int(r.root_count[a:a + ng].astype(np.uint64).sum())
+        hsh = int(r.root_hash[a:a + ng].astype(object).sum()) & ((1 << 64) - 1)
+        # the part alone (ids 0..ng-1) for its histogram
+        rp = b.row_ptr[a:a + ng + 1] - b.row_ptr[a]
+        col = b.col[b.row_ptr[a]:b.row_ptr[a + ng]] - a
+        part = oracle.mce(rp, col, mode=oracle.PIVOT_IP, threads=1)
+        assert part.count == cnt
+        hist = {int(k): int(v) for k, v in enumerate(part.hist) if v}
+        if mm[i]:
+            k = int(mm[i]) // 3
+            c2, h2 = oracle.multipartite(a + ng, k, 3)
+            cnt += c2
+            hsh = (hsh + h2) & ((1 << 64) - 1)
+            hist[k] = hist.get(k, 0) + c2
+        graphs.append({"count": cnt, "hash": "0x%016x" % hsh, "max_size": max(hist) if hist else 0,
+                       "hist": {str(k): v for k, v in sorted(hist.items())}})
+        total_c += cnt
+        total_h = (total_h + hsh) & ((1 << 64) - 1)
+    out = {"workload": name,
+           "source": "CPU oracle: Bron-Kerbosch (pivot from P u X_P) on the G(n,p) parts, "
+                     "oracle_multipartite on the Moon-Moser blocks, on gen.workload(%r)" % name,
+           "fingerprint": fingerprint(b), "graph_ptr_sha256": hashlib.sha256(gp.astype(np.int32).tobytes()).hexdigest(),
+           "G": G, "count": total_c, "hash": "0x%016x" % total_h, "graphs": graphs,
+           "oracle_seconds": round(time.time() - t0, 1)}
+    with open(os.path.join(HERE, name + ".json"), "w") as f:
+        json.dump(out, f)
+    print(name, total_c, out["hash"], "%.1fs" % out["oracle_seconds"], flush=True)
+
+
 if __name__ == "__main__":
     for name in sys.argv[1:]:
-        make(name)
+        if name.startswith("batch_"):
+            make_batch(name)
+        else:
+            make(name)

@@ -348,3 +348,15 @@ def test_bf16_rounding_reference():
     assert bf16_round(np.float32(1.0 + 3 * 2 ** -8)) == 1.0 + 2 ** -6    # halfway, even is up
     assert bf16_round(np.float32(-2.5)) == -2.5
     assert bf16_round(np.float32(1.0 + 2 ** -7 + 2 ** -9)) == 1.0 + 2 ** -7
+
+
+@pytest.mark.parametrize("k,size,first", [(1, 3, 0), (4, 3, 7), (6, 3, 100), (5, 2, 3), (3, 4, 11)])
+def test_multipartite_enumeration(k, size, first):
+    # transversal enumeration = Bron-Kerbosch on the same graph (ids offset by `first`)
+    g = gen.multipartite(k, size)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    e = np.stack([src, g.col], 1) + first
+    shifted = gen.from_edges(first + g.n, e.tolist())
+    r = oracle.mce(shifted.row_ptr, shifted.col, roots=np.arange(first, first + g.n, dtype=np.int32))
+    c, h = oracle.multipartite(first, k, size)
+    assert c == size ** k == r.count and h == r.hash
