@@ -276,10 +276,12 @@ int mce_peel_noalloc(const int32_t *row_ptr, const int32_t *col, int32_t n, int6
  * change. Features (int32, saturating at INT32_MAX), for a root v with
  * P0 = later and X0 = earlier neighbours in the degeneracy order:
  *   0 deg(v)             1 core(v)             2 |P0|              3 |X0|
- *   4 e(P0) + e(P0,X0)   5 e(P0)               6 e(P0,X0)          7 floor(2^16 e(P0) / C(|P0|,2))
+ *   4 e(P0) + e(P0,X0')  5 e(P0)               6 e(P0,X0')         7 floor(2^16 e(P0) / C(|P0|,2))
  *   8 sum of deg(u), u in N(v)                 9 max / 10 min over u in P0 of |N(u) n P0|
  *  11 #u in P0 adjacent to all other P0        12 max / 13 sum of core(u) over u in P0
- *  14 max over x in X0 of |N(x) n P0|          15 C(|P0|,2) - e(P0)
+ *  14 max over x in X0' of |N(x) n P0|         15 C(|P0|,2) - e(P0)
+ * where X0' = the 256 smallest input ids of X0 (all of X0 when smaller), which
+ * bounds the cost of a root with a very large X0.
  * The network input is log2(1 + feature), standardised with per-feature
  * mean/std stored in the model. Layers: 16 -> 64 (ReLU) -> 64 (ReLU) -> 1,
  * weights rounded to BF16 (nearest even) in every use, biases and all

@@ -3,13 +3,15 @@ TEST INFRASTRUCTURE ONLY (plain Python sets; small graphs).
 
 For a root v with P0 = later and X0 = earlier neighbours in the oracle's
 degeneracy order (oracle_peel), the 16 int32 features listed in
-include/mce.h, saturating at 2^31 - 1.
+include/mce.h, saturating at 2^31 - 1 (features 4, 6 and 14 use X0', the
+256 smallest input ids of X0).
 """
 import numpy as np
 
 from . import peel
 
 I32 = 2 ** 31 - 1
+XCAP = 256  # features 4, 6 and 14 look at X0' = the XCAP smallest input ids of X0
 
 
 def root_features(row_ptr, col):
@@ -24,7 +26,8 @@ def root_features(row_ptr, col):
         Ps = set(P0)
         dP = {u: len(nb[u] & Ps) for u in P0}
         eP = sum(dP.values()) // 2
-        xc = [len(nb[x] & Ps) for x in X0]
+        X0c = sorted(X0)[:XCAP]  # X0': the smallest input ids of X0
+        xc = [len(nb[x] & Ps) for x in X0c]
         eX = sum(xc)
         k = len(P0)
         pairs = k * (k - 1) // 2

@@ -982,19 +982,11 @@ extern "C" int mce_get_order(const mce_graph *g, int32_t *core, int32_t *rank, i
 extern "C" int mce_root_features(mce_graph *g, int32_t *raw, float *feat) {
     if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
     if (g->n == 0 || (!raw && !feat)) return MCE_OK;
-    const int threads = 256;
-    const int blocks = std::min<int64_t>((int64_t)g->sm_count * 16, ((int64_t)g->n * 32 + threads - 1) / threads);
-    const int warps = blocks * (threads / 32);
-    const int stride = g->d + 1;
     int rc = MCE_OK;
-    int32_t *scratch = (int32_t *)dalloc(g, (size_t)warps * stride * sizeof(int32_t));
-    if (!scratch) return fail(MCE_ENOMEM, "device allocation failed");
-    CK(launch_root_features(g->n, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->core, scratch, stride,
-                            warps, raw, feat, nullptr, g->stream));
+    CK(launch_root_features(g->n, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->core, g->d, g->sm_count,
+                            raw, feat, nullptr, g->stream));
     CK(cudaStreamSynchronize(g->stream));
 cleanup:
-    dfree(g, scratch);
-    if (g->stream) cudaStreamSynchronize(g->stream);
     return rc;
 }
 
@@ -1006,7 +998,7 @@ extern "C" int mce_predict_priority(mce_graph *g, mce_model *m, int32_t min_p, f
     int32_t *flags = (int32_t *)dalloc(g, (size_t)n * 4);
     int32_t *pos = (int32_t *)dalloc(g, ((size_t)n + 1) * 4);
     int32_t *stmp = (int32_t *)dalloc(g, (size_t)scan_tmp_words(n + 1) * 4);
-    int32_t *list = nullptr, *scratch = nullptr;
+    int32_t *list = nullptr;
     float *feat = nullptr, *pred = nullptr;
     int k = 0;
     if (!flags || !pos || !stmp) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
@@ -1014,18 +1006,13 @@ extern "C" int mce_predict_priority(mce_graph *g, mce_model *m, int32_t min_p, f
     CK(cudaMemcpyAsync(&k, pos + n, 4, cudaMemcpyDeviceToHost, g->stream));
     CK(cudaStreamSynchronize(g->stream));
     if (k > 0) {
-        const int threads = 256;
-        const int blocks = std::min<int64_t>((int64_t)g->sm_count * 16, ((int64_t)k * 32 + threads - 1) / threads);
-        const int warps = blocks * (threads / 32);
-        const int stride = g->d + 1;
         list = (int32_t *)dalloc(g, (size_t)k * 4);
         feat = (float *)dalloc(g, (size_t)k * kNumFeatures * 4);
         pred = (float *)dalloc(g, (size_t)k * 4);
-        scratch = (int32_t *)dalloc(g, (size_t)warps * stride * 4);
-        if (!list || !feat || !pred || !scratch) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+        if (!list || !feat || !pred) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
         CK(launch_select_roots(n, g->outdeg, min_p, flags, pos, stmp, list, g->stream));
-        CK(launch_root_features(k, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->core, scratch, stride,
-                                warps, nullptr, feat, list, g->stream));
+        CK(launch_root_features(k, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->core, g->d, g->sm_count,
+                                nullptr, feat, list, g->stream));
         CK(launch_mlp_predict(model_params(m), feat, k, pred, g->sm_count, g->stream));
     }
     // roots below the threshold get the lowest priority
@@ -1033,7 +1020,7 @@ extern "C" int mce_predict_priority(mce_graph *g, mce_model *m, int32_t min_p, f
     CK(cudaStreamSynchronize(g->stream));
 cleanup:
     if (g->stream) cudaStreamSynchronize(g->stream);
-    for (void *q : {(void *)flags, (void *)pos, (void *)stmp, (void *)list, (void *)feat, (void *)pred, (void *)scratch})
+    for (void *q : {(void *)flags, (void *)pos, (void *)stmp, (void *)list, (void *)feat, (void *)pred})
         dfree(g, q);
     return rc;
 }

@@ -29,24 +29,33 @@ __device__ __forceinline__ int find_sorted(const int32_t *a, int lo, int hi, int
 
 __device__ __forceinline__ int32_t sat32(long long x) { return x > INT32_MAX ? INT32_MAX : (int32_t)x; }
 
+// excluded vertices whose adjacency to P0 the features examine (bounds the
+// per-root cost for hubs with tens of thousands of earlier neighbours)
+constexpr int kXCap = 256;
+
 // One warp per root. Roots are all ranks 0..n-1 (list == NULL; outputs
 // indexed by input id) or list[0..n) (outputs indexed by list position).
-// scratch: per warp (d + 1) ints.
+// Each warp stages the root's P0 and the in-P0 degree counters in shared
+// memory (2 * stride ints per warp, stride >= degeneracy + 1).
 __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
                                 const int32_t *in_col, const int32_t *order, const int32_t *core_by_id,
-                                int32_t *scratch, int scratch_stride, int32_t *raw, float *feat,
-                                const int32_t *list) {
+                                int stride, int32_t *raw, float *feat, const int32_t *list) {
+    extern __shared__ int32_t fsm[];
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int32_t *dg = scratch + (size_t)w0 * scratch_stride;
+    int32_t *P0 = fsm + (size_t)(threadIdx.x >> 5) * 2 * stride;
+    int32_t *dg = P0 + stride;
     for (int64_t it = w0; it < n; it += nw) {
         const int64_t r = list ? list[it] : it;
-        const int32_t *P0 = out_col + out_ptr[r];
+        const int32_t *P0g = out_col + out_ptr[r];
         const int n0 = out_ptr[r + 1] - out_ptr[r];
         const int32_t *X0 = in_col + in_ptr[r];
         const int x0 = in_ptr[r + 1] - in_ptr[r];
-        for (int i = lane; i < n0; i += 32) dg[i] = 0;
+        for (int i = lane; i < n0; i += 32) {
+            P0[i] = P0g[i];
+            dg[i] = 0;
+        }
         __syncwarp();
         // edges inside P0: u = P0[i] finds its later neighbours w in P0
         long long eP = 0;
@@ -82,11 +91,15 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
             core_sum += cu;
             two_hop += (out_ptr[u + 1] - out_ptr[u]) + (in_ptr[u + 1] - in_ptr[u]);
         }
-        // edges between X0 and P0: x is earlier than r, so x->w with w in P0 is x's later edge
+        // edges between X0' and P0, X0' = the first kXCap vertices of X0 by
+        // input id (X0 keeps the input's ascending-id order); x is earlier than
+        // r, so x->w with w in P0 is one of x's later edges
         long long eX = 0;
         int xmax = 0;
         for (int i = lane; i < x0; i += 32) {
             const int32_t x = X0[i];
+            two_hop += (out_ptr[x + 1] - out_ptr[x]) + (in_ptr[x + 1] - in_ptr[x]);
+            if (i >= kXCap) continue;
             const int32_t *nx = out_col + out_ptr[x];
             const int lx = out_ptr[x + 1] - out_ptr[x];
             int c = 0, lo = 0;
@@ -101,7 +114,6 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
             }
             eX += c;
             xmax = max(xmax, c);
-            two_hop += lx + (in_ptr[x + 1] - in_ptr[x]);
         }
         for (int o = 16; o; o >>= 1) {
             eP += __shfl_xor_sync(0xffffffffu, eP, o);
@@ -122,9 +134,9 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
                 case 1: f = core_by_id[order[r]]; break;                     // core number
                 case 2: f = n0; break;                                       // |P0|
                 case 3: f = x0; break;                                       // |X0|
-                case 4: f = eP + eX; break;                                  // triangles with a later vertex
+                case 4: f = eP + eX; break;                                  // e(P0) + e(P0, X0')
                 case 5: f = eP; break;                                       // e(P0)
-                case 6: f = eX; break;                                       // e(P0, X0)
+                case 6: f = eX; break;                                       // e(P0, X0')
                 case 7: f = pairs > 0 ? (eP * 65536) / pairs : 0; break;     // floor(2^16 density(P0))
                 case 8: f = two_hop; break;                                  // sum of neighbour degrees
                 case 9: f = n0 ? degmax : 0; break;                          // max degree inside P0
@@ -132,7 +144,7 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
                 case 11: f = univ; break;                                    // vertices adjacent to all of P0
                 case 12: f = core_max; break;                                // max core over P0
                 case 13: f = core_sum; break;                                // sum of cores over P0
-                case 14: f = xmax; break;                                    // max |N(x) n P0|, x in X0
+                case 14: f = xmax; break;                                    // max |N(x) n P0|, x in X0'
                 case 15: f = pairs - eP; break;                              // missing edges in P0
             }
             const int32_t v = sat32(f);
@@ -146,13 +158,21 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
 
 cudaError_t launch_root_features(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
                                  const int32_t *in_col, const int32_t *order, const int32_t *core_by_id,
-                                 int32_t *scratch, int scratch_stride, int warps, int32_t *raw, float *feat,
-                                 const int32_t *list, cudaStream_t s) {
+                                 int degeneracy, int sm_count, int32_t *raw, float *feat, const int32_t *list,
+                                 cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    const int threads = 256;
-    const int blocks = (warps * 32 + threads - 1) / threads;
-    k_root_features<<<blocks, threads, 0, s>>>(n, out_ptr, out_col, in_ptr, in_col, order, core_by_id, scratch,
-                                               scratch_stride, raw, feat, list);
+    const int threads = 128;  // 4 warps, each with 2 * stride ints of shared memory
+    const int stride = (degeneracy + 4) / 4 * 4;
+    const size_t smem = (size_t)(threads / 32) * 2 * stride * sizeof(int32_t);
+    cudaError_t e = cudaFuncSetAttribute(k_root_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_root_features, threads, smem);
+    if (e != cudaSuccess) return e;
+    const int64_t want = ((int64_t)n + 3) / 4;
+    const int blocks = (int)std::min<int64_t>(want, (int64_t)sm_count * std::max(per_sm, 1));
+    k_root_features<<<blocks, threads, smem, s>>>(n, out_ptr, out_col, in_ptr, in_col, order, core_by_id, stride,
+                                                  raw, feat, list);
     count_launch();
     return cudaGetLastError();
 }

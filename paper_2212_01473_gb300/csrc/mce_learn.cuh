@@ -10,8 +10,8 @@ constexpr int kModelParams = MCE_MODEL_PARAMS;
 
 cudaError_t launch_root_features(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
                                  const int32_t *in_col, const int32_t *order, const int32_t *core_by_id,
-                                 int32_t *scratch, int scratch_stride, int warps, int32_t *raw, float *feat,
-                                 const int32_t *list, cudaStream_t s);
+                                 int degeneracy, int sm_count, int32_t *raw, float *feat, const int32_t *list,
+                                 cudaStream_t s);
 cudaError_t launch_select_roots(int n, const int32_t *outdeg, int min_p, int32_t *flags, int32_t *pos,
                                 int32_t *scan_tmp, int32_t *list, cudaStream_t s);
 cudaError_t launch_fill_and_scatter(int64_t n, float fill, int k, const int32_t *list, const int32_t *order,

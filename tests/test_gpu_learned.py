@@ -27,7 +27,8 @@ import paper_2212_01473_gb300 as mce  # noqa: E402
 from paper_2212_01473_gb300 import learn  # noqa: E402
 
 GRAPHS = [gen.complete(9), gen.moon_moser(5), gen.worked_example(), gen.gnp(300, 0.08, 2),
-          gen.chung_lu(3000, 12.0, 2.1, 300.0, 3, 10, 20, 4), gen.random_forest(200, 3)]
+          gen.chung_lu(3000, 12.0, 2.1, 300.0, 3, 10, 20, 4), gen.random_forest(200, 3),
+          gen.chung_lu(6000, 20.0, 2.1, 1500.0, 3, 10, 20, 6)]  # hubs with |X0| > 256
 
 
 @pytest.mark.parametrize("g", GRAPHS, ids=[g.name or "g" for g in GRAPHS])
