@@ -534,7 +534,6 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     if (opts.pivot < 0 || opts.pivot > 2) rc = fail(MCE_EINVAL, "bad opts.pivot");
     else if (opts.order != MCE_ORDER_PLAIN && opts.order != MCE_ORDER_PRIORITY) rc = fail(MCE_EINVAL, "bad opts.order");
     else if (opts.order == MCE_ORDER_PRIORITY && !opts.root_priority) rc = fail(MCE_EINVAL, "MCE_ORDER_PRIORITY needs opts.root_priority");
-    else if (opts.pivot == MCE_PIVOT_IPX) rc = fail(MCE_EINVAL, "IPX pivoting is not available in this build");
     else if (opts.donate_min_p < 0) rc = fail(MCE_EINVAL, "opts.donate_min_p < 0");
     else if (opts.donate_policy < 0 || opts.donate_policy > 2) rc = fail(MCE_EINVAL, "bad opts.donate_policy");
     else if (opts.roots && opts.n_roots < 0) rc = fail(MCE_EINVAL, "opts.n_roots < 0");
@@ -645,7 +644,10 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         a.n_roots = P->counts[c];
         a.rows_cap = k.rows;
         a.x_cap = g->class_x[c];
-        a.pivot_ipx = 0;
+        // IPX: pivots may also come from X_X; AUTO follows the Sec. IV-D rule
+        // (partial induced subgraphs when max degree / degeneracy > 200)
+        a.pivot_ipx = opts.pivot == MCE_PIVOT_IPX ||
+                      (opts.pivot == MCE_PIVOT_AUTO && g->d > 0 && (double)g->max_deg / g->d <= 200.0);
         a.worker_list = opts.worker_list ? 1 : 0;
         // 0 = automatic: a donated child must have at least 1/8 of the
         // class's widest root set, and never fewer than 10 candidates (Sec. III-C)

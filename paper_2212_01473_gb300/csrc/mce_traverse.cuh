@@ -84,6 +84,7 @@ __host__ __device__ inline GrpSmem grp_smem_layout(int wp, int gw, int rows, boo
     off += (size_t)rows * 4;
     L.cand = off;
     off += (size_t)rows * 4;
+    off = align_up(off, 16);  // holds 64-bit reduction words
     L.red = off;
     off += (size_t)gw * 4 * 4;
     L.misc = off;
@@ -102,20 +103,20 @@ __host__ __device__ inline size_t smem_bytes(const GrpSmem &L, int groups_per_bl
     return L.group0 + (size_t)groups_per_block * L.total;
 }
 
-// Arena words per group: [stack if global][A rows][X rows][xidx][xscr].
+// Arena words per group: [stack if global][A rows][X rows][xidx][xscr][xrank].
 // The A region holds A itself when it lives in global memory, else it is the
 // landing area where a donor writes A for this group when it is a receiver.
 __host__ __device__ inline size_t arena_words(int wp, int rows, int xcap, bool a_global, bool stack_smem) {
     size_t w = 0;
     if (!stack_smem) w += stack_words(wp, rows);
     w += (size_t)rows * wp;
-    w += (size_t)xcap * wp + 2 * (size_t)xcap;
+    w += (size_t)xcap * wp + 3 * (size_t)xcap;
     (void)a_global;
     return align_up(w, 4);
 }
 
 struct ArenaPtrs {
-    uint32_t *stk, *A, *xrows, *xidx, *xscr;
+    uint32_t *stk, *A, *xrows, *xidx, *xscr, *xrank;  // xrank[slot]: degeneracy rank of that X_X row's vertex
 };
 
 __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, int xcap, bool stack_smem) {
@@ -128,6 +129,7 @@ __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, 
     a.xrows = q;
     a.xidx = q + (size_t)xcap * wp;
     a.xscr = a.xidx + xcap;
+    a.xrank = a.xscr + xcap;
     return a;
 }
 
@@ -175,6 +177,23 @@ __device__ __forceinline__ int grp_or(const Grp<GW> &g, int *red, int x) {
     int t = 0;
 #pragma unroll
     for (int i = 0; i < GW; i++) t |= red[i];
+    g.sync();
+    return t;
+}
+
+template <int GW>
+__device__ __forceinline__ unsigned long long grp_max64(const Grp<GW> &g, unsigned long long *red64,
+                                                         unsigned long long x) {
+    for (int o = 16; o; o >>= 1) {
+        const unsigned long long y = __shfl_xor_sync(0xffffffffu, x, o);
+        x = y > x ? y : x;
+    }
+    if (GW == 1) return x;
+    if (g.lane == 0) red64[g.warp] = x;
+    g.sync();
+    unsigned long long t = 0;
+#pragma unroll
+    for (int i = 0; i < GW; i++) t = red64[i] > t ? red64[i] : t;
     g.sync();
     return t;
 }
@@ -261,6 +280,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
     uint32_t *xrows = ar.xrows;
     uint32_t *xidx = ar.xidx;
     uint32_t *xscr = ar.xscr;
+    uint32_t *xrank = ar.xrank;
 
     const uint64_t deadline = globaltimer_ns() + C.timeout_ns;
     PhaseClock pc{};
@@ -408,8 +428,9 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     int hits = 0;
                     const int32_t *nr = nullptr;
                     int len = 0, j0 = 0;
+                    int32_t x = 0;
                     if (idx < x0) {
-                        const int32_t x = xrow[idx];
+                        x = xrow[idx];
                         nr = G.out_col + G.out_ptr[x];
                         len = G.out_ptr[x + 1] - G.out_ptr[x];
                         j0 = find_in(nr, 0, len, r + 1);  // only later vertices can be in P0
@@ -443,6 +464,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         }
                         while (cw < WP) { row[cw++] = accw; accw = 0; }
                         xidx[slot] = (uint32_t)slot;
+                        xrank[slot] = (uint32_t)x;
                     }
                     base_slot += tot;
                 }
@@ -524,36 +546,79 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     }
                     g.sync();
                     const int nc = misc[2];
-                    // best score any candidate can reach: |P| for an excluded vertex, |P|-1 in P
-                    const unsigned bound = (unsigned)(xany ? np : np - 1);
-                    unsigned best = 0;
+                    // Pivot: the candidate with the largest |P n N(u)|, ties to the
+                    // smaller degeneracy rank. P u X_P candidates are keyed
+                    // score << 16 | (0xffff - local index) (local index order is rank
+                    // order). X_X candidates (IPX) all rank below every P0 vertex and
+                    // compare among themselves by score << 32 | ~rank.
+                    int best_x_score = -1;  // best X_X score, -1 if none scanned
+                    int piv_x = -1;         // X_X slot of the best X_X candidate
                     int scanned = 0;
-                    for (int j0 = 0; j0 < nc; j0 += GT) {
-                        const int j = j0 + g.gl;
-                        unsigned key = 0;
-                        if (j < nc) {
-                            const int c = cand[j];
-                            const uint32_t *arow = Arow + (size_t)c * WP;
-                            int sc = 0;
-                            if (WP % 4 == 0) {
-                                const uint4 *a4 = reinterpret_cast<const uint4 *>(arow);
-                                const uint4 *p4 = reinterpret_cast<const uint4 *>(curP);
-                                for (int qq = 0; qq < (W + 3) / 4; qq++) {
-                                    const uint4 a = a4[qq], pw = p4[qq];
-                                    sc += __popc(a.x & pw.x) + __popc(a.y & pw.y) + __popc(a.z & pw.z) +
-                                          __popc(a.w & pw.w);
-                                }
-                            } else {
-                                for (int w = 0; w < W; w++) sc += __popc(arow[w] & curP[w]);
+                    if (C.pivot_ipx && lpx > 0) {
+                        unsigned long long bx = 0;
+                        for (int j0 = 0; j0 < lpx; j0 += GT) {
+                            const int j = j0 + g.gl;
+                            unsigned long long key = 0;
+                            if (j < lpx) {
+                                const uint32_t e = xidx[j];
+                                const uint32_t *xr = xrows + (size_t)e * WP;
+                                int sc = 0;
+                                for (int w = 0; w < W; w++) sc += __popc(xr[w] & curP[w]);
+                                key = ((unsigned long long)(sc + 1) << 32) | (unsigned long long)(0xffffffffu - xrank[e]);
                             }
-                            key = ((unsigned)sc << 16) | (unsigned)(0xffff - c);
+                            const unsigned long long m = grp_max64(g, (unsigned long long *)red, key);
+                            bx = m > bx ? m : bx;
                         }
-                        best = max(best, grp_max(g, red, key));
-                        scanned = min(nc, j0 + GT);
-                        if ((best >> 16) >= bound) break;
+                        scanned += lpx;
+                        best_x_score = (int)(bx >> 32) - 1;
+                        // the slot of the winning X_X vertex (ranks are unique)
+                        const uint32_t want_rank = 0xffffffffu - (uint32_t)(bx & 0xffffffffull);
+                        int found = -1;
+                        for (int j0 = 0; j0 < lpx && found < 0; j0 += GT) {
+                            const int j = j0 + g.gl;
+                            const int hit = (j < lpx && xrank[xidx[j]] == want_rank) ? j : -1;
+                            found = (int)grp_max(g, red, (unsigned)(hit + 1)) - 1;
+                        }
+                        if (found >= 0) piv_x = (int)xidx[found];
+                        else best_x_score = -1;  // cannot happen (the max key came from a slot)
                     }
-                    const int piv = 0xffff - (int)(best & 0xffffu);
-                    b = own ? (p & ~Arow[(size_t)piv * WP + g.gl]) : 0u;
+                    int piv = -1;  // P0 local index of the pivot when it is not an X_X vertex
+                    if (best_x_score < np) {
+                        // best score a P u X_P candidate can reach: |P| in X_P, |P|-1 in P
+                        const unsigned bound = (unsigned)(xany ? np : np - 1);
+                        unsigned best = 0;
+                        for (int j0 = 0; j0 < nc; j0 += GT) {
+                            const int j = j0 + g.gl;
+                            unsigned key = 0;
+                            if (j < nc) {
+                                const int c = cand[j];
+                                const uint32_t *arow = Arow + (size_t)c * WP;
+                                int sc = 0;
+                                if (WP % 4 == 0) {
+                                    const uint4 *a4 = reinterpret_cast<const uint4 *>(arow);
+                                    const uint4 *p4 = reinterpret_cast<const uint4 *>(curP);
+                                    for (int qq = 0; qq < (W + 3) / 4; qq++) {
+                                        const uint4 a = a4[qq], pw = p4[qq];
+                                        sc += __popc(a.x & pw.x) + __popc(a.y & pw.y) + __popc(a.z & pw.z) +
+                                              __popc(a.w & pw.w);
+                                    }
+                                } else {
+                                    for (int w = 0; w < W; w++) sc += __popc(arow[w] & curP[w]);
+                                }
+                                key = ((unsigned)sc << 16) | (unsigned)(0xffff - c);
+                            }
+                            best = max(best, grp_max(g, red, key));
+                            scanned += min(nc - j0, GT);
+                            if ((best >> 16) >= bound) break;
+                        }
+                        // an X_X vertex wins ties (smaller rank)
+                        if ((int)(best >> 16) > best_x_score) piv = 0xffff - (int)(best & 0xffffu);
+                    }
+                    if (piv >= 0) {
+                        b = own ? (p & ~Arow[(size_t)piv * WP + g.gl]) : 0u;
+                    } else {
+                        b = own ? (p & ~xrows[(size_t)piv_x * WP + g.gl]) : 0u;
+                    }
                     enter = false;
                     pc.stop(PH_PIVOT);
                     pc.count(PH_PIVOT, (unsigned long long)scanned);
@@ -677,7 +742,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             const int k = i / WP, w = i - k * WP;
                             ra.xrows[i] = xrows[(size_t)xscr[k] * WP + w];
                         }
-                        for (int k = g.gl; k < out; k += GT) ra.xidx[k] = (uint32_t)k;
+                        for (int k = g.gl; k < out; k += GT) {
+                            ra.xidx[k] = (uint32_t)k;
+                            ra.xrank[k] = xrank[xscr[k]];
+                        }
                         uint32_t *m = C.mail + (size_t)recv * C.mail_words;
                         if (own) {
                             m[4 + g.gl] = 0u;

@@ -50,7 +50,7 @@ def test_prepared_single_graph_and_per_root_buffers():
     o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=True)
     h = mce.mce_create(g.row_ptr, g.col)
     nodes = torch.zeros(g.n, dtype=torch.int64, device="cuda")
-    opts = mce.mce_default_opts()
+    opts = mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP)  # the oracle's tree above is IP's
     opts.root_nodes = nodes.data_ptr()
     mce.mce_prepare(h, opts)
     for _ in range(2):

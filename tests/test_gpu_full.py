@@ -44,8 +44,11 @@ def test_workload_matches_stored_oracle(name):
     rp = torch.from_numpy(g.row_ptr).cuda()
     col = torch.from_numpy(g.col).cuda()
     h = mce.mce_create(rp, col)
-    r = mce.mce_run(h)
+    r = mce.mce_run(h, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP))  # the stored tree sizes are IP's
+    auto = mce.mce_run(h)
     mce.mce_destroy(h)
+    assert (auto.count, auto.hash, auto.max_size) == (gold["count"], int(gold["hash"], 16), gold["max_size"])
+    assert auto.hist.tolist() == gold["hist"]
     assert r.count == gold["count"]
     assert "0x%016x" % r.hash == gold["hash"]
     assert r.max_size == gold["max_size"]
@@ -85,7 +88,8 @@ def test_rmat_22_sampled_roots(rmat):
         picks.append(rs.choice(cand, min(k, len(cand)), replace=False))
     roots = np.sort(np.concatenate(picks)).astype(np.int32)
     o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, roots=roots, per_root=True)
-    r, (rc, rh, rn) = mce.enumerate_maximal_cliques(g.row_ptr, g.col, per_root=True, roots=roots)
+    r, (rc, rh, rn) = mce.enumerate_maximal_cliques(g.row_ptr, g.col, per_root=True, roots=roots,
+                                                     pivot=mce.MCE_PIVOT_IP)
     assert r.count == o.count and r.hash == o.hash and r.max_size == o.max_size
     assert np.array_equal(r.hist, o.hist)
     assert np.array_equal(rc[roots], o.root_count[roots])

@@ -32,8 +32,14 @@ def same(r, o):
     assert np.array_equal(r.hist.astype(np.uint64), o.hist.astype(np.uint64))
 
 
-def check_against_oracle(g, per_root=True, **opts):
-    o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=per_root)
+# GPU pivot rule -> the oracle mode that walks the same tree: pivot from
+# P u X_P (partial induced subgraph) or from all of P u X (full, Tomita)
+ORACLE_MODE = {mce.MCE_PIVOT_IP: oracle.PIVOT_IP, mce.MCE_PIVOT_IPX: oracle.PIVOT_FULL}
+
+
+def check_against_oracle(g, per_root=True, pivot=mce.MCE_PIVOT_IP, **opts):
+    o = oracle.mce(g.row_ptr, g.col, mode=ORACLE_MODE[pivot], per_root=per_root)
+    opts["pivot"] = pivot
     if per_root:
         r, (rc, rh, rn) = run(g, per_root=True, **opts)
         same(r, o)
@@ -52,19 +58,31 @@ CLOSED = [gen.complete(1), gen.complete(2), gen.complete(7), gen.empty(5), gen.c
           gen.worked_example(), gen.random_forest(60, 1)]
 
 
+PIVOTS = [mce.MCE_PIVOT_IP, mce.MCE_PIVOT_IPX]
+
+
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
 @pytest.mark.parametrize("g", CLOSED, ids=[g.name for g in CLOSED])
-def test_closed_forms(g):
-    check_against_oracle(g)
+def test_closed_forms(g, pivot):
+    check_against_oracle(g, pivot=pivot)
 
 
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
 @pytest.mark.parametrize("n,p,seed", [(30, 0.3, 0), (64, 0.5, 1), (100, 0.2, 2), (150, 0.6, 3),
                                       (300, 0.1, 4), (500, 0.05, 5), (120, 0.85, 6), (1000, 0.02, 7)])
-def test_random_graphs(n, p, seed):
-    check_against_oracle(gen.gnp(n, p, seed))
+def test_random_graphs(n, p, seed, pivot):
+    check_against_oracle(gen.gnp(n, p, seed), pivot=pivot)
 
 
-def test_er_2000_per_root():
-    check_against_oracle(gen.workload("er_2000"))
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
+def test_er_2000_per_root(pivot):
+    check_against_oracle(gen.workload("er_2000"), pivot=pivot)
+
+
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
+def test_chunglu_small_per_root(pivot):
+    # hubs: large excluded sets, many X_X pivots under IPX
+    check_against_oracle(gen.chung_lu(6000, 20.0, 2.1, 1500.0, 3, 10, 20, 6), pivot=pivot)
 
 
 @pytest.mark.parametrize("maker", [lambda: gen.workload("er_2000"), lambda: gen.gnp(3000, 0.01, 3),
@@ -86,12 +104,15 @@ def test_peel_matches_oracle(maker):
     assert info["max_degree"] == (int(g.degrees().max()) if g.n else 0)
 
 
-@pytest.mark.parametrize("blocks,donate,wl", [(1, 1, 1), (2, 1, 1), (3, 2, 1), (5, 10, 1), (4, 1, 0)])
-def test_worker_list_interleavings(blocks, donate, wl):
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
+@pytest.mark.parametrize("blocks,donate,wl,policy", [(1, 1, 1, 0), (2, 1, 1, 1), (3, 2, 1, 2), (5, 10, 1, 1),
+                                                     (4, 1, 0, 0)])
+def test_worker_list_interleavings(blocks, donate, wl, policy, pivot):
     # tiny grids force phase 2 early and many donations; results and the
     # tree itself (node counts per root) must not change
     g = gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5)
-    r, o = check_against_oracle(g, blocks=blocks, donate_min_p=donate, worker_list=wl)
+    r, o = check_against_oracle(g, pivot=pivot, blocks=blocks, donate_min_p=donate, worker_list=wl,
+                                donate_policy=policy)
     if wl == 0:
         assert r.donations == 0
 
@@ -128,12 +149,15 @@ def test_wide_rows_closed_form(n, t):
 
 
 def test_complete_graph_node_counts():
-    # K_n: root r walks a chain of n - r calls (pivot restricted to P u X_P)
+    # K_n, pivot from P u X_P: root r walks a chain of n - r calls
     n = 200
     g = gen.complete(n)
-    r, (rc, rh, rn) = run(g, per_root=True)
+    r, (rc, rh, rn) = run(g, per_root=True, pivot=mce.MCE_PIVOT_IP)
     assert rn.tolist() == [n - i for i in range(n)]
     assert r.tree_nodes == n * (n + 1) // 2
+    # full Tomita (IPX): every later root's excluded vertex 0 covers all of P
+    r, (rc, rh, rn) = run(g, per_root=True, pivot=mce.MCE_PIVOT_IPX)
+    assert rn.tolist() == [n] + [1] * (n - 1)
 
 
 def test_device_pointer_input():
@@ -223,7 +247,7 @@ def test_root_subset():
     g = gen.gnp(600, 0.06, 12)
     roots = np.random.default_rng(3).choice(g.n, 150, replace=False).astype(np.int32)
     o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, roots=roots, per_root=True)
-    r, (rc, rh, rn) = run(g, per_root=True, roots=roots)
+    r, (rc, rh, rn) = run(g, per_root=True, roots=roots, pivot=mce.MCE_PIVOT_IP)
     same(r, o)
     assert np.array_equal(rc, o.root_count) and np.array_equal(rh, o.root_hash)
     assert np.array_equal(rn, o.root_nodes)
@@ -244,7 +268,7 @@ def test_timeout_is_reported_and_context_survives():
     g = gen.chung_lu(20000, 16.0, 2.1, 2000.0, 5, 25, 40, 3)
     h = mce.mce_create(g.row_ptr, g.col)
     with pytest.raises(mce.MCEError) as ei:
-        mce.mce_run(h, mce.mce_default_opts(timeout_ms=1, blocks=1))
+        mce.mce_run(h, mce.mce_default_opts(timeout_ms=1, blocks=1, pivot=mce.MCE_PIVOT_IP))
     assert ei.value.code == mce.MCE_ETIMEOUT
     r = mce.mce_run(h)
     mce.mce_destroy(h)
