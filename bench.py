@@ -40,6 +40,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample", type=float, default=0.05,
                     help="fraction of roots (seeded) the CPU oracle runs for its baseline")
+    ap.add_argument("--pivot", default="auto", choices=["auto", "ip", "ipx"],
+                    help="pivot rule of the timed steps (auto = the Sec. IV-D heuristic)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned-order and batched comparisons")
     return ap.parse_args()
@@ -271,9 +273,11 @@ def run_ours(args):
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
+    pivot = {"auto": mce.MCE_PIVOT_AUTO, "ip": mce.MCE_PIVOT_IP, "ipx": mce.MCE_PIVOT_IPX}[args.pivot]
+
     def step():
         h = mce.mce_create(rp_d, col_d)
-        r = mce.mce_run(h)
+        r = mce.mce_run(h, mce.mce_default_opts(pivot=pivot))
         st = mce.mce_get_stats(h)
         mce.mce_destroy(h)
         return r, st
@@ -322,7 +326,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = mce.mce_create(rp_h, col_h)
-        r = mce.mce_run(h, hist_len=hl)
+        r = mce.mce_run(h, mce.mce_default_opts(pivot=pivot), hist_len=hl)
         t1 = time.perf_counter()
         mce.mce_destroy(h)
         assert r.count == count
@@ -377,7 +381,9 @@ def run_ours(args):
             "config": {"workload": args.workload, "n": g.n, "m": g.m, "degeneracy": results[-1].degeneracy,
                        "maximal_cliques": count, "hash": "0x%016x" % results[-1].hash,
                        "tree_nodes": results[-1].tree_nodes, "donations": results[-1].donations,
-                       "pivot": "AUTO (Sec. IV-D: IPX when max degree / degeneracy <= 200)",
+                       "pivot": {"auto": "AUTO (Sec. IV-D: IPX when max degree / degeneracy <= 200)",
+                                 "ip": "IP (pivot from P u X_P)",
+                                 "ipx": "IPX (pivot from P u X)"}[args.pivot],
                        "ms_prep": results[-1].ms_prep, "ms_traverse": results[-1].ms_traverse,
                        "classes": st["classes"], "peel_rounds": st["peel_rounds"],
                        "l2": "flushed before every step by a 256 MiB device write",
