@@ -141,19 +141,33 @@ __device__ void block_bitonic(int *a, int len) {
     }
 }
 
-// Once at most this many vertices remain at a level start, block 0 finishes
-// the peel alone (block barriers instead of grid barriers); the other blocks
-// return. The rounds, ranks and core numbers are the same either way.
-constexpr int kSoloRemaining = 16384;
+// Level-synchronous peel (Sec. II-C). At a level start k = max(k, smallest
+// remaining degree) and S = every remaining vertex of degree <= k; each
+// sub-round removes S (core number k) and the next S is the set of vertices
+// whose degree fell to k while it was removed. Ranks follow the removal
+// sub-round, then ascending vertex id inside a sub-round.
+//
+// One grid barrier per sub-round: a vertex is marked removed (rank = 0, core
+// = k) and appended to the next sub-round's segment of `order` by the thread
+// whose decrement took its degree from k + 1 to k, so nothing needs a second
+// pass. Decrements are unconditional: a removed vertex already has degree
+// <= k and never reaches k + 1 again. The three sub-round counters form a
+// ring, so the one that is reset is never the one being read or filled.
+// Segments longer than kSmallSort are put in id order here through a bitmap;
+// shorter ones, and all final ranks, are done by k_peel_rank afterwards.
+//
+// When the live degree sum at a level start is at most kSoloDegrees, block 0
+// finishes alone (block barriers instead of grid barriers); the other blocks
+// return. Removal order and core numbers are the same either way.
+constexpr long long kSoloDegrees = 32768;
 
 __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp, const int32_t *col,
                                                        int32_t *deg, int32_t *rank, int32_t *core,
                                                        int32_t *order, int32_t *remA, int32_t *remB,
-                                                       int32_t *SA, int32_t *SB, unsigned *bitmap,
-                                                       int *blocksums, PeelCtl *ctl, int *status,
-                                                       uint64_t timeout_ns) {
+                                                       int32_t *segstart, unsigned *bitmap, int *blocksums,
+                                                       PeelCtl *ctl, int *status, uint64_t timeout_ns) {
     __shared__ int sh[64];
-    __shared__ int ssort[kSmallSort];
+    __shared__ long long shl[32];
     const uint64_t deadline = globaltimer_ns() + timeout_ns;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
@@ -177,11 +191,42 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     }
     if (!barrier()) return;
 
-    for (;;) {
-        if (vload(&ctl->next) >= n) break;
-        const int nrem = vload(&ctl->nrem);
-        if (!solo && nrem <= kSoloRemaining) {
-            // every block read the same nrem after the last grid barrier
+    // every block keeps the same copies of these
+    int k = 0, next = 0, nrem = n, t = 0, L = 0;
+    bool remsel = false;
+    while (next < n) {
+        const int32_t *rem = remsel ? remB : remA;
+        int32_t *rem2 = remsel ? remA : remB;
+        // level start: smallest live degree and the live degree sum
+        int lmin = INT_MAX;
+        long long lsum = 0;
+        for (int64_t i = tid; i < nrem; i += nth) {
+            const int v = rem[i];
+            if (rank[v] < 0) {
+                const int d = deg[v];
+                lmin = min(lmin, d);
+                lsum += d;
+            }
+        }
+        lmin = block_reduce_min<kPeelThreads>(lmin, sh);
+        for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+        if (lane == 0) shl[threadIdx.x >> 5] = lsum;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long bs = 0;
+            for (int w = 0; w < kPeelThreads / 32; w++) bs += shl[w];
+            if (lmin != INT_MAX) atomicMin(&ctl->minval[L & 1], lmin);
+            if (bs) atomicAdd(&ctl->sumdeg[L & 1], (unsigned long long)bs);
+            // read by every block before the previous level's second barrier
+            if (bid == 0) {
+                ctl->minval[(L + 1) & 1] = INT_MAX;
+                ctl->sumdeg[(L + 1) & 1] = 0ull;
+            }
+        }
+        if (!barrier()) return;
+        k = max(k, vload(&ctl->minval[L & 1]));
+        if (!solo && (long long)*(volatile unsigned long long *)&ctl->sumdeg[L & 1] <= kSoloDegrees) {
+            // every block read the same sum after the barrier
             if (blockIdx.x != 0) return;
             solo = true;
             tid = threadIdx.x;
@@ -191,20 +236,9 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             nblocks = 1;
             bid = 0;
         }
-        int32_t *rem = vload(&ctl->remsel) ? remB : remA;
-        int32_t *rem2 = vload(&ctl->remsel) ? remA : remB;
-        // level start: k = max(k, min remaining degree)
-        int lmin = INT_MAX;
-        for (int64_t i = tid; i < nrem; i += nth) {
-            int v = rem[i];
-            if (rank[v] < 0) lmin = min(lmin, deg[v]);
-        }
-        lmin = block_reduce_min<kPeelThreads>(lmin, sh);
-        if (threadIdx.x == 0 && lmin != INT_MAX) atomicMin(&ctl->minval, lmin);
-        if (!barrier()) return;
-        const int k = max(vload(&ctl->k), vload(&ctl->minval));
         {
-            int32_t *S = vload(&ctl->sel) ? SB : SA;
+            // S of the level into order[next..), the rest into the next remaining list
+            int *cnt = &ctl->cnt[t % 3];
             const int64_t lim = (nrem + 31) / 32 * 32;
             for (int64_t i = tid; i < lim; i += nth) {
                 bool live = false, inS = false;
@@ -214,39 +248,38 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     live = rank[v] < 0;
                     inS = live && deg[v] <= k;
                 }
-                int ps = warp_push(&ctl->ns, inS);
-                if (inS) S[ps] = v;
-                int pk = warp_push(&ctl->nrem2, live && !inS);
+                const int ps = warp_push(cnt, inS);
+                if (inS) {
+                    rank[v] = 0;
+                    core[v] = k;
+                    order[next + ps] = v;
+                }
+                const int pk = warp_push(&ctl->nrem2[L & 1], live && !inS);
                 if (live && !inS) rem2[pk] = v;
             }
+            // read by every block before this level's first barrier
+            if (bid == 0 && threadIdx.x == 0) ctl->nrem2[(L + 1) & 1] = 0;
         }
         if (!barrier()) return;
-        if (bid == 0 && threadIdx.x == 0) {
-            ctl->k = k;
-            ctl->minval = INT_MAX;
-            ctl->remsel ^= 1;
-            ctl->nrem = ctl->nrem2;
-            ctl->nrem2 = 0;
-        }
-        if (!barrier()) return;
+        nrem = vload(&ctl->nrem2[L & 1]);
+        remsel = !remsel;
+        L++;
 
-        // sub-rounds at level k: S_t = remaining vertices with degree <= k
+        // sub-rounds at level k
         for (;;) {
-            const int ns = vload(&ctl->ns);
+            const int ns = vload(&ctl->cnt[t % 3]);
             if (ns == 0) break;
-            int32_t *S = vload(&ctl->sel) ? SB : SA;
-            int32_t *S2 = vload(&ctl->sel) ? SA : SB;
-            // ranks inside a sub-round follow ascending vertex id
-            if (ns <= kSmallSort) {
-                if (bid == 0) {
-                    for (int i = threadIdx.x; i < ns; i += blockDim.x) ssort[i] = S[i];
-                    __syncthreads();
-                    block_bitonic(ssort, ns);
-                    for (int i = threadIdx.x; i < ns; i += blockDim.x) S[i] = ssort[i];
-                }
-            } else {
+            if (bid == 0 && threadIdx.x == 0) {
+                // cnt[(t+2)%3] held the previous sub-round's size, read by every block
+                // before the last barrier
+                ctl->cnt[(t + 2) % 3] = 0;
+                segstart[t] = next;
+            }
+            int32_t *S = order + next;
+            if (ns > kSmallSort) {
+                // ascending id through a bitmap: mark, count per block chunk, compact
                 for (int64_t i = tid; i < ns; i += nth) {
-                    int v = S[i];
+                    const int v = S[i];
                     atomicOr(&bitmap[v >> 5], 1u << (v & 31));
                 }
                 if (!barrier()) return;
@@ -262,56 +295,74 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 for (int b = threadIdx.x; b < bid; b += blockDim.x) off += blocksums[b];
                 off = block_reduce_sum<kPeelThreads>(off, sh);
                 for (int t0 = w_lo; t0 < w_hi; t0 += blockDim.x) {
-                    int w = t0 + threadIdx.x;
+                    const int w = t0 + threadIdx.x;
                     unsigned bits = (w < w_hi) ? bitmap[w] : 0u;
                     int tot;
-                    int pre = block_scan_excl<kPeelThreads>(__popc(bits), sh, &tot);
+                    const int pre = block_scan_excl<kPeelThreads>(__popc(bits), sh, &tot);
                     int pos = off + pre;
                     while (bits) {
-                        int b = __ffs(bits) - 1;
+                        const int b = __ffs(bits) - 1;
                         bits &= bits - 1;
                         S[pos++] = w * 32 + b;
                     }
                     if (w < w_hi) bitmap[w] = 0u;
                     off += tot;
                 }
+                if (!barrier()) return;
             }
-            if (!barrier()) return;
-            const int base = vload(&ctl->next);
-            for (int64_t i = tid; i < ns; i += nth) {
-                int v = S[i];
-                rank[v] = base + (int)i;
-                core[v] = k;
-                order[base + i] = v;
-            }
-            if (!barrier()) return;
+            // remove S: the vertices whose degree falls to k form the next sub-round
+            int *cn = &ctl->cnt[(t + 1) % 3];
+            int32_t *S2 = S + ns;
             for (int64_t i = gwarp; i < ns; i += nwarps) {
                 const int v = S[i];
                 const int b = rp[v], e = rp[v + 1];
                 for (int j0 = b; j0 < e; j0 += 32) {
-                    int j = j0 + lane;
+                    const int j = j0 + lane;
                     bool push = false;
                     int u = 0;
                     if (j < e) {
                         u = col[j];
-                        if (rank[u] < 0) {
-                            int old = atomicSub(&deg[u], 1);
-                            push = (old == k + 1);
-                        }
+                        push = atomicSub(&deg[u], 1) == k + 1;
                     }
-                    int p = warp_push(&ctl->ns2, push);
-                    if (push) S2[p] = u;
+                    const int p = warp_push(cn, push);
+                    if (push) {
+                        rank[u] = 0;
+                        core[u] = k;
+                        S2[p] = u;
+                    }
                 }
             }
             if (!barrier()) return;
-            if (bid == 0 && threadIdx.x == 0) {
-                ctl->next += ns;
-                ctl->ns = ctl->ns2;
-                ctl->ns2 = 0;
-                ctl->sel ^= 1;
-                ctl->rounds++;
+            next += ns;
+            t++;
+        }
+    }
+    if (bid == 0 && threadIdx.x == 0) {
+        ctl->next = next;
+        ctl->rounds = t;
+        ctl->k = k;
+    }
+}
+
+// Final ranks: sort each short sub-round segment of `order` by vertex id (the
+// long ones are sorted already), then rank[order[i]] = i.
+__global__ void __launch_bounds__(kPeelThreads) k_peel_rank(int n, const int32_t *segstart, const PeelCtl *ctl,
+                                                            int32_t *order, int32_t *rank) {
+    __shared__ int ssort[kSmallSort];
+    const int rounds = ctl->rounds;
+    for (int r = blockIdx.x; r < rounds; r += gridDim.x) {
+        const int a = segstart[r], b = r + 1 < rounds ? segstart[r + 1] : n;
+        const int len = b - a;
+        if (len > 1 && len <= kSmallSort) {
+            for (int i = threadIdx.x; i < len; i += blockDim.x) ssort[i] = order[a + i];
+            block_bitonic(ssort, len);
+            for (int i = threadIdx.x; i < len; i += blockDim.x) {
+                order[a + i] = ssort[i];
+                rank[ssort[i]] = a + i;
             }
-            if (!barrier()) return;
+            __syncthreads();
+        } else {
+            for (int i = a + threadIdx.x; i < b; i += blockDim.x) rank[order[i]] = i;
         }
     }
 }
@@ -633,25 +684,29 @@ cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int blocks = sm_count * (per_sm < 2 ? per_sm : 2);
     if (blocks > b.max_blocks) blocks = b.max_blocks;
-    void *args[] = {(void *)&n,        (void *)&rp,       (void *)&col,       (void *)&b.deg,
-                    (void *)&b.rank,   (void *)&b.core,   (void *)&b.order,   (void *)&b.remA,
-                    (void *)&b.remB,   (void *)&b.SA,     (void *)&b.SB,      (void *)&b.bitmap,
-                    (void *)&b.blocksums, (void *)&b.ctl, (void *)&b.status, (void *)&timeout_ns};
+    int32_t *segstart = b.SA;
+    void *args[] = {(void *)&n,        (void *)&rp,      (void *)&col,         (void *)&b.deg,
+                    (void *)&b.rank,   (void *)&b.core,  (void *)&b.order,     (void *)&b.remA,
+                    (void *)&b.remB,   (void *)&segstart, (void *)&b.bitmap,   (void *)&b.blocksums,
+                    (void *)&b.ctl,    (void *)&b.status, (void *)&timeout_ns};
     count_launch();
-    return cudaLaunchCooperativeKernel((void *)k_peel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
+    e = cudaLaunchCooperativeKernel((void *)k_peel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
+    if (e != cudaSuccess) return e;
+    k_peel_rank<<<2 * sm_count, kPeelThreads, 0, s>>>(n, segstart, b.ctl, b.order, b.rank);
+    count_launch();
+    return cudaGetLastError();
 }
 
 __global__ void k_peel_init(PeelCtl *ctl, int n) {
     ctl->k = 0;
     ctl->next = 0;
-    ctl->ns = 0;
-    ctl->ns2 = 0;
-    ctl->nrem = n;
-    ctl->nrem2 = 0;
-    ctl->minval = INT_MAX;
     ctl->rounds = 0;
-    ctl->sel = 0;
-    ctl->remsel = 0;
+    for (int i = 0; i < 3; i++) ctl->cnt[i] = 0;
+    for (int i = 0; i < 2; i++) {
+        ctl->nrem2[i] = 0;
+        ctl->minval[i] = INT_MAX;
+        ctl->sumdeg[i] = 0ull;
+    }
     ctl->bar.count = 0;
     ctl->bar.gen = 0;
 }

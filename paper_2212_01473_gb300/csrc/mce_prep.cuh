@@ -5,12 +5,18 @@
 namespace mce {
 
 struct PeelCtl {
-    int k, next, ns, ns2, nrem, nrem2, minval, rounds, sel, remsel, pad[6];
+    int k, next, rounds;  // written at the end of the peel
+    int cnt[3];           // sub-round sizes, a ring indexed by sub-round % 3
+    int nrem2[2];         // next remaining-list size, by level parity
+    int minval[2];        // smallest live degree at a level start, by level parity
+    unsigned long long sumdeg[2];  // live degree sum at a level start, by level parity
     GridBar bar;
 };
 
 struct PeelBufs {
-    int32_t *deg, *rank, *core, *order, *remA, *remB, *SA, *SB;
+    int32_t *deg, *rank, *core, *order, *remA, *remB;
+    int32_t *SA;  // n ints: start of each removal sub-round in order
+    int32_t *SB;  // unused
     unsigned *bitmap;  // ceil(n/32) words, zero on entry and on exit
     int *blocksums;    // max_blocks
     PeelCtl *ctl;
