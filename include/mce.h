@@ -230,7 +230,8 @@ typedef struct {
      * (candidates scored), 2 branch + child sets (tree nodes), 3 leaf
      * maximality tests (excluded rows tested), 4 excluded-set partition
      * (rows moved), 5 worker-list donations (donations), 6 idle wait
-     * (subtrees received), 7 unused */
+     * (subtrees received), 7 reloading the parent level on backtrack
+     * (backtracks) */
     uint64_t phase_cycles[MCE_STATS_PHASES];
     uint64_t phase_counts[MCE_STATS_PHASES];
 } mce_stats;

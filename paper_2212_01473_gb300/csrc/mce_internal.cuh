@@ -129,6 +129,7 @@ enum Phase : int {
     PH_PARTITION = 4,  // X_X partition on descent; count = X_X rows moved
     PH_DONATE = 5,     // worker-list checks and donations; count = donations
     PH_IDLE = 6,       // waiting in the worker list; count = subtrees received
+    PH_POP = 7,        // reloading the parent level on backtrack; count = backtracks
     kNumPhases = 8
 };
 

@@ -528,24 +528,46 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     t_nodes++;
                     if (own) {
                         curP[g.gl] = p;
-                        curPX[g.gl] = p | xp;
+                        if (GW > 1) curPX[g.gl] = p | xp;
                     }
                     const int np = grp_sum(g, red, __popc(p));
                     const int xany = grp_or(g, red, xp != 0u);
-                    g.sync();
                     // candidate list P u X_P in ascending index
-                    if (g.warp == 0) {
-                        int nc = 0;
-                        for (int w = 0; w < W; w++) {
-                            const uint32_t bits = curPX[w];
-                            if ((bits >> g.lane) & 1u)
-                                cand[nc + __popc(bits & ((1u << g.lane) - 1u))] = w * 32 + g.lane;
-                            nc += __popc(bits);
+                    int nc;
+                    if (GW == 1) {
+                        // one warp owns every word: each owner writes its word's
+                        // candidates at its exclusive prefix of the popcounts
+                        const uint32_t u = own ? (p | xp) : 0u;
+                        const int c = __popc(u);
+                        int inc = c;
+#pragma unroll
+                        for (int o = 1; o < WP; o <<= 1) {
+                            const int y = __shfl_up_sync(0xffffffffu, inc, o);
+                            if (g.lane >= o) inc += y;
                         }
-                        if (g.lane == 0) misc[2] = nc;
+                        nc = __shfl_sync(0xffffffffu, inc, WP - 1);
+                        int pos = inc - c;
+                        uint32_t bits = u;
+                        while (bits) {
+                            cand[pos++] = g.gl * 32 + __ffs(bits) - 1;
+                            bits &= bits - 1;
+                        }
+                        __syncwarp();
+                    } else {
+                        g.sync();
+                        if (g.warp == 0) {
+                            int n = 0;
+                            for (int w = 0; w < W; w++) {
+                                const uint32_t bits = curPX[w];
+                                if ((bits >> g.lane) & 1u)
+                                    cand[n + __popc(bits & ((1u << g.lane) - 1u))] = w * 32 + g.lane;
+                                n += __popc(bits);
+                            }
+                            if (g.lane == 0) misc[2] = n;
+                        }
+                        g.sync();
+                        nc = misc[2];
                     }
-                    g.sync();
-                    const int nc = misc[2];
                     // Pivot: the candidate with the largest |P n N(u)|, ties to the
                     // smaller degeneracy rank. P u X_P candidates are keyed
                     // score << 16 | (0xffff - local index) (local index order is rank
@@ -640,6 +662,13 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     lpx = (int)lv[Lvl<WP>::LPX];
                     npend = (int)lv[Lvl<WP>::NPEND];
                     S = (uint64_t)lv[Lvl<WP>::SLO] | ((uint64_t)lv[Lvl<WP>::SHI] << 32);
+                    if (pc.on) {
+                        // wait for the reloads so that their latency lands in this phase
+                        const uint32_t used = p ^ xp ^ b ^ (uint32_t)lpx ^ (uint32_t)npend ^ (uint32_t)S;
+                        asm volatile("" ::"r"(used));
+                        pc.stop(PH_POP);
+                        pc.count(PH_POP, 1);
+                    }
                     continue;
                 }
                 const int v = (int)(~bsel);
@@ -793,26 +822,27 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         lv[Lvl<WP>::SHI] = (uint32_t)(S >> 32);
                     }
                     int out = 0, nout = 0;
-                    for (int it = 0; it < lpx; it += GT) {
-                        const int idx = it + g.gl;
-                        const bool valid = idx < lpx;
-                        const uint32_t e = valid ? xidx[idx] : 0u;
-                        const bool surv = valid && (xrows[(size_t)e * WP + vw] & vb) != 0u;
-                        int ts, tn;
-                        const int ps = grp_prefix(g, red, surv, &ts);
-                        const int pn = grp_prefix(g, red, valid && !surv, &tn);
-                        if (surv) xidx[out + ps] = e;
-                        else if (valid) xscr[nout + pn] = e;
-                        out += ts;
-                        nout += tn;
-                    }
-                    if (nout > 0) {
-                        __threadfence_block();
+                    if (lpx > 0) {
+                        for (int it = 0; it < lpx; it += GT) {
+                            const int idx = it + g.gl;
+                            const bool valid = idx < lpx;
+                            const uint32_t e = valid ? xidx[idx] : 0u;
+                            const bool surv = valid && (xrows[(size_t)e * WP + vw] & vb) != 0u;
+                            int ts, tn;
+                            const int ps = grp_prefix(g, red, surv, &ts);
+                            const int pn = grp_prefix(g, red, valid && !surv, &tn);
+                            if (surv) xidx[out + ps] = e;
+                            else if (valid) xscr[nout + pn] = e;
+                            out += ts;
+                            nout += tn;
+                        }
+                        // the group barrier orders these arena writes for the whole group
+                        if (nout > 0) {
+                            g.sync();
+                            for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
+                        }
                         g.sync();
-                        for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
                     }
-                    __threadfence_block();
-                    g.sync();
                     pc.stop(PH_PARTITION);
                     pc.count(PH_PARTITION, (unsigned long long)lpx);
                     p = cp;

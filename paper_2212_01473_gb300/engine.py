@@ -67,7 +67,7 @@ class mce_stats(ctypes.Structure):
                 ("phase_counts", ctypes.c_uint64 * 8)]
 
 
-PHASES = ["setup", "pivot", "branch", "leaf", "partition", "donate", "idle", "unused"]
+PHASES = ["setup", "pivot", "branch", "leaf", "partition", "donate", "idle", "backtrack"]
 
 _lib = None
 
@@ -337,8 +337,8 @@ def mce_get_stats(h: Handle) -> dict:
                      "group_warps": st.class_group_warps[i], "ms": st.class_ms[i]} for i in range(k)],
         "kernel_launches": int(st.kernel_launches),
         "peel_rounds": int(st.peel_rounds),
-        "phase_cycles": {PHASES[i]: int(st.phase_cycles[i]) for i in range(7)},
-        "phase_counts": {PHASES[i]: int(st.phase_counts[i]) for i in range(7)},
+        "phase_cycles": {PHASES[i]: int(st.phase_cycles[i]) for i in range(8)},
+        "phase_counts": {PHASES[i]: int(st.phase_counts[i]) for i in range(8)},
     }
 
 
