@@ -97,6 +97,19 @@ class Clocks:
                 "reasons": reasons, "samples": len(rows)}
 
 
+TRAVERSAL_SOURCES = ("mce_traverse.cuh", "mce_trav_inst.cuh", "mce_internal.cuh", "mce_trav_mid.cu")
+
+
+def traversal_source_hash():
+    """sha256 over the sources that define the traversal kernels."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAVERSAL_SOURCES:
+        with open(os.path.join(ROOT, "paper_2212_01473_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def load_golden(name):
     p = os.path.join(ROOT, "tests", "golden", name + ".json")
     if os.path.exists(p):
@@ -371,8 +384,14 @@ def run_ours(args):
         if os.path.exists(prof):
             with open(prof) as f:
                 tr = json.load(f)
-            if tr.get("kernel_wp") == dom["wp"]:
+            # counters taken on another build of the kernel do not describe this one
+            if tr.get("kernel_wp") == dom["wp"] and tr.get("source_sha256") == traversal_source_hash():
                 roofline["traffic"] = tr.get("dram_bytes_per_launch")
+                roofline["traffic_note"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (%s)" % (
+                    os.path.relpath(prof, ROOT))
+            else:
+                roofline["traffic_note"] = "null: the traversal kernel changed since %s was captured" % (
+                    os.path.relpath(prof, ROOT))
 
     line = {"metric": "maximal cliques/sec", "value": value, "unit": "cliques/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
