@@ -317,7 +317,6 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
     if (!status) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
     CK(cudaMemsetAsync(status, 0, 16, g->stream));
     if (n == 0) {
-        int32_t zero = 0;
         if (dev_in) {
             int32_t v0 = 0;
             CK(cudaMemcpyAsync(&v0, row_ptr, 4, cudaMemcpyDeviceToHost, g->stream));
@@ -327,7 +326,6 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
             rc = fail(MCE_EINVAL, "row_ptr[0] must be 0 and m 0 for n = 0");
             goto cleanup;
         }
-        (void)zero;
     }
     // ------------------------------------------------------------- validate
     CK(launch_validate(n, d_rp, d_col, 2 * m, status, g->stream, false));
