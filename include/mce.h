@@ -92,7 +92,7 @@ typedef struct {
     int32_t order;         /* MCE_ORDER_* */
     int32_t worker_list;   /* 1 = idle workers receive donated subtrees (Sec. III-C), 0 = off */
     int32_t donate_min_p;  /* donate a child only if its |P| >= this (Sec. III-C uses 10); 0 = automatic:
-                            max(10, largest |P0| of the width class / 8) */
+                            max(10, largest |P0| of the width class / 10) */
     int32_t blocks;        /* persistent blocks per width class; 0 = all that fit on the GPU */
     int32_t donate_policy; /* which busy groups may donate a child (Sec. III-C): MCE_DONATE_* */
     int32_t stats;         /* 1 = collect per-phase SM cycle counters (see mce_stats); slows the run */

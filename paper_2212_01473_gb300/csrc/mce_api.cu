@@ -647,10 +647,10 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         a.pivot_ipx = opts.pivot == MCE_PIVOT_IPX ||
                       (opts.pivot == MCE_PIVOT_AUTO && g->d > 0 && (double)g->max_deg / g->d <= 200.0);
         a.worker_list = opts.worker_list ? 1 : 0;
-        // 0 = automatic: a donated child must have at least 1/8 of the
+        // 0 = automatic: a donated child must have at least 1/10 of the
         // class's widest root set, and never fewer than 10 candidates (Sec. III-C)
         const int dmp = (t && t->dmp > 0) ? t->dmp : opts.donate_min_p;
-        a.donate_min_p = dmp > 0 ? dmp : std::max(10, k.rows / 8);
+        a.donate_min_p = dmp > 0 ? dmp : std::max(10, k.rows / 10);
         a.donate_policy = (t && t->policy >= 0) ? t->policy : opts.donate_policy;
         a.root_chunk = 1;
         a.stats = opts.stats ? 1 : 0;
@@ -888,10 +888,10 @@ extern "C" int mce_autotune(mce_graph *g, const mce_opts *base, double budget_ms
         g->tuned[c] = Tuned{};
         if (g->class_count[c] == 0) continue;
         const int rows = g->class_rows[c];
-        const int A = std::max(10, rows / 8);
+        const int A = std::max(10, rows / 10);
         const Tuned cands[] = {{A, MCE_DONATE_EITHER, 0},
-                               {std::max(10, rows / 16), MCE_DONATE_EITHER, 0},
-                               {std::max(10, rows / 4), MCE_DONATE_EITHER, 0},
+                               {std::max(10, rows / 20), MCE_DONATE_EITHER, 0},
+                               {std::max(10, rows / 5), MCE_DONATE_EITHER, 0},
                                {A, MCE_DONATE_PAPER, 0},
                                {A, MCE_DONATE_ANY, 0},
                                {A, MCE_DONATE_EITHER, g->sm_count}};

@@ -115,7 +115,8 @@ __device__ __forceinline__ int block_scan_excl(int x, int *sh, int *total) {
 
 // ---------------------------------------------------------------- peel
 
-constexpr int kPeelThreads = 512;
+constexpr int kPeelThreads = 1024;  // one block per SM: fewer arrivals per grid barrier
+constexpr int kRankThreads = 512;
 constexpr int kSmallSort = 4096;
 
 __device__ __forceinline__ int vload(const int *p) { return *(volatile const int *)p; }
@@ -160,6 +161,8 @@ __device__ void block_bitonic(int *a, int len) {
 // finishes alone (block barriers instead of grid barriers); the other blocks
 // return. Removal order and core numbers are the same either way.
 constexpr long long kSoloDegrees = 32768;
+// adjacency lists longer than this are removed by a whole block
+constexpr int kHeavyDeg = 256;
 
 __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp, const int32_t *col,
                                                        int32_t *deg, int32_t *rank, int32_t *core,
@@ -310,27 +313,56 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 }
                 if (!barrier()) return;
             }
-            // remove S: the vertices whose degree falls to k form the next sub-round
+            // remove S: the vertices whose degree falls to k form the next sub-round.
+            // A vertex of degree <= kHeavyDeg is one warp's work (two 32-edge
+            // chunks in flight); a longer adjacency list is strided over a block.
             int *cn = &ctl->cnt[(t + 1) % 3];
             int32_t *S2 = S + ns;
+            auto remove_edge = [&](bool valid, int j) {
+                bool push = false;
+                int u = 0;
+                if (valid) {
+                    u = col[j];
+                    push = atomicSub(&deg[u], 1) == k + 1;
+                }
+                const int p = warp_push(cn, push);
+                if (push) {
+                    rank[u] = 0;
+                    core[u] = k;
+                    S2[p] = u;
+                }
+            };
             for (int64_t i = gwarp; i < ns; i += nwarps) {
                 const int v = S[i];
                 const int b = rp[v], e = rp[v + 1];
-                for (int j0 = b; j0 < e; j0 += 32) {
-                    const int j = j0 + lane;
-                    bool push = false;
-                    int u = 0;
-                    if (j < e) {
-                        u = col[j];
-                        push = atomicSub(&deg[u], 1) == k + 1;
+                if (e - b > kHeavyDeg) continue;
+                for (int j0 = b; j0 < e; j0 += 64) {
+                    const int ja = j0 + lane, jb = ja + 32;
+                    const bool va = ja < e, vb = jb < e;
+                    int ua = 0, ub = 0;
+                    if (va) ua = col[ja];
+                    if (vb) ub = col[jb];
+                    const bool pa = va && atomicSub(&deg[ua], 1) == k + 1;
+                    const bool pb = vb && atomicSub(&deg[ub], 1) == k + 1;
+                    const int qa = warp_push(cn, pa);
+                    if (pa) {
+                        rank[ua] = 0;
+                        core[ua] = k;
+                        S2[qa] = ua;
                     }
-                    const int p = warp_push(cn, push);
-                    if (push) {
-                        rank[u] = 0;
-                        core[u] = k;
-                        S2[p] = u;
+                    const int qb = warp_push(cn, pb);
+                    if (pb) {
+                        rank[ub] = 0;
+                        core[ub] = k;
+                        S2[qb] = ub;
                     }
                 }
+            }
+            for (int64_t i = bid; i < ns; i += nblocks) {
+                const int v = S[i];
+                const int b = rp[v], e = rp[v + 1];
+                if (e - b <= kHeavyDeg) continue;
+                for (int j0 = b; j0 < e; j0 += blockDim.x) remove_edge(j0 + (int)threadIdx.x < e, j0 + threadIdx.x);
             }
             if (!barrier()) return;
             next += ns;
@@ -346,7 +378,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
 
 // Final ranks: sort each short sub-round segment of `order` by vertex id (the
 // long ones are sorted already), then rank[order[i]] = i.
-__global__ void __launch_bounds__(kPeelThreads) k_peel_rank(int n, const int32_t *segstart, const PeelCtl *ctl,
+__global__ void __launch_bounds__(kRankThreads) k_peel_rank(int n, const int32_t *segstart, const PeelCtl *ctl,
                                                             int32_t *order, int32_t *rank) {
     __shared__ int ssort[kSmallSort];
     const int rounds = ctl->rounds;
@@ -682,7 +714,7 @@ cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &
     cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, kPeelThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    int blocks = sm_count * (per_sm < 2 ? per_sm : 2);
+    int blocks = sm_count;  // per_sm >= 1 checked above
     if (blocks > b.max_blocks) blocks = b.max_blocks;
     int32_t *segstart = b.SA;
     void *args[] = {(void *)&n,        (void *)&rp,      (void *)&col,         (void *)&b.deg,
@@ -692,7 +724,7 @@ cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &
     count_launch();
     e = cudaLaunchCooperativeKernel((void *)k_peel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
     if (e != cudaSuccess) return e;
-    k_peel_rank<<<2 * sm_count, kPeelThreads, 0, s>>>(n, segstart, b.ctl, b.order, b.rank);
+    k_peel_rank<<<2 * sm_count, kRankThreads, 0, s>>>(n, segstart, b.ctl, b.order, b.rank);
     count_launch();
     return cudaGetLastError();
 }
