@@ -103,20 +103,23 @@ __host__ __device__ inline size_t smem_bytes(const GrpSmem &L, int groups_per_bl
     return L.group0 + (size_t)groups_per_block * L.total;
 }
 
-// Arena words per group: [stack if global][A rows][X rows][xidx][xscr][xrank].
+// Arena words per group: [stack if global][A rows][X rows][xidx][xscr][xrank]
+// [xcomp].
 // The A region holds A itself when it lives in global memory, else it is the
 // landing area where a donor writes A for this group when it is a receiver.
 __host__ __device__ inline size_t arena_words(int wp, int rows, int xcap, bool a_global, bool stack_smem) {
     size_t w = 0;
     if (!stack_smem) w += stack_words(wp, rows);
     w += (size_t)rows * wp;
-    w += (size_t)xcap * wp + 3 * (size_t)xcap;
+    w += (size_t)xcap * wp + 4 * (size_t)xcap;
     (void)a_global;
     return align_up(w, 4);
 }
 
 struct ArenaPtrs {
-    uint32_t *stk, *A, *xrows, *xidx, *xscr, *xrank;  // xrank[slot]: degeneracy rank of that X_X row's vertex
+    uint32_t *stk, *A, *xrows, *xidx, *xscr;
+    uint32_t *xrank;  // xrank[slot]: degeneracy rank of that X_X row's vertex
+    uint32_t *xcomp;  // xcomp[slot]: that row over a compact subtree's index space
 };
 
 __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, int xcap, bool stack_smem) {
@@ -130,6 +133,7 @@ __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, 
     a.xidx = q + (size_t)xcap * wp;
     a.xscr = a.xidx + xcap;
     a.xrank = a.xscr + xcap;
+    a.xcomp = a.xrank + xcap;
     return a;
 }
 
@@ -221,6 +225,70 @@ __device__ __forceinline__ int grp_prefix(const Grp<GW> &g, int *red, bool pred,
     return off + in_warp;
 }
 
+// Writes the set bits of a bitset held one word per thread (thread gl owns
+// word gl < WP) to list[] as indices in ascending order and returns their
+// number. Each owner writes its word's bits at its exclusive prefix of the
+// popcounts; the list is complete for the whole group on return.
+template <int WP, int GW>
+__device__ __forceinline__ int grp_bits_to_list(const Grp<GW> &g, int *red, uint32_t word, int32_t *list) {
+    const int c = __popc(word);
+    int inc = c;
+    constexpr int span = GW == 1 ? WP : 32;
+#pragma unroll
+    for (int o = 1; o < span; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (g.lane >= o) inc += y;
+    }
+    int pre, tot;
+    if (GW == 1) {
+        tot = __shfl_sync(0xffffffffu, inc, WP - 1);
+        pre = inc - c;
+    } else {
+        if (g.lane == 31) red[g.warp] = inc;
+        g.sync();
+        int off = 0;
+        tot = 0;
+#pragma unroll
+        for (int i = 0; i < GW; i++) {
+            const int t = red[i];
+            if (i < g.warp) off += t;
+            tot += t;
+        }
+        g.sync();
+        pre = off + inc - c;
+    }
+    uint32_t bits = word;
+    while (bits) {
+        list[pre++] = g.gl * 32 + __ffs(bits) - 1;
+        bits &= bits - 1;
+    }
+    g.sync();
+    return tot;
+}
+
+// Copies the rows listed in rows[0..nrows) of a WP-word bit matrix.
+template <int WP, int GW>
+__device__ __forceinline__ void grp_copy_rows(const Grp<GW> &g, const int32_t *rows, int nrows, const uint32_t *src,
+                                              uint32_t *dst) {
+    constexpr int GT = 32 * GW;
+    if (WP % 4 == 0) {
+        constexpr int Q = WP / 4;
+        const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
+        uint4 *d4 = reinterpret_cast<uint4 *>(dst);
+        for (int i = g.gl; i < nrows * Q; i += GT) {
+            const int j = i / Q, q = i - j * Q;
+            const size_t at = (size_t)rows[j] * Q + q;
+            d4[at] = s4[at];
+        }
+    } else {
+        for (int i = g.gl; i < nrows * WP; i += GT) {
+            const int j = i / WP, w = i - j * WP;
+            const size_t at = (size_t)rows[j] * WP + w;
+            dst[at] = src[at];
+        }
+    }
+}
+
 // Optional per-phase cycle counters (runtime switch; thread 0 of each group).
 struct PhaseClock {
     bool on;
@@ -281,6 +349,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
     uint32_t *xidx = ar.xidx;
     uint32_t *xscr = ar.xscr;
     uint32_t *xrank = ar.xrank;
+    uint32_t *xcomp = ar.xcomp;
 
     const uint64_t deadline = globaltimer_ns() + C.timeout_ns;
     PhaseClock pc{};
@@ -390,14 +459,14 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             for (int i = g.gl; i < n0; i += GT) p0[i] = prow[i];
             int nx = 0;
             if (have_mail) {
-                // the donor wrote A into the arena's A region and the surviving
-                // X_X rows into the arena's X rows: nothing to rebuild
+                // the donor wrote the A rows of P' u X_P' into the arena's A region
+                // and the surviving X_X rows into the arena's X rows: nothing to
+                // rebuild. Every row the subtree reads (candidates, branches) is
+                // one of those; the other rows are never read.
                 if (!AG) {
-                    const uint4 *src = reinterpret_cast<const uint4 *>(ar.A);
-                    uint4 *dst = reinterpret_cast<uint4 *>(Arow);
-                    for (int i = g.gl; i < n0 * WP / 4; i += GT) dst[i] = src[i];
-                    if (WP % 4 != 0)
-                        for (int i = g.gl; i < n0 * WP; i += GT) Arow[i] = ar.A[i];
+                    const uint32_t want = g.gl < WP ? (mb[4 + WP + g.gl] | mb[4 + 2 * WP + g.gl]) : 0u;
+                    const int nrows = grp_bits_to_list<WP, GW>(g, red, want, cand);
+                    grp_copy_rows<WP, GW>(g, cand, nrows, ar.A, Arow);
                 }
                 nx = (int)mb[2];
                 g.sync();
@@ -512,7 +581,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             pc.stop(PH_SETUP);
 
             // ------------------------------------------------- DFS (Algorithm 2)
-            uint32_t *curP = cur, *curPX = cur + WP;
+            uint32_t *curP = cur;
             int l = l0;
             bool enter = true;
             bool timed_out = false;
@@ -526,48 +595,11 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 }
                 if (enter) {
                     t_nodes++;
-                    if (own) {
-                        curP[g.gl] = p;
-                        if (GW > 1) curPX[g.gl] = p | xp;
-                    }
+                    if (own) curP[g.gl] = p;
                     const int np = grp_sum(g, red, __popc(p));
                     const int xany = grp_or(g, red, xp != 0u);
                     // candidate list P u X_P in ascending index
-                    int nc;
-                    if (GW == 1) {
-                        // one warp owns every word: each owner writes its word's
-                        // candidates at its exclusive prefix of the popcounts
-                        const uint32_t u = own ? (p | xp) : 0u;
-                        const int c = __popc(u);
-                        int inc = c;
-#pragma unroll
-                        for (int o = 1; o < WP; o <<= 1) {
-                            const int y = __shfl_up_sync(0xffffffffu, inc, o);
-                            if (g.lane >= o) inc += y;
-                        }
-                        nc = __shfl_sync(0xffffffffu, inc, WP - 1);
-                        int pos = inc - c;
-                        uint32_t bits = u;
-                        while (bits) {
-                            cand[pos++] = g.gl * 32 + __ffs(bits) - 1;
-                            bits &= bits - 1;
-                        }
-                        __syncwarp();
-                    } else {
-                        g.sync();
-                        if (g.warp == 0) {
-                            int n = 0;
-                            for (int w = 0; w < W; w++) {
-                                const uint32_t bits = curPX[w];
-                                if ((bits >> g.lane) & 1u)
-                                    cand[n + __popc(bits & ((1u << g.lane) - 1u))] = w * 32 + g.lane;
-                                n += __popc(bits);
-                            }
-                            if (g.lane == 0) misc[2] = n;
-                        }
-                        g.sync();
-                        nc = misc[2];
-                    }
+                    const int nc = grp_bits_to_list<WP, GW>(g, red, own ? (p | xp) : 0u, cand);
                     // Pivot: the candidate with the largest |P n N(u)|, ties to the
                     // smaller degeneracy rank. P u X_P candidates are keyed
                     // score << 16 | (0xffff - local index) (local index order is rank
@@ -881,29 +913,45 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                         (C.donate_policy == MCE_DONATE_EITHER ? (others_here || npend >= 1)
                                                                               : (others_here && npend >= 1));
                 if (C.worker_list && pcnt >= C.donate_min_p && may_donate) {
-                    if (g.gl == 0) {
+                    if (g.warp == 0) {
+                        // claim an idle group: the lanes read 32 words of the idle
+                        // bitmap at a time, and the first lane holding a set bit tries
+                        // to take one with atomicAnd (another donor may win the race)
                         int claimed = -1;
-                        if (ld_relaxed(&C.ctl[CTL_IDLE]) > 0) {
+                        const bool any_idle = __shfl_sync(0xffffffffu,
+                                                          g.lane == 0 ? ld_relaxed(&C.ctl[CTL_IDLE]) > 0 : false, 0);
+                        if (any_idle) {
                             const int nwords = (ngroups + 31) >> 5;
-                            for (int qd = 0; qd < nwords && claimed < 0; qd++) {
+                            for (int q0 = 0; q0 < nwords && claimed < 0; q0 += 32) {
+                                const int qd = q0 + g.lane;
                                 const int wi = (gg / 32 + 1 + qd) % nwords;
-                                unsigned bits = *((volatile unsigned *)&C.idle_bits[wi]);
-                                while (bits) {
-                                    const int bb = __ffs(bits) - 1;
-                                    const unsigned old = atomicAnd(&C.idle_bits[wi], ~(1u << bb));
-                                    if (old & (1u << bb)) {
-                                        claimed = wi * 32 + bb;
-                                        break;
+                                const unsigned bits = qd < nwords ? *((volatile unsigned *)&C.idle_bits[wi]) : 0u;
+                                unsigned nz = __ballot_sync(0xffffffffu, bits != 0u);
+                                while (nz && claimed < 0) {
+                                    const int src = __ffs(nz) - 1;
+                                    nz &= nz - 1;
+                                    int got = -1;
+                                    if (g.lane == src) {
+                                        unsigned left = bits;
+                                        while (left) {
+                                            const int bb = __ffs(left) - 1;
+                                            const unsigned old = atomicAnd(&C.idle_bits[wi], ~(1u << bb));
+                                            if (old & (1u << bb)) {
+                                                got = wi * 32 + bb;
+                                                break;
+                                            }
+                                            left = old & ~(1u << bb) & ~((2u << bb) - 1u);
+                                        }
                                     }
-                                    bits &= bits - 1;
+                                    claimed = __shfl_sync(0xffffffffu, got, src);
                                 }
                             }
-                            if (claimed >= 0) {
+                            if (claimed >= 0 && g.lane == 0) {
                                 atomicSub(&C.ctl[CTL_IDLE], 1);
                                 atomicAdd(&C.ctl[CTL_ACTIVE], 1);
                             }
                         }
-                        misc[4] = claimed;
+                        if (g.lane == 0) misc[4] = claimed;
                     }
                     g.sync();
                     const int recv = misc[4];
@@ -926,12 +974,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         // push A and the surviving rows into the receiver's arena
                         const ArenaPtrs ra = arena_at(C.arena + (size_t)recv * C.arena_words_per_group, WP,
                                                       rows_cap, C.x_cap, stack_smem != 0);
-                        if (WP % 4 == 0) {
-                            const uint4 *src = reinterpret_cast<const uint4 *>(Arow);
-                            uint4 *dst = reinterpret_cast<uint4 *>(ra.A);
-                            for (int i = g.gl; i < n0 * WP / 4; i += GT) dst[i] = src[i];
-                        } else {
-                            for (int i = g.gl; i < n0 * WP; i += GT) ra.A[i] = Arow[i];
+                        {
+                            // only the rows of the child's P' u X_P'
+                            const int nrows = grp_bits_to_list<WP, GW>(g, red, own ? (cp | cx) : 0u, cand);
+                            grp_copy_rows<WP, GW>(g, cand, nrows, Arow, ra.A);
                         }
                         for (int i = g.gl; i < out * WP; i += GT) {
                             const int k = i / WP, w = i - k * WP;
