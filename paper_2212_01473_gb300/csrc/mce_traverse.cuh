@@ -1018,6 +1018,267 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     }
                     pc.stop(PH_DONATE);
                 }
+                // ------------------------------ compact subtree
+                // When |P'| + |X_P'| <= 32 the child's whole subtree runs on one-word
+                // sets over the index space L = P' u X_P' (ascending local index, so
+                // ties still go to the smaller rank). Lane i holds the row of L[i]
+                // over L and the ancestors' (P, X_P, branches, X_X end, hash sum) at
+                // depth i; X_X' rows are re-encoded over L once. Node for node this
+                // is the same walk as below, without donations.
+                if (GW == 1 && WP > 1 && pcnt <= 32) {
+                    const int nxc = grp_sum(g, red, __popc(cx));
+                    if (pcnt + nxc <= 32) {
+                        constexpr unsigned FULL = 0xffffffffu;
+                        t_nodes++;  // the child R u {v}
+                        // X_X' = rows of this prefix holding v, moved to the front
+                        auto partition = [&](int n_in, auto holds) -> int {
+                            int out = 0, nout = 0;
+                            for (int it = 0; it < n_in; it += GT) {
+                                const int idx = it + g.gl;
+                                const bool valid = idx < n_in;
+                                const uint32_t e = valid ? xidx[idx] : 0u;
+                                const bool surv = valid && holds(e);
+                                int ts, tn;
+                                const int ps = grp_prefix(g, red, surv, &ts);
+                                const int pn = grp_prefix(g, red, valid && !surv, &tn);
+                                if (surv) xidx[out + ps] = e;
+                                else if (valid) xscr[nout + pn] = e;
+                                out += ts;
+                                nout += tn;
+                            }
+                            if (nout > 0) {
+                                g.sync();
+                                for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
+                            }
+                            g.sync();
+                            return out;
+                        };
+                        int clx = 0;
+                        if (lpx > 0) clx = partition(lpx, [&](uint32_t e) { return (xrows[(size_t)e * WP + vw] & vb) != 0u; });
+                        const int c = grp_bits_to_list<WP, GW>(g, red, own ? (cp | cx) : 0u, cand);
+                        if (own) curP[g.gl] = cp;
+                        __syncwarp();
+                        const bool inl = g.lane < c;
+                        const int Lj = inl ? cand[g.lane] : 0;
+                        const bool inP = inl && ((curP[Lj >> 5] >> (Lj & 31)) & 1u) != 0u;
+                        uint32_t P = __ballot_sync(FULL, inP);
+                        uint32_t X = __ballot_sync(FULL, inl && !inP);
+                        uint32_t row = 0u;
+                        {
+                            const uint32_t *ar_ = Arow + (size_t)Lj * WP;
+#pragma unroll 4
+                            for (int j = 0; j < c; j++) {
+                                const int lj = __shfl_sync(FULL, Lj, j);
+                                row |= ((ar_[lj >> 5] >> (lj & 31)) & 1u) << j;
+                            }
+                            if (!inl) row = 0u;
+                        }
+                        const uint64_t mj = inl ? G.mixid[p0[Lj]] : 0ull;
+                        for (int i = 0; i < clx; i++) {
+                            const uint32_t e = xidx[i];
+                            const bool bit = inl && ((xrows[(size_t)e * WP + (Lj >> 5)] >> (Lj & 31)) & 1u) != 0u;
+                            const uint32_t w = __ballot_sync(FULL, bit);
+                            if (g.lane == 0) xcomp[e] = w;
+                        }
+                        __syncwarp();
+                        auto record = [&](int sz, uint64_t sum) {
+                            if (g.gl == 0) {
+                                t_cnt++;
+                                t_hash += mix64(sum + (uint64_t)sz * kPhi);
+                                if (block_hist) atomicAdd(&hist[sz], 1ull);
+                                else hist[sz] += 1ull;
+                                acc_maxsz = max(acc_maxsz, sz);
+                            }
+                        };
+                        pc.stop(PH_SETUP);
+                        uint32_t sP = 0u, sX = 0u, sB = 0u, B = 0u;
+                        int sL = 0, d = 0;
+                        uint64_t sS = 0ull, cS = S + G.mixid[p0[v]];
+                        const int base = l + 2;  // |R| at compact depth 0
+                        bool centr = true;
+                        for (;;) {
+                            if ((++iters & 1023u) == 0) {
+                                if (__any_sync(FULL, g.lane == 0 && globaltimer_ns() > deadline)) {
+                                    timed_out = true;
+                                    break;
+                                }
+                            }
+                            if (centr) {
+                                centr = false;
+                                // pivot over P u X_P: lane u scores |P n N(u)|, ties to the
+                                // smaller index; IPX also scores the X_X' rows, which win ties
+                                const bool isc = (((P | X) >> g.lane) & 1u) != 0u;
+                                const unsigned key =
+                                    isc ? (((unsigned)__popc(row & P) + 1u) << 8) | (unsigned)(31 - g.lane) : 0u;
+                                const unsigned best = __reduce_max_sync(FULL, key);
+                                const int bsc = (int)(best >> 8) - 1;
+                                uint32_t prow = __shfl_sync(FULL, row, 31 - (int)(best & 255u));
+                                if (C.pivot_ipx && clx > 0) {
+                                    unsigned long long bx = 0ull;
+                                    for (int i0 = 0; i0 < clx; i0 += 32) {
+                                        const int i = i0 + g.lane;
+                                        unsigned long long k2 = 0ull;
+                                        if (i < clx) {
+                                            const uint32_t e = xidx[i];
+                                            k2 = ((unsigned long long)(__popc(xcomp[e] & P) + 1) << 32) |
+                                                 (unsigned long long)(0xffffffffu - xrank[e]);
+                                        }
+                                        for (int o = 16; o; o >>= 1) {
+                                            const unsigned long long y = __shfl_xor_sync(FULL, k2, o);
+                                            k2 = y > k2 ? y : k2;
+                                        }
+                                        bx = k2 > bx ? k2 : bx;
+                                    }
+                                    if ((int)(bx >> 32) - 1 >= bsc) {
+                                        const uint32_t want = 0xffffffffu - (uint32_t)(bx & 0xffffffffull);
+                                        for (int i0 = 0; i0 < clx; i0 += 32) {
+                                            const int i = i0 + g.lane;
+                                            uint32_t e = 0u;
+                                            bool hit = false;
+                                            if (i < clx) {
+                                                e = xidx[i];
+                                                hit = xrank[e] == want;
+                                            }
+                                            const unsigned hm = __ballot_sync(FULL, hit);
+                                            if (hm) {
+                                                prow = xcomp[__shfl_sync(FULL, e, __ffs(hm) - 1)];
+                                                break;
+                                            }
+                                        }
+                                    }
+                                }
+                                B = P & ~prow;
+                                pc.stop(PH_PIVOT);
+                                pc.count(PH_PIVOT, (unsigned long long)__popc(P | X));
+                            }
+                            if (B == 0u) {
+                                if (d == 0) break;
+                                d--;
+                                P = __shfl_sync(FULL, sP, d);
+                                X = __shfl_sync(FULL, sX, d);
+                                B = __shfl_sync(FULL, sB, d);
+                                clx = __shfl_sync(FULL, sL, d);
+                                cS = __shfl_sync(FULL, sS, d);
+                                pc.stop(PH_POP);
+                                pc.count(PH_POP, 1);
+                                continue;
+                            }
+                            const int u = __ffs(B) - 1;
+                            const uint32_t ubit = 1u << u;
+                            const uint32_t ru = __shfl_sync(FULL, row, u);
+                            const uint32_t q = P & ru, qx = X & ru;  // the child's P and X_P
+                            B &= ~ubit;
+                            P &= ~ubit;
+                            X |= ubit;
+                            const int qn = __popc(q);
+                            const uint64_t mu = __shfl_sync(FULL, mj, u);
+                            const int szc = base + d + 1;  // |R u {u}|
+                            pc.stop(PH_BRANCH);
+                            if (qn <= 2) {
+                                t_nodes++;
+                                // the child's X_X rows are those of [0, clx) holding u
+                                if (qn == 0) {
+                                    if (qx == 0u) {
+                                        bool found = false;
+                                        for (int i0 = 0; i0 < clx && !found; i0 += 32) {
+                                            const int i = i0 + g.lane;
+                                            found = __any_sync(FULL, i < clx && ((xcomp[xidx[i]] >> u) & 1u) != 0u);
+                                        }
+                                        if (!found) record(szc, cS + mu);
+                                    }
+                                } else if (qn == 1) {
+                                    // as for a one-vertex P' above
+                                    const int w = __ffs(q) - 1;
+                                    const uint32_t rw = __shfl_sync(FULL, row, w);
+                                    if ((qx & rw) == 0u) {
+                                        bool found = false;
+                                        for (int i0 = 0; i0 < clx && !found; i0 += 32) {
+                                            const int i = i0 + g.lane;
+                                            bool hit = false;
+                                            if (i < clx) {
+                                                const uint32_t xc = xcomp[xidx[i]];
+                                                hit = ((xc >> u) & 1u) != 0u && ((xc >> w) & 1u) != 0u;
+                                            }
+                                            found = __any_sync(FULL, hit);
+                                        }
+                                        if (!found || !C.pivot_ipx) t_nodes++;
+                                        if (!found) record(szc + 1, cS + mu + __shfl_sync(FULL, mj, w));
+                                    }
+                                } else {
+                                    // as for a two-vertex P' above
+                                    const int w1 = __ffs(q) - 1, w2 = 31 - __clz(q);
+                                    const uint32_t a1 = __shfl_sync(FULL, row, w1), a2 = __shfl_sync(FULL, row, w2);
+                                    const uint64_t m1 = __shfl_sync(FULL, mj, w1), m2 = __shfl_sync(FULL, mj, w2);
+                                    const bool e12 = ((a1 >> w2) & 1u) != 0u;
+                                    const bool s2p = (qx & a1 & a2) != 0u;
+                                    const uint32_t one = qx & (a1 ^ a2);
+                                    bool s2x = false, x1 = false, x2 = false;
+                                    unsigned firstx = 0u;
+                                    for (int i0 = 0; i0 < clx; i0 += 32) {
+                                        const int i = i0 + g.lane;
+                                        bool h1 = false, h2 = false;
+                                        unsigned k1 = 0u;
+                                        if (i < clx) {
+                                            const uint32_t e = xidx[i];
+                                            const uint32_t xc = xcomp[e];
+                                            if ((xc >> u) & 1u) {
+                                                h1 = ((xc >> w1) & 1u) != 0u;
+                                                h2 = ((xc >> w2) & 1u) != 0u;
+                                                if (C.pivot_ipx && h1 != h2)
+                                                    k1 = ((0x7fffffffu - xrank[e]) << 1) | (h1 ? 1u : 0u);
+                                            }
+                                        }
+                                        s2x |= __any_sync(FULL, h1 && h2) != 0;
+                                        x1 |= __any_sync(FULL, h1) != 0;
+                                        x2 |= __any_sync(FULL, h2) != 0;
+                                        if (C.pivot_ipx) firstx = max(firstx, __reduce_max_sync(FULL, k1));
+                                    }
+                                    const bool s2 = s2p || (C.pivot_ipx && s2x);
+                                    if (e12) {
+                                        if (!s2) {
+                                            t_nodes += 2;
+                                            if (!s2x) record(szc + 2, cS + mu + m1 + m2);
+                                        }
+                                    } else if (!s2) {
+                                        int touch = 0;
+                                        if (firstx) touch = (firstx & 1u) ? 1 : 2;
+                                        else if (one) touch = ((a1 >> (__ffs(one) - 1)) & 1u) ? 1 : 2;
+                                        if (touch) {
+                                            t_nodes++;
+                                            const uint32_t aj = touch == 1 ? a2 : a1;
+                                            const bool xj = touch == 1 ? x2 : x1;
+                                            if (!xj && (qx & aj) == 0u) record(szc + 1, cS + mu + (touch == 1 ? m2 : m1));
+                                        } else {
+                                            t_nodes += 2;
+                                            if (!x1) record(szc + 1, cS + mu + m1);
+                                            if (!x2) record(szc + 1, cS + mu + m2);
+                                        }
+                                    }
+                                }
+                                pc.stop(PH_LEAF);
+                                continue;
+                            }
+                            // descend
+                            if (g.lane == d) {
+                                sP = P;
+                                sX = X;
+                                sB = B;
+                                sL = clx;
+                                sS = cS;
+                            }
+                            if (clx > 0) clx = partition(clx, [&](uint32_t e) { return ((xcomp[e] >> u) & 1u) != 0u; });
+                            P = q;
+                            X = qx;
+                            cS += mu;
+                            d++;
+                            centr = true;
+                            t_nodes++;
+                            pc.stop(PH_PARTITION);
+                        }
+                        if (timed_out) break;
+                        continue;
+                    }
+                }
                 // ------------------------------ descend: push this level, partition X_X by v
                 {
                     uint32_t *lv = stk + (size_t)l * LS;
