@@ -474,16 +474,59 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 // ----------------------------------- induced subgraph (Sec. III-D)
                 for (int i = g.gl; i < n0 * WP; i += GT) Arow[i] = 0u;
                 g.sync();
-                for (int i = g.warp; i < n0; i += GW) {
-                    const int32_t u = p0[i];
-                    const int32_t *nr = G.out_col + G.out_ptr[u];
-                    const int len = G.out_ptr[u + 1] - G.out_ptr[u];
-                    for (int j = g.lane; j < len; j += 32) {
-                        int32_t w = nr[j];
-                        int k = find_in(p0, i + 1, n0, w);
-                        if (k < n0 && p0[k] == w) {
-                            atomicOr(&Arow[(size_t)i * WP + (k >> 5)], 1u << (k & 31));
-                            atomicOr(&Arow[(size_t)k * WP + (i >> 5)], 1u << (i & 31));
+                if (GW == 1 && n0 <= 32) {
+                    // Few rows whose out-lists are long (a small root's later
+                    // neighbours sit deeper in the order): test each pair i < k
+                    // by a binary search for P0[k] in the out-list of P0[i], all
+                    // pairs of the root spread over the lanes.
+                    int rb = 0, re = 0;
+                    if (g.lane < n0) {
+                        const int32_t u = p0[g.lane];
+                        rb = G.out_ptr[u];
+                        re = G.out_ptr[u + 1];
+                    }
+                    const int npairs = n0 * (n0 - 1) / 2;
+                    for (int q0 = 0; q0 < npairs; q0 += 32) {
+                        const int q = q0 + g.lane;
+                        // row i of pair q: the largest i with i (2 n0 - i - 1) / 2 <= q
+                        int i = 0;
+                        if (q < npairs) {
+                            int lo = 0, hi = n0 - 2;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (mid * (2 * n0 - mid - 1) / 2 <= q) lo = mid;
+                                else hi = mid - 1;
+                            }
+                            i = lo;
+                        }
+                        const int lo0 = __shfl_sync(0xffffffffu, rb, i), hi0 = __shfl_sync(0xffffffffu, re, i);
+                        if (q < npairs) {
+                            const int k = i + 1 + (q - i * (2 * n0 - i - 1) / 2);
+                            const int32_t w = p0[k];
+                            int lo = lo0, hi = hi0;
+                            while (lo < hi) {
+                                const int mid = (lo + hi) >> 1;
+                                if (G.out_col[mid] < w) lo = mid + 1;
+                                else hi = mid;
+                            }
+                            if (lo < hi0 && G.out_col[lo] == w) {
+                                atomicOr(&Arow[(size_t)i * WP + (k >> 5)], 1u << (k & 31));
+                                atomicOr(&Arow[(size_t)k * WP + (i >> 5)], 1u << (i & 31));
+                            }
+                        }
+                    }
+                } else {
+                    for (int i = g.warp; i < n0; i += GW) {
+                        const int32_t u = p0[i];
+                        const int32_t *nr = G.out_col + G.out_ptr[u];
+                        const int len = G.out_ptr[u + 1] - G.out_ptr[u];
+                        for (int j = g.lane; j < len; j += 32) {
+                            int32_t w = nr[j];
+                            int k = find_in(p0, i + 1, n0, w);
+                            if (k < n0 && p0[k] == w) {
+                                atomicOr(&Arow[(size_t)i * WP + (k >> 5)], 1u << (k & 31));
+                                atomicOr(&Arow[(size_t)k * WP + (i >> 5)], 1u << (i & 31));
+                            }
                         }
                     }
                 }
