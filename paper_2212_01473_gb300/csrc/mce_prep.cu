@@ -162,7 +162,7 @@ __device__ void block_bitonic(int *a, int len) {
 // return. Removal order and core numbers are the same either way.
 constexpr long long kSoloDegrees = 32768;
 // adjacency lists longer than this are removed by a whole block
-constexpr int kHeavyDeg = 256;
+constexpr int kHeavyDeg = 64;
 
 __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp, const int32_t *col,
                                                        int32_t *deg, int32_t *rank, int32_t *core,

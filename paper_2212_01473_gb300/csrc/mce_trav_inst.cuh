@@ -5,7 +5,12 @@
 namespace mce {
 
 __host__ __device__ constexpr int group_warps(int wp) { return wp <= 12 ? 1 : wp <= 20 ? 4 : 8; }
-__host__ __device__ constexpr bool a_in_global(int wp) { return wp >= 68; }
+// A rows in global memory (L1/L2) instead of shared memory: always when too
+// wide for shared memory, and for WP = 12, where one-warp groups on rows of up
+// to 340 x 12 words would fit only 11 per SM in shared memory while registers
+// allow 16. Compact subtrees, where most nodes are, do not read A; the extra
+// groups win (chunglu_1m widest class 69 -> 55 ms).
+__host__ __device__ constexpr bool a_in_global(int wp) { return wp == 12 || wp >= 68; }
 __host__ __device__ constexpr bool stack_in_smem(int wp) { return wp <= 4; }
 
 template <int WP>

@@ -271,7 +271,7 @@ template <int WP, int GW>
 __device__ __forceinline__ void grp_copy_rows(const Grp<GW> &g, const int32_t *rows, int nrows, const uint32_t *src,
                                               uint32_t *dst) {
     constexpr int GT = 32 * GW;
-    if (WP % 4 == 0) {
+    if constexpr (WP % 4 == 0) {
         constexpr int Q = WP / 4;
         const uint4 *s4 = reinterpret_cast<const uint4 *>(src);
         uint4 *d4 = reinterpret_cast<uint4 *>(dst);
