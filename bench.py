@@ -369,14 +369,18 @@ def run_ours(args):
     max_mhz = clk.get("sm_max_mhz") or 2070.0
     peak_gops = sm_count * POPC_PER_SM_CLK * max_mhz * 1e6 / 1e9
     roofline = {"bound": "alu", "achieved": None, "peak": peak_gops, "unit": "Gop/s", "frac": None,
-                "traffic": None, "kernel": "k_traverse<WP=%d,GW=%d> (pivot rule IP)" % (dom["wp"], dom["group_warps"]),
+                "traffic": None, "kernel": "k_traverse<WP=%d,GW=%d> (pivot rule IP; roots of width classes %d..%d words)" % (
+                    dom["wp"], dom["group_warps"], dom.get("wp_min") or dom["wp"], dom["wp"]),
                 "kernel_ms": avg_ms,
                 "peak_basis": "derived: %d SMs x %d POPC/clk x %.0f MHz (max SM clock)" % (
                     sm_count, POPC_PER_SM_CLK, max_mhz),
                 "work": "bitset word AND+POPC operations of the oracle-counted Bron-Kerbosch tree (pivot rule IP; "
                         "tests/golden/%s.json word_ops_by_W) for the roots of this launch" % args.workload}
     if golden and golden.get("count") == count and r_ip.tree_nodes == golden.get("tree_nodes"):
-        words = sum(v for w, v in golden["word_ops_by_W"].items() if wp_of_words(int(w)) == dom["wp"])
+        # the launch runs the roots of every width class from wp_min to wp
+        lo = dom.get("wp_min") or dom["wp"]
+        words = sum(v for w, v in golden["word_ops_by_W"].items()
+                    if int(w) > 0 and lo <= wp_of_words(int(w)) <= dom["wp"])
         achieved = words / (avg_ms / 1e3) / 1e9
         roofline["achieved"] = achieved
         roofline["frac"] = achieved / peak_gops

@@ -234,6 +234,9 @@ typedef struct {
      * (backtracks) */
     uint64_t phase_cycles[MCE_STATS_PHASES];
     uint64_t phase_counts[MCE_STATS_PHASES];
+    /* narrowest row width whose roots the launch ran: one launch takes the
+     * roots of every width class of at most 12 words, widest first */
+    int32_t class_wp_min[MCE_STATS_MAX_CLASSES];
 } mce_stats;
 
 int mce_get_stats(const mce_graph *g, mce_stats *out);

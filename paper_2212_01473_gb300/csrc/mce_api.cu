@@ -487,10 +487,12 @@ struct RunPlan {
     int32_t counts[kNumClasses + 1] = {};
     struct Cls {
         int c = 0, rows = 0, groups = 0;
+        int x_cap = 0, wp_min = 0;  // with merged classes: largest X0, narrowest row width
         ClassLaunch L{};
         ClassArgs a{};
     } cls[kNumClasses];
     int ncls = 0;
+    int merged_top = -1, merged_xcap = 0, merged_wp_min = 0;  // one-warp classes sharing one launch
     unsigned trivial_blocks = 0;
     std::vector<void *> tmp;
     std::vector<cudaEvent_t> ev;  // [0] start, [1] end, then one pair per launch
@@ -621,6 +623,36 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     }
     if (P->counts[kNumClasses] > 0)
         P->trivial_blocks = (unsigned)std::min<int64_t>(4096, ((int64_t)P->counts[kNumClasses] + 255) / 256);
+    // The one-warp classes (row width <= 12 words) share one launch of the
+    // widest of them, its roots first: the narrow classes' roots fill the
+    // groups that would otherwise idle at the end of each separate launch.
+    {
+        int top = -1, nmerge = 0;
+        int64_t total = 0;
+        for (int c = kNumClasses - 1; c >= 0; c--) {
+            if (P->counts[c] == 0 || class_wp(c) > 12) continue;
+            if (top < 0) top = c;
+            nmerge++;
+            total += P->counts[c];
+            P->merged_xcap = std::max(P->merged_xcap, (int)g->class_x[c]);
+            P->merged_wp_min = class_wp(c);
+        }
+        if (nmerge > 1) {
+            int32_t *lst = (int32_t *)dalloc(g, (size_t)total * 4);
+            P->tmp.push_back(lst);
+            if (!lst) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+            int64_t at = 0;
+            for (int c = top; c >= 0; c--) {
+                if (P->counts[c] == 0 || class_wp(c) > 12) continue;
+                CK(cudaMemcpyAsync(lst + at, P->lists[c], (size_t)P->counts[c] * 4, cudaMemcpyDeviceToDevice, g->stream));
+                at += P->counts[c];
+                if (c != top) P->counts[c] = 0;
+            }
+            P->lists[top] = lst;
+            P->counts[top] = (int32_t)total;
+            P->merged_top = top;
+        }
+    }
     // width classes, heaviest first: launch shapes, then one scratch for all
     for (int c = kNumClasses - 1; c >= 0; c--) {
         if (P->counts[c] == 0) continue;
@@ -628,10 +660,12 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         const Tuned *t = tune_override ? &tune_override[c] : (opts.tuned ? &g->tuned[c] : nullptr);
         k.c = c;
         k.rows = g->class_rows[c];
+        k.x_cap = c == P->merged_top ? P->merged_xcap : g->class_x[c];
+        k.wp_min = c == P->merged_top ? P->merged_wp_min : class_wp(c);
         const int blocks = (t && t->blocks > 0) ? t->blocks : opts.blocks;
         CK(plan_class_wp(class_wp(c), k.rows, g->sm_count, g->smem_optin, blocks, g->gid == nullptr, &k.L));
         k.groups = k.L.blocks * (k.L.warps_per_block / k.L.gw);
-        const size_t aw = arena_words(k.L.wp, k.rows, g->class_x[c], k.L.a_global, stack_in_smem(k.L.wp));
+        const size_t aw = arena_words(k.L.wp, k.rows, k.x_cap, k.L.a_global, stack_in_smem(k.L.wp));
         const size_t idle_words = ((size_t)k.groups + 31) / 32;
         const size_t flag_words = (size_t)k.groups * kMailFlagStride;
         const int mail_words = 4 + 3 * k.L.wp;
@@ -641,7 +675,7 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         a.roots = P->lists[c];
         a.n_roots = P->counts[c];
         a.rows_cap = k.rows;
-        a.x_cap = g->class_x[c];
+        a.x_cap = k.x_cap;
         // IPX: pivots may also come from X_X; AUTO follows the Sec. IV-D rule
         // (partial induced subgraphs when max degree / degeneracy > 200)
         a.pivot_ipx = opts.pivot == MCE_PIVOT_IPX ||
@@ -761,6 +795,7 @@ static int collect_run(mce_graph *g, RunPlan *P, mce_result *per_graph, uint64_t
             CK(cudaEventElapsedTime(&cms, P->ev[e], P->ev[e + 1]));
             e += 2;
             st.class_wp[k] = c.L.wp;
+            st.class_wp_min[k] = c.wp_min;
             st.class_roots[k] = P->counts[c.c];
             st.class_rows[k] = c.rows;
             st.class_blocks[k] = c.L.blocks;

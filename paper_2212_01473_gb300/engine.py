@@ -64,7 +64,7 @@ class mce_stats(ctypes.Structure):
                 ("class_groups", ctypes.c_int32 * 16), ("class_group_warps", ctypes.c_int32 * 16),
                 ("class_ms", ctypes.c_double * 16), ("kernel_launches", ctypes.c_uint64),
                 ("peel_rounds", ctypes.c_int64), ("phase_cycles", ctypes.c_uint64 * 8),
-                ("phase_counts", ctypes.c_uint64 * 8)]
+                ("phase_counts", ctypes.c_uint64 * 8), ("class_wp_min", ctypes.c_int32 * 16)]
 
 
 PHASES = ["setup", "pivot", "branch", "leaf", "partition", "donate", "idle", "backtrack"]
@@ -332,7 +332,7 @@ def mce_get_stats(h: Handle) -> dict:
     _check(library().mce_get_stats(h.ptr, ctypes.byref(st)))
     k = st.n_classes
     return {
-        "classes": [{"wp": st.class_wp[i], "roots": st.class_roots[i], "rows": st.class_rows[i],
+        "classes": [{"wp": st.class_wp[i], "wp_min": st.class_wp_min[i], "roots": st.class_roots[i], "rows": st.class_rows[i],
                      "blocks": st.class_blocks[i], "groups": st.class_groups[i],
                      "group_warps": st.class_group_warps[i], "ms": st.class_ms[i]} for i in range(k)],
         "kernel_launches": int(st.kernel_launches),
