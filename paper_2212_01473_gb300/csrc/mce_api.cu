@@ -668,7 +668,9 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         const size_t aw = arena_words(k.L.wp, k.rows, k.x_cap, k.L.a_global, stack_in_smem(k.L.wp));
         const size_t idle_words = ((size_t)k.groups + 31) / 32;
         const size_t flag_words = (size_t)k.groups * kMailFlagStride;
-        const int mail_words = 4 + 3 * k.L.wp;
+        // a wide subtree: root, level, rows, kind, R', P', X_P'; a compact one
+        // (one-warp classes): root, level, rows, kind, 32 rows, 32 indices, P, X_P, hash sum
+        const int mail_words = std::max(4 + 3 * k.L.wp, 72);
         const size_t words = aw * k.groups + CTL_NCTL + idle_words + flag_words + (size_t)k.groups * mail_words + 64;
         need_words = std::max(need_words, words);
         ClassArgs &a = k.a;

@@ -451,11 +451,15 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             pc.start();
             pc.count(PH_SETUP, 1);
 
-            // layout of a donated subtree's mail: [0] root, [1] level,
+            // layout of a donated subtree's mail: [0] root, [1] level (|R| - 1),
             // [2] number of X_X rows the donor wrote into this group's arena,
-            // [4..4+WP) R' (path below the root), then P', then X_P'
+            // [3] kind. Kind 0 (wide): [4..4+WP) R' (path below the root), then
+            // P', then X_P'. Kind 1 (compact, one-warp groups): [4..36) the rows
+            // over the index space, [36..68) its local indices, [68] P, [69] X_P,
+            // [70..72) the hash sum of R; its X_X rows are in the arena's xcomp.
             const uint32_t *mb = C.mail + (size_t)gg * C.mail_words;
             const int l0 = have_mail ? (int)mb[1] : 0;
+            const bool cmail = GW == 1 && have_mail && mb[3] != 0u;
             for (int i = g.gl; i < n0; i += GT) p0[i] = prow[i];
             int nx = 0;
             if (have_mail) {
@@ -463,7 +467,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 // and the surviving X_X rows into the arena's X rows: nothing to
                 // rebuild. Every row the subtree reads (candidates, branches) is
                 // one of those; the other rows are never read.
-                if (!AG) {
+                if (!AG && !cmail) {
                     const uint32_t want = g.gl < WP ? (mb[4 + WP + g.gl] | mb[4 + 2 * WP + g.gl]) : 0u;
                     const int nrows = grp_bits_to_list<WP, GW>(g, red, want, cand);
                     grp_copy_rows<WP, GW>(g, cand, nrows, ar.A, Arow);
@@ -598,7 +602,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     const int lo = g.gl * 32;
                     if (lo < n0) p = (n0 - lo >= 32) ? 0xffffffffu : ((1u << (n0 - lo)) - 1u);
                 }
-            } else {
+            } else if (!cmail) {
                 // P', X_P' and the path R' below the root come from the mail; the
                 // X_X rows in the arena are exactly the donor's survivors
                 const uint32_t *mR = mb + 4, *mP = mb + 4 + WP, *mX = mb + 4 + 2 * WP;
@@ -628,6 +632,116 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             int l = l0;
             bool enter = true;
             bool timed_out = false;
+            auto record = [&](int sz, uint64_t sum) {
+                if (g.gl == 0) {
+                    t_cnt++;
+                    t_hash += mix64(sum + (uint64_t)sz * kPhi);
+                    if (block_hist) atomicAdd(&hist[sz], 1ull);
+                    else hist[sz] += 1ull;
+                    acc_maxsz = max(acc_maxsz, sz);
+                }
+            };
+            // move the X_X rows e of xidx[0, n_in) with holds(e) to the front; returns their number
+            auto partition = [&](int n_in, auto holds) -> int {
+                int out = 0, nout = 0;
+                for (int it = 0; it < n_in; it += GT) {
+                    const int idx = it + g.gl;
+                    const bool valid = idx < n_in;
+                    const uint32_t e = valid ? xidx[idx] : 0u;
+                    const bool surv = valid && holds(e);
+                    int ts, tn;
+                    const int ps = grp_prefix(g, red, surv, &ts);
+                    const int pn = grp_prefix(g, red, valid && !surv, &tn);
+                    if (surv) xidx[out + ps] = e;
+                    else if (valid) xscr[nout + pn] = e;
+                    out += ts;
+                    nout += tn;
+                }
+                if (nout > 0) {
+                    g.sync();
+                    for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
+                }
+                g.sync();
+                return out;
+            };
+            // claim an idle group for a donation (-1: none): the lanes read 32 words
+            // of the idle bitmap at a time, and the first lane holding a set bit
+            // tries to take one with atomicAnd (another donor may win the race)
+            auto claim_idle = [&]() -> int {
+                if (g.warp == 0) {
+                    int claimed = -1;
+                    const bool any_idle =
+                        __shfl_sync(0xffffffffu, g.lane == 0 ? ld_relaxed(&C.ctl[CTL_IDLE]) > 0 : false, 0);
+                    if (any_idle) {
+                        const int nwords = (ngroups + 31) >> 5;
+                        for (int q0 = 0; q0 < nwords && claimed < 0; q0 += 32) {
+                            const int qd = q0 + g.lane;
+                            const int wi = (gg / 32 + 1 + qd) % nwords;
+                            const unsigned bits = qd < nwords ? *((volatile unsigned *)&C.idle_bits[wi]) : 0u;
+                            unsigned nz = __ballot_sync(0xffffffffu, bits != 0u);
+                            while (nz && claimed < 0) {
+                                const int src = __ffs(nz) - 1;
+                                nz &= nz - 1;
+                                int got = -1;
+                                if (g.lane == src) {
+                                    unsigned left = bits;
+                                    while (left) {
+                                        const int bb = __ffs(left) - 1;
+                                        const unsigned old = atomicAnd(&C.idle_bits[wi], ~(1u << bb));
+                                        if (old & (1u << bb)) {
+                                            got = wi * 32 + bb;
+                                            break;
+                                        }
+                                        left = old & ~(1u << bb) & ~((2u << bb) - 1u);
+                                    }
+                                }
+                                claimed = __shfl_sync(0xffffffffu, got, src);
+                            }
+                        }
+                        if (claimed >= 0 && g.lane == 0) {
+                            atomicSub(&C.ctl[CTL_IDLE], 1);
+                            atomicAdd(&C.ctl[CTL_ACTIVE], 1);
+                        }
+                    }
+                    if (g.lane == 0) misc[4] = claimed;
+                }
+                g.sync();
+                const int recv = misc[4];
+                g.sync();
+                return recv;
+            };
+
+            // Compact mode (one-warp groups). A node with |P| + |X_P| <= 32 and
+            // its whole subtree run on one-word sets over the index space
+            // L = P u X_P of that node, in ascending local index so ties still go
+            // to the smaller rank. Lane i holds L[i]'s adjacency row over L (kRow),
+            // its local index (kL) and clique-hash id (kmj), and the saved state
+            // of compact depth i (ks*); X_X rows are re-encoded over L once
+            // (xcomp). Entered from a wide descent, at a root with |P0| <= 32, or
+            // from a donated compact subtree; when the subtree is done the wide
+            // loop backtracks as from any child.
+            bool kstart = GW == 1 && !have_mail && n0 <= 32;  // the root itself
+            bool kmode = false, kcentr = false, kpend = false;
+            // In compact mode the node's P, X_P, branch set, X_X end and hash sum
+            // reuse the wide registers: the wide node is on the stack meanwhile.
+            uint32_t &kP = p, &kX = xp, &kB = b;
+            int &kclx = lpx;
+            uint64_t &kS = S;
+            uint32_t kRow = 0u;
+            int kL = 0, kd = 0, kbase = 0;
+            if (cmail) {
+                kRow = mb[4 + g.lane];
+                kL = (int)mb[36 + g.lane];
+                kP = mb[68];
+                kX = mb[69];
+                kS = (uint64_t)mb[70] | ((uint64_t)mb[71] << 32);
+                kbase = l0 + 1;
+                kd = 0;
+                kcentr = true;
+                kmode = true;
+                t_nodes++;  // the donated node
+                enter = false;
+            }
             while (true) {
                 if ((++iters & 1023u) == 0) {
                     // group-uniform decision (every thread must leave together)
@@ -635,6 +749,307 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         timed_out = true;
                         break;
                     }
+                }
+                if (GW == 1 && kstart) {
+                    // enter compact mode at the current node (P = p, X_P = xp, X_X =
+                    // xidx[0, lpx), hash sum S, level l)
+                    constexpr unsigned FULL = 0xffffffffu;
+                    kstart = false;
+                    t_nodes++;  // the node itself
+                    const int c = grp_bits_to_list<WP, GW>(g, red, own ? (p | xp) : 0u, cand);
+                    if (own) curP[g.gl] = p;
+                    __syncwarp();
+                    const bool inl = g.lane < c;
+                    kL = inl ? cand[g.lane] : 0;
+                    const bool inP = inl && ((curP[kL >> 5] >> (kL & 31)) & 1u) != 0u;
+                    kP = __ballot_sync(FULL, inP);
+                    kX = __ballot_sync(FULL, inl && !inP);
+                    // At a root L is P0 itself (local indices 0 .. c-1): rows and
+                    // X_X rows are their first words. Elsewhere each lane gathers
+                    // the bits of L from its row (lane i: A row of L[i]; lane k:
+                    // X_X row k).
+                    const bool ident = l == 0;
+                    const uint32_t cmask = c == 32 ? FULL : (1u << c) - 1u;
+                    kRow = 0u;
+                    if (ident) {
+                        if (inl) kRow = Arow[(size_t)kL * WP] & cmask;
+                    } else {
+                        const uint32_t *ar_ = Arow + (size_t)kL * WP;
+#pragma unroll 4
+                        for (int j = 0; j < c; j++) {
+                            const int lj = __shfl_sync(FULL, kL, j);
+                            kRow |= ((ar_[lj >> 5] >> (lj & 31)) & 1u) << j;
+                        }
+                        if (!inl) kRow = 0u;
+                    }
+                    for (int i0 = 0; i0 < lpx; i0 += 32) {
+                        const int i = i0 + g.lane;
+                        const uint32_t e = i < lpx ? xidx[i] : 0u;
+                        const uint32_t *xr = xrows + (size_t)e * WP;
+                        uint32_t w = 0u;
+                        if (ident) {
+                            w = xr[0] & cmask;
+                        } else {
+#pragma unroll 4
+                            for (int j = 0; j < c; j++) {
+                                const int lj = __shfl_sync(FULL, kL, j);
+                                w |= ((xr[lj >> 5] >> (lj & 31)) & 1u) << j;
+                            }
+                        }
+                        if (i < lpx) xcomp[e] = w;
+                    }
+                    __syncwarp();
+                    kbase = l + 1;
+                    kd = 0;
+                    kcentr = true;
+                    kpend = npend > 0;
+                    kmode = true;
+                    enter = false;
+                    pc.stop(PH_SETUP);
+                }
+                if (GW == 1 && kmode) {
+                    constexpr unsigned FULL = 0xffffffffu;
+                    const bool ipx = C.pivot_ipx != 0;
+                    // lane i: clique-hash id of L[i] (lanes past |L| hold a harmless
+                    // copy of P0[0]'s), and the saved state of compact depth i
+                    const uint64_t kmj = G.mixid[p0[kL]];
+                    uint32_t ksP = 0u, ksX = 0u, ksB = 0u, ksL = 0u;
+                    uint64_t ksS = 0ull;
+                    for (;;) {
+                        if ((++iters & 1023u) == 0 && __any_sync(FULL, g.lane == 0 && globaltimer_ns() > deadline)) {
+                            timed_out = true;
+                            break;
+                        }
+                        if (kcentr) {
+                            kcentr = false;
+                            // pivot over P u X_P: lane u scores |P n N(u)|, ties to the
+                            // smaller index; IPX also scores the X_X rows, which win ties
+                            const bool isc = (((kP | kX) >> g.lane) & 1u) != 0u;
+                            const unsigned key =
+                                isc ? (((unsigned)__popc(kRow & kP) + 1u) << 8) | (unsigned)(31 - g.lane) : 0u;
+                            const unsigned best = __reduce_max_sync(FULL, key);
+                            const int bsc = (int)(best >> 8) - 1;
+                            uint32_t prow = __shfl_sync(FULL, kRow, 31 - (int)(best & 255u));
+                            if (ipx && kclx > 0) {
+                                unsigned long long bx = 0ull;
+                                for (int i0 = 0; i0 < kclx; i0 += 32) {
+                                    const int i = i0 + g.lane;
+                                    unsigned long long k2 = 0ull;
+                                    if (i < kclx) {
+                                        const uint32_t e = xidx[i];
+                                        k2 = ((unsigned long long)(__popc(xcomp[e] & kP) + 1) << 32) |
+                                             (unsigned long long)(0xffffffffu - xrank[e]);
+                                    }
+                                    for (int o = 16; o; o >>= 1) {
+                                        const unsigned long long y = __shfl_xor_sync(FULL, k2, o);
+                                        k2 = y > k2 ? y : k2;
+                                    }
+                                    bx = k2 > bx ? k2 : bx;
+                                }
+                                if ((int)(bx >> 32) - 1 >= bsc) {
+                                    const uint32_t want = 0xffffffffu - (uint32_t)(bx & 0xffffffffull);
+                                    for (int i0 = 0; i0 < kclx; i0 += 32) {
+                                        const int i = i0 + g.lane;
+                                        uint32_t e = 0u;
+                                        bool hit = false;
+                                        if (i < kclx) {
+                                            e = xidx[i];
+                                            hit = xrank[e] == want;
+                                        }
+                                        const unsigned hm = __ballot_sync(FULL, hit);
+                                        if (hm) {
+                                            prow = xcomp[__shfl_sync(FULL, e, __ffs(hm) - 1)];
+                                            break;
+                                        }
+                                    }
+                                }
+                            }
+                            kB = kP & ~prow;
+                            pc.stop(PH_PIVOT);
+                            pc.count(PH_PIVOT, (unsigned long long)__popc(kP | kX));
+                        }
+                        if (kB == 0u) {
+                            if (kd == 0) break;  // the compact subtree is done
+                            kd--;
+                            kP = __shfl_sync(FULL, ksP, kd);
+                            kX = __shfl_sync(FULL, ksX, kd);
+                            kB = __shfl_sync(FULL, ksB, kd);
+                            kclx = (int)__shfl_sync(FULL, ksL, kd);
+                            kS = __shfl_sync(FULL, ksS, kd);
+                            pc.stop(PH_POP);
+                            pc.count(PH_POP, 1);
+                            continue;
+                        }
+                        const int u = __ffs(kB) - 1;
+                        const uint32_t ubit = 1u << u;
+                        const uint32_t ru = __shfl_sync(FULL, kRow, u);
+                        const uint32_t q = kP & ru, qx = kX & ru;  // the child's P and X_P
+                        kB &= ~ubit;
+                        kP &= ~ubit;
+                        kX |= ubit;
+                        const int qn = __popc(q);
+                        const uint64_t mu = __shfl_sync(FULL, kmj, u);
+                        const int szc = kbase + kd + 1;  // |R u {u}|
+                        pc.stop(PH_BRANCH);
+                        if (qn <= 2) {
+                            t_nodes++;
+                            // the child's X_X rows are this node's rows holding u
+                            auto xx_any = [&](auto f) -> bool {
+                                bool found = false;
+                                for (int i0 = 0; i0 < kclx && !found; i0 += 32) {
+                                    const int i = i0 + g.lane;
+                                    found = __any_sync(FULL, i < kclx && f(xcomp[xidx[i]])) != 0;
+                                }
+                                return found;
+                            };
+                            if (qn == 0) {
+                                if (qx == 0u && !xx_any([&](uint32_t xc) { return ((xc >> u) & 1u) != 0u; }))
+                                    record(szc, kS + mu);
+                            } else if (qn == 1) {
+                                // as for a one-vertex P' in the wide walk
+                                const int w = __ffs(q) - 1;
+                                const uint32_t rw = __shfl_sync(FULL, kRow, w);
+                                if ((qx & rw) == 0u) {
+                                    const uint32_t both = ubit | (1u << w);
+                                    const bool found = xx_any([&](uint32_t xc) { return (xc & both) == both; });
+                                    if (!found || !ipx) t_nodes++;
+                                    if (!found) record(szc + 1, kS + mu + __shfl_sync(FULL, kmj, w));
+                                }
+                            } else {
+                                // as for a two-vertex P' in the wide walk
+                                const int w1 = __ffs(q) - 1, w2 = 31 - __clz(q);
+                                const uint32_t a1 = __shfl_sync(FULL, kRow, w1), a2 = __shfl_sync(FULL, kRow, w2);
+                                const uint64_t m1 = __shfl_sync(FULL, kmj, w1), m2 = __shfl_sync(FULL, kmj, w2);
+                                const bool e12 = ((a1 >> w2) & 1u) != 0u;
+                                const bool s2p = (qx & a1 & a2) != 0u;
+                                const uint32_t one = qx & (a1 ^ a2);
+                                bool s2x = false, x1 = false, x2 = false;
+                                unsigned firstx = 0u;
+                                for (int i0 = 0; i0 < kclx; i0 += 32) {
+                                    const int i = i0 + g.lane;
+                                    bool h1 = false, h2 = false;
+                                    unsigned k1 = 0u;
+                                    if (i < kclx) {
+                                        const uint32_t e = xidx[i];
+                                        const uint32_t xc = xcomp[e];
+                                        if ((xc >> u) & 1u) {
+                                            h1 = ((xc >> w1) & 1u) != 0u;
+                                            h2 = ((xc >> w2) & 1u) != 0u;
+                                            if (ipx && h1 != h2) k1 = ((0x7fffffffu - xrank[e]) << 1) | (h1 ? 1u : 0u);
+                                        }
+                                    }
+                                    s2x |= __any_sync(FULL, h1 && h2) != 0;
+                                    x1 |= __any_sync(FULL, h1) != 0;
+                                    x2 |= __any_sync(FULL, h2) != 0;
+                                    if (ipx) firstx = max(firstx, __reduce_max_sync(FULL, k1));
+                                }
+                                const bool s2 = s2p || (ipx && s2x);
+                                if (e12) {
+                                    if (!s2) {
+                                        t_nodes += 2;
+                                        if (!s2x) record(szc + 2, kS + mu + m1 + m2);
+                                    }
+                                } else if (!s2) {
+                                    int touch = 0;
+                                    if (firstx) touch = (firstx & 1u) ? 1 : 2;
+                                    else if (one) touch = ((a1 >> (__ffs(one) - 1)) & 1u) ? 1 : 2;
+                                    if (touch) {
+                                        t_nodes++;
+                                        const uint32_t aj = touch == 1 ? a2 : a1;
+                                        const bool xj = touch == 1 ? x2 : x1;
+                                        if (!xj && (qx & aj) == 0u) record(szc + 1, kS + mu + (touch == 1 ? m2 : m1));
+                                    } else {
+                                        t_nodes += 2;
+                                        if (!x1) record(szc + 1, kS + mu + m1);
+                                        if (!x2) record(szc + 1, kS + mu + m2);
+                                    }
+                                }
+                            }
+                            pc.stop(PH_LEAF);
+                            continue;
+                        }
+                        // donation of the child as a compact subtree (Sec. III-C): the
+                        // receiver gets the rows over L, the child's sets and its X_X rows
+                        if (C.worker_list && qn >= C.donate_min_p) {
+                            const bool above = kpend || __ballot_sync(FULL, g.lane < kd && ksB != 0u) != 0u;
+                            const bool may = C.donate_policy == MCE_DONATE_ANY ||
+                                             (C.donate_policy == MCE_DONATE_EITHER ? (kB != 0u || above)
+                                                                                   : (kB != 0u && above));
+                            if (may) {
+                                const int recv = claim_idle();
+                                if (recv >= 0) {
+                                    const ArenaPtrs ra = arena_at(C.arena + (size_t)recv * C.arena_words_per_group, WP,
+                                                                  rows_cap, C.x_cap, stack_smem != 0);
+                                    int out = 0;
+                                    for (int i0 = 0; i0 < kclx; i0 += 32) {
+                                        const int i = i0 + g.lane;
+                                        const uint32_t e = i < kclx ? xidx[i] : 0u;
+                                        const uint32_t xc = i < kclx ? xcomp[e] : 0u;
+                                        const bool surv = i < kclx && ((xc >> u) & 1u) != 0u;
+                                        const unsigned bm = __ballot_sync(FULL, surv);
+                                        if (surv) {
+                                            const int k = out + __popc(bm & ((1u << g.lane) - 1u));
+                                            ra.xcomp[k] = xc;
+                                            ra.xrank[k] = xrank[e];
+                                            ra.xidx[k] = (uint32_t)k;
+                                        }
+                                        out += __popc(bm);
+                                    }
+                                    uint32_t *m = C.mail + (size_t)recv * C.mail_words;
+                                    m[4 + g.lane] = kRow;
+                                    m[36 + g.lane] = (uint32_t)kL;
+                                    if (g.lane == 0) {
+                                        const uint64_t s2 = kS + mu;
+                                        m[0] = (uint32_t)r;
+                                        m[1] = (uint32_t)(szc - 1);
+                                        m[2] = (uint32_t)out;
+                                        m[3] = 1u;
+                                        m[68] = q;
+                                        m[69] = qx;
+                                        m[70] = (uint32_t)s2;
+                                        m[71] = (uint32_t)(s2 >> 32);
+                                    }
+                                    __threadfence();
+                                    __syncwarp();
+                                    if (g.lane == 0) {
+                                        st_release(&C.mail_flag[(size_t)recv * kMailFlagStride], 1);
+                                        acc_don++;
+                                    }
+                                    __syncwarp();
+                                    pc.stop(PH_DONATE);
+                                    pc.count(PH_DONATE, 1);
+                                    continue;
+                                }
+                            }
+                            pc.stop(PH_DONATE);
+                        }
+                        // descend
+                        if (g.lane == kd) {
+                            ksP = kP;
+                            ksX = kX;
+                            ksB = kB;
+                            ksL = (uint32_t)kclx;
+                            ksS = kS;
+                        }
+                        if (kclx > 0) kclx = partition(kclx, [&](uint32_t e) { return ((xcomp[e] >> u) & 1u) != 0u; });
+                        kP = q;
+                        kX = qx;
+                        kS += mu;
+                        kd++;
+                        kcentr = true;
+                        t_nodes++;
+                        pc.stop(PH_PARTITION);
+                        continue;
+                    }
+                    // the compact subtree is done; the wide loop backtracks (the
+                    // branch set is empty, and words no thread owns are 0)
+                    kmode = false;
+                    if (timed_out) break;
+                    if (!own) {
+                        p = 0u;
+                        xp = 0u;
+                    }
+                    continue;
                 }
                 if (enter) {
                     t_nodes++;
@@ -956,49 +1371,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                         (C.donate_policy == MCE_DONATE_EITHER ? (others_here || npend >= 1)
                                                                               : (others_here && npend >= 1));
                 if (C.worker_list && pcnt >= C.donate_min_p && may_donate) {
-                    if (g.warp == 0) {
-                        // claim an idle group: the lanes read 32 words of the idle
-                        // bitmap at a time, and the first lane holding a set bit tries
-                        // to take one with atomicAnd (another donor may win the race)
-                        int claimed = -1;
-                        const bool any_idle = __shfl_sync(0xffffffffu,
-                                                          g.lane == 0 ? ld_relaxed(&C.ctl[CTL_IDLE]) > 0 : false, 0);
-                        if (any_idle) {
-                            const int nwords = (ngroups + 31) >> 5;
-                            for (int q0 = 0; q0 < nwords && claimed < 0; q0 += 32) {
-                                const int qd = q0 + g.lane;
-                                const int wi = (gg / 32 + 1 + qd) % nwords;
-                                const unsigned bits = qd < nwords ? *((volatile unsigned *)&C.idle_bits[wi]) : 0u;
-                                unsigned nz = __ballot_sync(0xffffffffu, bits != 0u);
-                                while (nz && claimed < 0) {
-                                    const int src = __ffs(nz) - 1;
-                                    nz &= nz - 1;
-                                    int got = -1;
-                                    if (g.lane == src) {
-                                        unsigned left = bits;
-                                        while (left) {
-                                            const int bb = __ffs(left) - 1;
-                                            const unsigned old = atomicAnd(&C.idle_bits[wi], ~(1u << bb));
-                                            if (old & (1u << bb)) {
-                                                got = wi * 32 + bb;
-                                                break;
-                                            }
-                                            left = old & ~(1u << bb) & ~((2u << bb) - 1u);
-                                        }
-                                    }
-                                    claimed = __shfl_sync(0xffffffffu, got, src);
-                                }
-                            }
-                            if (claimed >= 0 && g.lane == 0) {
-                                atomicSub(&C.ctl[CTL_IDLE], 1);
-                                atomicAdd(&C.ctl[CTL_ACTIVE], 1);
-                            }
-                        }
-                        if (g.lane == 0) misc[4] = claimed;
-                    }
-                    g.sync();
-                    const int recv = misc[4];
-                    g.sync();
+                    const int recv = claim_idle();
                     if (recv >= 0) {
                         // X_X of the child = rows of this level's prefix with bit v
                         int out = 0;
@@ -1047,6 +1420,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             m[0] = (uint32_t)r;
                             m[1] = (uint32_t)(l + 1);
                             m[2] = (uint32_t)out;
+                            m[3] = 0u;
                         }
                         __threadfence();
                         g.sync();
@@ -1061,267 +1435,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     }
                     pc.stop(PH_DONATE);
                 }
-                // ------------------------------ compact subtree
-                // When |P'| + |X_P'| <= 32 the child's whole subtree runs on one-word
-                // sets over the index space L = P' u X_P' (ascending local index, so
-                // ties still go to the smaller rank). Lane i holds the row of L[i]
-                // over L and the ancestors' (P, X_P, branches, X_X end, hash sum) at
-                // depth i; X_X' rows are re-encoded over L once. Node for node this
-                // is the same walk as below, without donations.
-                if (GW == 1 && WP > 1 && pcnt <= 32) {
-                    const int nxc = grp_sum(g, red, __popc(cx));
-                    if (pcnt + nxc <= 32) {
-                        constexpr unsigned FULL = 0xffffffffu;
-                        t_nodes++;  // the child R u {v}
-                        // X_X' = rows of this prefix holding v, moved to the front
-                        auto partition = [&](int n_in, auto holds) -> int {
-                            int out = 0, nout = 0;
-                            for (int it = 0; it < n_in; it += GT) {
-                                const int idx = it + g.gl;
-                                const bool valid = idx < n_in;
-                                const uint32_t e = valid ? xidx[idx] : 0u;
-                                const bool surv = valid && holds(e);
-                                int ts, tn;
-                                const int ps = grp_prefix(g, red, surv, &ts);
-                                const int pn = grp_prefix(g, red, valid && !surv, &tn);
-                                if (surv) xidx[out + ps] = e;
-                                else if (valid) xscr[nout + pn] = e;
-                                out += ts;
-                                nout += tn;
-                            }
-                            if (nout > 0) {
-                                g.sync();
-                                for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
-                            }
-                            g.sync();
-                            return out;
-                        };
-                        int clx = 0;
-                        if (lpx > 0) clx = partition(lpx, [&](uint32_t e) { return (xrows[(size_t)e * WP + vw] & vb) != 0u; });
-                        const int c = grp_bits_to_list<WP, GW>(g, red, own ? (cp | cx) : 0u, cand);
-                        if (own) curP[g.gl] = cp;
-                        __syncwarp();
-                        const bool inl = g.lane < c;
-                        const int Lj = inl ? cand[g.lane] : 0;
-                        const bool inP = inl && ((curP[Lj >> 5] >> (Lj & 31)) & 1u) != 0u;
-                        uint32_t P = __ballot_sync(FULL, inP);
-                        uint32_t X = __ballot_sync(FULL, inl && !inP);
-                        uint32_t row = 0u;
-                        {
-                            const uint32_t *ar_ = Arow + (size_t)Lj * WP;
-#pragma unroll 4
-                            for (int j = 0; j < c; j++) {
-                                const int lj = __shfl_sync(FULL, Lj, j);
-                                row |= ((ar_[lj >> 5] >> (lj & 31)) & 1u) << j;
-                            }
-                            if (!inl) row = 0u;
-                        }
-                        const uint64_t mj = inl ? G.mixid[p0[Lj]] : 0ull;
-                        for (int i = 0; i < clx; i++) {
-                            const uint32_t e = xidx[i];
-                            const bool bit = inl && ((xrows[(size_t)e * WP + (Lj >> 5)] >> (Lj & 31)) & 1u) != 0u;
-                            const uint32_t w = __ballot_sync(FULL, bit);
-                            if (g.lane == 0) xcomp[e] = w;
-                        }
-                        __syncwarp();
-                        auto record = [&](int sz, uint64_t sum) {
-                            if (g.gl == 0) {
-                                t_cnt++;
-                                t_hash += mix64(sum + (uint64_t)sz * kPhi);
-                                if (block_hist) atomicAdd(&hist[sz], 1ull);
-                                else hist[sz] += 1ull;
-                                acc_maxsz = max(acc_maxsz, sz);
-                            }
-                        };
-                        pc.stop(PH_SETUP);
-                        uint32_t sP = 0u, sX = 0u, sB = 0u, B = 0u;
-                        int sL = 0, d = 0;
-                        uint64_t sS = 0ull, cS = S + G.mixid[p0[v]];
-                        const int base = l + 2;  // |R| at compact depth 0
-                        bool centr = true;
-                        for (;;) {
-                            if ((++iters & 1023u) == 0) {
-                                if (__any_sync(FULL, g.lane == 0 && globaltimer_ns() > deadline)) {
-                                    timed_out = true;
-                                    break;
-                                }
-                            }
-                            if (centr) {
-                                centr = false;
-                                // pivot over P u X_P: lane u scores |P n N(u)|, ties to the
-                                // smaller index; IPX also scores the X_X' rows, which win ties
-                                const bool isc = (((P | X) >> g.lane) & 1u) != 0u;
-                                const unsigned key =
-                                    isc ? (((unsigned)__popc(row & P) + 1u) << 8) | (unsigned)(31 - g.lane) : 0u;
-                                const unsigned best = __reduce_max_sync(FULL, key);
-                                const int bsc = (int)(best >> 8) - 1;
-                                uint32_t prow = __shfl_sync(FULL, row, 31 - (int)(best & 255u));
-                                if (C.pivot_ipx && clx > 0) {
-                                    unsigned long long bx = 0ull;
-                                    for (int i0 = 0; i0 < clx; i0 += 32) {
-                                        const int i = i0 + g.lane;
-                                        unsigned long long k2 = 0ull;
-                                        if (i < clx) {
-                                            const uint32_t e = xidx[i];
-                                            k2 = ((unsigned long long)(__popc(xcomp[e] & P) + 1) << 32) |
-                                                 (unsigned long long)(0xffffffffu - xrank[e]);
-                                        }
-                                        for (int o = 16; o; o >>= 1) {
-                                            const unsigned long long y = __shfl_xor_sync(FULL, k2, o);
-                                            k2 = y > k2 ? y : k2;
-                                        }
-                                        bx = k2 > bx ? k2 : bx;
-                                    }
-                                    if ((int)(bx >> 32) - 1 >= bsc) {
-                                        const uint32_t want = 0xffffffffu - (uint32_t)(bx & 0xffffffffull);
-                                        for (int i0 = 0; i0 < clx; i0 += 32) {
-                                            const int i = i0 + g.lane;
-                                            uint32_t e = 0u;
-                                            bool hit = false;
-                                            if (i < clx) {
-                                                e = xidx[i];
-                                                hit = xrank[e] == want;
-                                            }
-                                            const unsigned hm = __ballot_sync(FULL, hit);
-                                            if (hm) {
-                                                prow = xcomp[__shfl_sync(FULL, e, __ffs(hm) - 1)];
-                                                break;
-                                            }
-                                        }
-                                    }
-                                }
-                                B = P & ~prow;
-                                pc.stop(PH_PIVOT);
-                                pc.count(PH_PIVOT, (unsigned long long)__popc(P | X));
-                            }
-                            if (B == 0u) {
-                                if (d == 0) break;
-                                d--;
-                                P = __shfl_sync(FULL, sP, d);
-                                X = __shfl_sync(FULL, sX, d);
-                                B = __shfl_sync(FULL, sB, d);
-                                clx = __shfl_sync(FULL, sL, d);
-                                cS = __shfl_sync(FULL, sS, d);
-                                pc.stop(PH_POP);
-                                pc.count(PH_POP, 1);
-                                continue;
-                            }
-                            const int u = __ffs(B) - 1;
-                            const uint32_t ubit = 1u << u;
-                            const uint32_t ru = __shfl_sync(FULL, row, u);
-                            const uint32_t q = P & ru, qx = X & ru;  // the child's P and X_P
-                            B &= ~ubit;
-                            P &= ~ubit;
-                            X |= ubit;
-                            const int qn = __popc(q);
-                            const uint64_t mu = __shfl_sync(FULL, mj, u);
-                            const int szc = base + d + 1;  // |R u {u}|
-                            pc.stop(PH_BRANCH);
-                            if (qn <= 2) {
-                                t_nodes++;
-                                // the child's X_X rows are those of [0, clx) holding u
-                                if (qn == 0) {
-                                    if (qx == 0u) {
-                                        bool found = false;
-                                        for (int i0 = 0; i0 < clx && !found; i0 += 32) {
-                                            const int i = i0 + g.lane;
-                                            found = __any_sync(FULL, i < clx && ((xcomp[xidx[i]] >> u) & 1u) != 0u);
-                                        }
-                                        if (!found) record(szc, cS + mu);
-                                    }
-                                } else if (qn == 1) {
-                                    // as for a one-vertex P' above
-                                    const int w = __ffs(q) - 1;
-                                    const uint32_t rw = __shfl_sync(FULL, row, w);
-                                    if ((qx & rw) == 0u) {
-                                        bool found = false;
-                                        for (int i0 = 0; i0 < clx && !found; i0 += 32) {
-                                            const int i = i0 + g.lane;
-                                            bool hit = false;
-                                            if (i < clx) {
-                                                const uint32_t xc = xcomp[xidx[i]];
-                                                hit = ((xc >> u) & 1u) != 0u && ((xc >> w) & 1u) != 0u;
-                                            }
-                                            found = __any_sync(FULL, hit);
-                                        }
-                                        if (!found || !C.pivot_ipx) t_nodes++;
-                                        if (!found) record(szc + 1, cS + mu + __shfl_sync(FULL, mj, w));
-                                    }
-                                } else {
-                                    // as for a two-vertex P' above
-                                    const int w1 = __ffs(q) - 1, w2 = 31 - __clz(q);
-                                    const uint32_t a1 = __shfl_sync(FULL, row, w1), a2 = __shfl_sync(FULL, row, w2);
-                                    const uint64_t m1 = __shfl_sync(FULL, mj, w1), m2 = __shfl_sync(FULL, mj, w2);
-                                    const bool e12 = ((a1 >> w2) & 1u) != 0u;
-                                    const bool s2p = (qx & a1 & a2) != 0u;
-                                    const uint32_t one = qx & (a1 ^ a2);
-                                    bool s2x = false, x1 = false, x2 = false;
-                                    unsigned firstx = 0u;
-                                    for (int i0 = 0; i0 < clx; i0 += 32) {
-                                        const int i = i0 + g.lane;
-                                        bool h1 = false, h2 = false;
-                                        unsigned k1 = 0u;
-                                        if (i < clx) {
-                                            const uint32_t e = xidx[i];
-                                            const uint32_t xc = xcomp[e];
-                                            if ((xc >> u) & 1u) {
-                                                h1 = ((xc >> w1) & 1u) != 0u;
-                                                h2 = ((xc >> w2) & 1u) != 0u;
-                                                if (C.pivot_ipx && h1 != h2)
-                                                    k1 = ((0x7fffffffu - xrank[e]) << 1) | (h1 ? 1u : 0u);
-                                            }
-                                        }
-                                        s2x |= __any_sync(FULL, h1 && h2) != 0;
-                                        x1 |= __any_sync(FULL, h1) != 0;
-                                        x2 |= __any_sync(FULL, h2) != 0;
-                                        if (C.pivot_ipx) firstx = max(firstx, __reduce_max_sync(FULL, k1));
-                                    }
-                                    const bool s2 = s2p || (C.pivot_ipx && s2x);
-                                    if (e12) {
-                                        if (!s2) {
-                                            t_nodes += 2;
-                                            if (!s2x) record(szc + 2, cS + mu + m1 + m2);
-                                        }
-                                    } else if (!s2) {
-                                        int touch = 0;
-                                        if (firstx) touch = (firstx & 1u) ? 1 : 2;
-                                        else if (one) touch = ((a1 >> (__ffs(one) - 1)) & 1u) ? 1 : 2;
-                                        if (touch) {
-                                            t_nodes++;
-                                            const uint32_t aj = touch == 1 ? a2 : a1;
-                                            const bool xj = touch == 1 ? x2 : x1;
-                                            if (!xj && (qx & aj) == 0u) record(szc + 1, cS + mu + (touch == 1 ? m2 : m1));
-                                        } else {
-                                            t_nodes += 2;
-                                            if (!x1) record(szc + 1, cS + mu + m1);
-                                            if (!x2) record(szc + 1, cS + mu + m2);
-                                        }
-                                    }
-                                }
-                                pc.stop(PH_LEAF);
-                                continue;
-                            }
-                            // descend
-                            if (g.lane == d) {
-                                sP = P;
-                                sX = X;
-                                sB = B;
-                                sL = clx;
-                                sS = cS;
-                            }
-                            if (clx > 0) clx = partition(clx, [&](uint32_t e) { return ((xcomp[e] >> u) & 1u) != 0u; });
-                            P = q;
-                            X = qx;
-                            cS += mu;
-                            d++;
-                            centr = true;
-                            t_nodes++;
-                            pc.stop(PH_PARTITION);
-                        }
-                        if (timed_out) break;
-                        continue;
-                    }
-                }
+                // A child with |P'| + |X_P'| <= 32 runs in compact mode (below) after
+                // the usual push of this level and partition of X_X.
+                bool to_compact = false;
+                if (GW == 1 && WP > 1 && pcnt <= 32) to_compact = pcnt + grp_sum(g, red, __popc(cx)) <= 32;
                 // ------------------------------ descend: push this level, partition X_X by v
                 {
                     uint32_t *lv = stk + (size_t)l * LS;
@@ -1337,28 +1454,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         lv[Lvl<WP>::SLO] = (uint32_t)S;
                         lv[Lvl<WP>::SHI] = (uint32_t)(S >> 32);
                     }
-                    int out = 0, nout = 0;
-                    if (lpx > 0) {
-                        for (int it = 0; it < lpx; it += GT) {
-                            const int idx = it + g.gl;
-                            const bool valid = idx < lpx;
-                            const uint32_t e = valid ? xidx[idx] : 0u;
-                            const bool surv = valid && (xrows[(size_t)e * WP + vw] & vb) != 0u;
-                            int ts, tn;
-                            const int ps = grp_prefix(g, red, surv, &ts);
-                            const int pn = grp_prefix(g, red, valid && !surv, &tn);
-                            if (surv) xidx[out + ps] = e;
-                            else if (valid) xscr[nout + pn] = e;
-                            out += ts;
-                            nout += tn;
-                        }
-                        // the group barrier orders these arena writes for the whole group
-                        if (nout > 0) {
-                            g.sync();
-                            for (int j = g.gl; j < nout; j += GT) xidx[out + j] = xscr[j];
-                        }
-                        g.sync();
-                    }
+                    int out = 0;
+                    if (lpx > 0) out = partition(lpx, [&](uint32_t e) { return (xrows[(size_t)e * WP + vw] & vb) != 0u; });
                     pc.stop(PH_PARTITION);
                     pc.count(PH_PARTITION, (unsigned long long)lpx);
                     p = cp;
@@ -1372,6 +1469,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 if (l > rows_cap) {
                     if (g.gl == 0) atomicOr(O.status, ST_OVERFLOW);
                     break;
+                }
+                if (GW == 1 && to_compact) {
+                    kstart = true;
+                    enter = false;
                 }
             }
             if (timed_out && g.gl == 0) atomicOr(O.status, ST_TIMEOUT);

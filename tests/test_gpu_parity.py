@@ -117,6 +117,20 @@ def test_worker_list_interleavings(blocks, donate, wl, policy, pivot):
         assert r.donations == 0
 
 
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
+@pytest.mark.parametrize("blocks,donate", [(2, 3), (8, 10), (0, 0)])
+def test_deep_balanced_tree_split(blocks, donate, pivot):
+    # K_{3x12} plus a sparse random part: every subtree below depth ~3 has
+    # |P| + |X_P| <= 32, so the split across groups must happen inside the
+    # one-word (compact) subtrees; the tree must not change
+    mm = gen.moon_moser(12)
+    g = gen.disjoint_union([gen.gnp(300, 0.03, 7), mm])
+    r, o = check_against_oracle(g, pivot=pivot, blocks=blocks, donate_min_p=donate)
+    assert r.count > 3 ** 12  # the multipartite block alone holds 3^12 maximal cliques
+    if blocks:
+        assert r.donations > 0
+
+
 def test_worker_list_donates():
     g = gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5)
     r = run(g, blocks=2, donate_min_p=1)
