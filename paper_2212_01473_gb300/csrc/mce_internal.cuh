@@ -76,16 +76,19 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
             __threadfence();
             st_release_u(&bar->gen, g + 1);
         } else {
-            unsigned ns = 32;
+            // poll the generation word back to back; the status word and the
+            // clock are read every 64 polls, and long waits back off
+            unsigned spins = 0;
             while (ld_acquire_u(&bar->gen) == g) {
-                if (ld_relaxed(status) & ST_TIMEOUT) { ok = 0; break; }
-                if (globaltimer_ns() > deadline) {
-                    atomicOr(status, ST_TIMEOUT);
-                    ok = 0;
-                    break;
+                if ((++spins & 63u) == 0) {
+                    if (ld_relaxed(status) & ST_TIMEOUT) { ok = 0; break; }
+                    if (globaltimer_ns() > deadline) {
+                        atomicOr(status, ST_TIMEOUT);
+                        ok = 0;
+                        break;
+                    }
+                    if (spins > 4096) __nanosleep(256);
                 }
-                __nanosleep(ns);
-                if (ns < 256) ns <<= 1;
             }
         }
         __threadfence();
