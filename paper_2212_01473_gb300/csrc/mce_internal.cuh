@@ -63,7 +63,9 @@ struct GridBar {
     unsigned gen;
 };
 
-__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t deadline) {
+// nblk: the number of blocks taking part (gridDim.x, or fewer once the others
+// have returned for good).
+__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t deadline, unsigned nblk) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
@@ -71,7 +73,7 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
         unsigned g = ld_acquire_u(&bar->gen);
         __threadfence();
         unsigned arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == gridDim.x - 1) {
+        if (arrived == nblk - 1) {
             atomicExch(&bar->count, 0u);
             __threadfence();
             st_release_u(&bar->gen, g + 1);

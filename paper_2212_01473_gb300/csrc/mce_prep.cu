@@ -157,9 +157,13 @@ __device__ void block_bitonic(int *a, int len) {
 // Segments longer than kSmallSort are put in id order here through a bitmap;
 // shorter ones, and all final ranks, are done by k_peel_rank afterwards.
 //
-// When the live degree sum at a level start is at most kSoloDegrees, block 0
-// finishes alone (block barriers instead of grid barriers); the other blocks
-// return. Removal order and core numbers are the same either way.
+// As the remaining graph shrinks, fewer blocks go on: when the live degree sum
+// at a level start is at most kNarrowDegrees, blocks kNarrowBlocks and up
+// return and the rest meet at cheaper barriers (the dense core's many short
+// sub-rounds are barrier-bound); at most kSoloDegrees, block 0 finishes alone
+// with block barriers. Removal order and core numbers are the same either way.
+constexpr long long kNarrowDegrees = 1ll << 22;
+constexpr int kNarrowBlocks = 16;
 constexpr long long kSoloDegrees = 32768;
 // adjacency lists longer than this are removed by a whole block
 constexpr int kHeavyDeg = 64;
@@ -178,13 +182,14 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     int64_t gwarp = tid >> 5, nwarps = nth >> 5;
     int nblocks = gridDim.x, bid = blockIdx.x;
     bool solo = false;
+    unsigned nbar = gridDim.x;  // blocks meeting at grid barriers
     GridBar *gbar = &ctl->bar;
     auto barrier = [&]() -> bool {
         if (solo) {
             __syncthreads();
             return true;
         }
-        return grid_barrier(gbar, status, deadline);
+        return grid_barrier(gbar, status, deadline, nbar);
     };
 
     for (int64_t v = tid; v < n; v += nth) {
@@ -228,8 +233,18 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         }
         if (!barrier()) return;
         k = max(k, vload(&ctl->minval[L & 1]));
-        if (!solo && (long long)*(volatile unsigned long long *)&ctl->sumdeg[L & 1] <= kSoloDegrees) {
-            // every block read the same sum after the barrier
+        // every block reads the same sum after the barrier and decides alike
+        const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[L & 1];
+        if (!solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && live > kSoloDegrees) {
+            if (blockIdx.x >= kNarrowBlocks) return;
+            nbar = kNarrowBlocks;
+            nblocks = kNarrowBlocks;
+            tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+            nth = (int64_t)kNarrowBlocks * blockDim.x;
+            gwarp = tid >> 5;
+            nwarps = nth >> 5;
+        }
+        if (!solo && live <= kSoloDegrees) {
             if (blockIdx.x != 0) return;
             solo = true;
             tid = threadIdx.x;
