@@ -173,6 +173,25 @@ int mce_run(mce_graph *g, const mce_opts *opts, mce_result *out, uint64_t *hist,
  * g's histogram), both HOST buffers; hist may be NULL. `total`, when not
  * NULL, receives the sums over all graphs.
  */
+/*
+ * mce_run_list -- every maximal clique of a single-graph handle, listed.
+ * The paper's kernels only count the cliques they find; this call also writes
+ * each clique C to buf as one record [|C|, id_1, ..., id_|C|] of int32 words (input
+ * vertex ids, in no particular order; records in no particular order).
+ *   buf        device memory of cap_words int32 words, or NULL: then only
+ *              the size is computed (cap_words ignored)
+ *   *words     receives the number of words the complete list needs
+ *   out        the same results as mce_run (count, hash, ...)
+ * opts as for mce_run; opts.roots restricts the listing to those roots'
+ * first-level subtrees, which partition M(G) (every clique is listed under
+ * its earliest vertex in the degeneracy order), so a list too large for one
+ * buffer is produced root subset by root subset. Returns MCE_ERANGE when buf
+ * is given and *words > cap_words: the records that fit are written, the
+ * others dropped.
+ */
+int mce_run_list(mce_graph *g, const mce_opts *opts, int32_t *buf, int64_t cap_words, int64_t *words,
+                 mce_result *out);
+
 int mce_run_batch(mce_graph *g, const mce_opts *opts, mce_result *per_graph, uint64_t *hist,
                   int32_t hist_len, mce_result *total);
 

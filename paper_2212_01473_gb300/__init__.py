@@ -9,7 +9,8 @@ from .engine import (mce_predict_priority, mce_autotune, mce_prepare, mce_run_pr
                      MCE_PIVOT_IP, MCE_PIVOT_IPX, MCEError, Result, enumerate_maximal_cliques, library,
                      mce_batch_create, mce_create, mce_default_opts, mce_destroy, mce_get_order,
                      mce_get_stats, mce_graph_info, mce_peel_noalloc, mce_root_features, mce_run, mce_run_batch,
+                     mce_run_list, decode_clique_records, list_maximal_cliques,
                      Model, MCE_MODEL_PARAMS, MCE_NUM_FEATURES)
 
 __all__ = [name for name in dir() if name.startswith(("mce_", "MCE"))] + [
-    "Model", "Result", "enumerate_maximal_cliques", "library"]
+    "Model", "Result", "enumerate_maximal_cliques", "library", "decode_clique_records", "list_maximal_cliques"]

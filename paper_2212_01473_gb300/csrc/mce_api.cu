@@ -75,6 +75,14 @@ __global__ void k_trivial_roots(DevGraph G, DevOut O, const int32_t *roots, int 
             if (O.root_nodes) O.root_nodes[id] += 1ull;
             if (clique && O.root_count) O.root_count[id] += 1ull;
             if (clique && O.root_hash) O.root_hash[id] += h;
+            if (clique && O.list) {
+                // record [1, id]; the cursor counts it even when it does not fit
+                const unsigned long long pos = atomicAdd(O.list_used, 2ull);
+                if (pos + 2ull <= O.list_cap) {
+                    O.list[pos] = 1;
+                    O.list[pos + 1] = id;
+                }
+            }
             if (G.gid) {
                 if (clique) {
                     const int gid = G.gid[r];
@@ -978,6 +986,48 @@ extern "C" int mce_run(mce_graph *g, const mce_opts *opts, mce_result *out, uint
     if (g->G != 1) return fail(MCE_EINVAL, "batched handle: use mce_run_batch");
     if (!out) return fail(MCE_EINVAL, "out is NULL");
     return run_impl(g, opts, out, hist, hist_len, nullptr);
+}
+
+extern "C" int mce_run_list(mce_graph *g, const mce_opts *opts, int32_t *buf, int64_t cap_words, int64_t *words,
+                            mce_result *out) {
+    if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    if (g->G != 1) return fail(MCE_EINVAL, "batched handle: listing takes one graph");
+    if (!out || !words) return fail(MCE_EINVAL, "out or words is NULL");
+    if (cap_words < 0) return fail(MCE_EINVAL, "cap_words < 0");
+    if (cap_words > 0 && !buf) return fail(MCE_EINVAL, "buf is NULL");
+    if (buf) {
+        cudaPointerAttributes at{};
+        if (cudaPointerGetAttributes(&at, buf) != cudaSuccess ||
+            (at.type != cudaMemoryTypeDevice && at.type != cudaMemoryTypeManaged)) {
+            cudaGetLastError();
+            return fail(MCE_EINVAL, "buf must be device memory");
+        }
+    }
+    *words = 0;
+    RunPlan *P = nullptr;
+    int rc = plan_run(g, opts, kAllClasses, nullptr, &P);
+    if (rc != MCE_OK) return rc;
+    // the records' cursor sits in the spare words after the run's outputs
+    unsigned long long *cursor = P->obuf + (P->obuf_bytes - 64) / 8;
+    P->dout.list = buf ? buf : (int32_t *)P->obuf;  // non-null; with cap 0 nothing is written
+    P->dout.list_cap = buf ? (unsigned long long)cap_words : 0ull;
+    P->dout.list_used = cursor;
+    rc = enqueue_run(g, P);
+    if (rc == MCE_OK) rc = collect_run(g, P, out, nullptr, 0, nullptr);
+    if (rc == MCE_OK) {
+        unsigned long long used = 0;
+        cudaError_t e = cudaMemcpyAsync(&used, cursor, 8, cudaMemcpyDeviceToHost, g->stream);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(g->stream);
+        if (e != cudaSuccess) rc = fail(MCE_ECUDA, "reading the list cursor: %s", cudaGetErrorString(e));
+        else {
+            *words = (int64_t)used;
+            if (buf && used > (unsigned long long)cap_words)
+                rc = fail(MCE_ERANGE, "the list needs %llu words, buf holds %lld (split opts.roots)", used,
+                          (long long)cap_words);
+        }
+    }
+    free_plan(g, P);
+    return rc;
 }
 
 extern "C" int mce_run_batch(mce_graph *g, const mce_opts *opts, mce_result *per_graph, uint64_t *hist,

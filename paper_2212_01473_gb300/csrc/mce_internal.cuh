@@ -153,6 +153,9 @@ struct DevOut {
     int *status;
     unsigned long long *phase_cycles;  // [kNumPhases]
     unsigned long long *phase_counts;  // [kNumPhases]
+    int32_t *list;                     // optional clique records [k, id_1 .. id_k]
+    unsigned long long list_cap;       // words of list
+    unsigned long long *list_used;     // [1] words the complete list needs
 };
 
 // Host-side launch of one width class of the traversal (mce_traverse*.cu).

@@ -22,7 +22,7 @@
 // index reaching it is then the argmax, so the pivot is the same as a full scan.
 //
 // Template parameters: WP padded words per row, GW warps per group, AG true
-// when A lives in the global arena (rows too wide for shared memory).
+// when A lives in the global arena, LIST true when cliques are listed.
 #pragma once
 #include "mce_internal.cuh"
 
@@ -104,7 +104,7 @@ __host__ __device__ inline size_t smem_bytes(const GrpSmem &L, int groups_per_bl
 }
 
 // Arena words per group: [stack if global][A rows][X rows][xidx][xscr][xrank]
-// [xcomp].
+// [xcomp][R ids: the current clique's input ids, when cliques are listed].
 // The A region holds A itself when it lives in global memory, else it is the
 // landing area where a donor writes A for this group when it is a receiver.
 __host__ __device__ inline size_t arena_words(int wp, int rows, int xcap, bool a_global, bool stack_smem) {
@@ -112,6 +112,7 @@ __host__ __device__ inline size_t arena_words(int wp, int rows, int xcap, bool a
     if (!stack_smem) w += stack_words(wp, rows);
     w += (size_t)rows * wp;
     w += (size_t)xcap * wp + 4 * (size_t)xcap;
+    w += (size_t)rows + 2;
     (void)a_global;
     return align_up(w, 4);
 }
@@ -120,6 +121,7 @@ struct ArenaPtrs {
     uint32_t *stk, *A, *xrows, *xidx, *xscr;
     uint32_t *xrank;  // xrank[slot]: degeneracy rank of that X_X row's vertex
     uint32_t *xcomp;  // xcomp[slot]: that row over a compact subtree's index space
+    uint32_t *rid;    // rid[i]: input id of the i-th vertex of the current R (listing)
 };
 
 __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, int xcap, bool stack_smem) {
@@ -134,6 +136,7 @@ __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, 
     a.xscr = a.xidx + xcap;
     a.xrank = a.xscr + xcap;
     a.xcomp = a.xrank + xcap;
+    a.rid = a.xcomp + xcap;
     return a;
 }
 
@@ -309,7 +312,9 @@ struct PhaseClock {
     }
 };
 
-template <int WP, int GW, bool AG>
+// LIST: the variant that also writes each clique's members (mce_run_list);
+// the counting variant carries none of that code.
+template <int WP, int GW, bool AG, bool LIST>
 __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArgs C, int rows_cap, int stack_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int GT = 32 * GW;
@@ -350,6 +355,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
     uint32_t *xscr = ar.xscr;
     uint32_t *xrank = ar.xrank;
     uint32_t *xcomp = ar.xcomp;
+    uint32_t *rid = ar.rid;
+    constexpr bool listing = LIST;
 
     const uint64_t deadline = globaltimer_ns() + C.timeout_ns;
     PhaseClock pc{};
@@ -602,6 +609,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     const int lo = g.gl * 32;
                     if (lo < n0) p = (n0 - lo >= 32) ? 0xffffffffu : ((1u << (n0 - lo)) - 1u);
                 }
+                if (listing && g.gl == 0) rid[0] = (uint32_t)G.order[r];
             } else if (!cmail) {
                 // P', X_P' and the path R' below the root come from the mail; the
                 // X_X rows in the arena are exactly the donor's survivors
@@ -632,13 +640,28 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             int l = l0;
             bool enter = true;
             bool timed_out = false;
-            auto record = [&](int sz, uint64_t sum) {
+            // one maximal clique of sz vertices: R's first sz - nx ids (rid) and up
+            // to three more (x1..x3); sum = the sum of its members' hash ids
+            auto record = [&](int sz, uint64_t sum, int nx, int32_t x1, int32_t x2, int32_t x3) {
                 if (g.gl == 0) {
                     t_cnt++;
                     t_hash += mix64(sum + (uint64_t)sz * kPhi);
                     if (block_hist) atomicAdd(&hist[sz], 1ull);
                     else hist[sz] += 1ull;
                     acc_maxsz = max(acc_maxsz, sz);
+                    if (listing) {
+                        // the cursor counts every record; only those that fit are written
+                        const unsigned long long pos = atomicAdd(O.list_used, (unsigned long long)sz + 1ull);
+                        if (pos + (unsigned long long)sz + 1ull <= O.list_cap) {
+                            int32_t *dst = O.list + pos;
+                            const int nr = sz - nx;
+                            dst[0] = sz;
+                            for (int i = 0; i < nr; i++) dst[1 + i] = (int32_t)rid[i];
+                            if (nx > 0) dst[1 + nr] = x1;
+                            if (nx > 1) dst[2 + nr] = x2;
+                            if (nx > 2) dst[3 + nr] = x3;
+                        }
+                    }
                 }
             };
             // move the X_X rows e of xidx[0, n_in) with holds(e) to the front; returns their number
@@ -813,6 +836,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     // lane i: clique-hash id of L[i] (lanes past |L| hold a harmless
                     // copy of P0[0]'s), and the saved state of compact depth i
                     const uint64_t kmj = G.mixid[p0[kL]];
+                    const int32_t kid = listing ? G.order[p0[kL]] : 0;  // input id of L[i]
                     uint32_t ksP = 0u, ksX = 0u, ksB = 0u, ksL = 0u;
                     uint64_t ksS = 0ull;
                     for (;;) {
@@ -889,6 +913,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         kX |= ubit;
                         const int qn = __popc(q);
                         const uint64_t mu = __shfl_sync(FULL, kmj, u);
+                        const int32_t idu = __shfl_sync(FULL, kid, u);
                         const int szc = kbase + kd + 1;  // |R u {u}|
                         pc.stop(PH_BRANCH);
                         if (qn <= 2) {
@@ -904,7 +929,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             };
                             if (qn == 0) {
                                 if (qx == 0u && !xx_any([&](uint32_t xc) { return ((xc >> u) & 1u) != 0u; }))
-                                    record(szc, kS + mu);
+                                    record(szc, kS + mu, 1, idu, 0, 0);
                             } else if (qn == 1) {
                                 // as for a one-vertex P' in the wide walk
                                 const int w = __ffs(q) - 1;
@@ -913,13 +938,15 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                     const uint32_t both = ubit | (1u << w);
                                     const bool found = xx_any([&](uint32_t xc) { return (xc & both) == both; });
                                     if (!found || !ipx) t_nodes++;
-                                    if (!found) record(szc + 1, kS + mu + __shfl_sync(FULL, kmj, w));
+                                    const int32_t idw = __shfl_sync(FULL, kid, w);
+                                    if (!found) record(szc + 1, kS + mu + __shfl_sync(FULL, kmj, w), 2, idu, idw, 0);
                                 }
                             } else {
                                 // as for a two-vertex P' in the wide walk
                                 const int w1 = __ffs(q) - 1, w2 = 31 - __clz(q);
                                 const uint32_t a1 = __shfl_sync(FULL, kRow, w1), a2 = __shfl_sync(FULL, kRow, w2);
                                 const uint64_t m1 = __shfl_sync(FULL, kmj, w1), m2 = __shfl_sync(FULL, kmj, w2);
+                                const int32_t id1 = __shfl_sync(FULL, kid, w1), id2 = __shfl_sync(FULL, kid, w2);
                                 const bool e12 = ((a1 >> w2) & 1u) != 0u;
                                 const bool s2p = (qx & a1 & a2) != 0u;
                                 const uint32_t one = qx & (a1 ^ a2);
@@ -947,7 +974,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                 if (e12) {
                                     if (!s2) {
                                         t_nodes += 2;
-                                        if (!s2x) record(szc + 2, kS + mu + m1 + m2);
+                                        if (!s2x) record(szc + 2, kS + mu + m1 + m2, 3, idu, id1, id2);
                                     }
                                 } else if (!s2) {
                                     int touch = 0;
@@ -957,11 +984,12 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                         t_nodes++;
                                         const uint32_t aj = touch == 1 ? a2 : a1;
                                         const bool xj = touch == 1 ? x2 : x1;
-                                        if (!xj && (qx & aj) == 0u) record(szc + 1, kS + mu + (touch == 1 ? m2 : m1));
+                                        if (!xj && (qx & aj) == 0u)
+                                            record(szc + 1, kS + mu + (touch == 1 ? m2 : m1), 2, idu, touch == 1 ? id2 : id1, 0);
                                     } else {
                                         t_nodes += 2;
-                                        if (!x1) record(szc + 1, kS + mu + m1);
-                                        if (!x2) record(szc + 1, kS + mu + m2);
+                                        if (!x1) record(szc + 1, kS + mu + m1, 2, idu, id1, 0);
+                                        if (!x2) record(szc + 1, kS + mu + m2, 2, idu, id2, 0);
                                     }
                                 }
                             }
@@ -1006,6 +1034,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                         m[3] = 1u;
                                         m[68] = q;
                                         m[69] = qx;
+                                        if (listing) {
+                                            for (int qd = 0; qd < szc - 1; qd++) ra.rid[qd] = rid[qd];
+                                            ra.rid[szc - 1] = (uint32_t)idu;
+                                        }
                                         m[70] = (uint32_t)s2;
                                         m[71] = (uint32_t)(s2 >> 32);
                                     }
@@ -1032,6 +1064,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             ksS = kS;
                         }
                         if (kclx > 0) kclx = partition(kclx, [&](uint32_t e) { return ((xcomp[e] >> u) & 1u) != 0u; });
+                        if (listing && g.lane == 0) rid[kbase + kd] = (uint32_t)idu;
                         kP = q;
                         kX = qx;
                         kS += mu;
@@ -1187,14 +1220,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             found = grp_or(g, red, hit);
                         }
                         pc.count(PH_LEAF, (unsigned long long)min(it, lpx));
-                        if (!found && g.gl == 0) {
-                            const int sz = l + 2;
-                            t_cnt++;
-                            t_hash += mix64(S + G.mixid[p0[v]] + (uint64_t)sz * kPhi);
-                            if (block_hist) atomicAdd(&hist[sz], 1ull);
-                            else hist[sz] += 1ull;
-                            acc_maxsz = max(acc_maxsz, sz);
-                        }
+                        if (!found && g.gl == 0)
+                            record(l + 2, S + G.mixid[p0[v]], 1, listing ? G.order[p0[v]] : 0, 0, 0);
                     }
                     pc.stop(PH_LEAF);
                     continue;
@@ -1230,14 +1257,9 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         // maximality. IPX also scores X_X': an adjacent row there is
                         // a score-1 pivot and the leaf does not exist.
                         if (!found || !C.pivot_ipx) t_nodes++;
-                        if (!found && g.gl == 0) {
-                            const int sz = l + 3;
-                            t_cnt++;
-                            t_hash += mix64(S + G.mixid[p0[v]] + G.mixid[p0[u]] + (uint64_t)sz * kPhi);
-                            if (block_hist) atomicAdd(&hist[sz], 1ull);
-                            else hist[sz] += 1ull;
-                            acc_maxsz = max(acc_maxsz, sz);
-                        }
+                        if (!found && g.gl == 0)
+                            record(l + 3, S + G.mixid[p0[v]] + G.mixid[p0[u]], 2, listing ? G.order[p0[v]] : 0,
+                                   listing ? G.order[p0[u]] : 0, 0);
                     }
                     pc.stop(PH_LEAF);
                     continue;
@@ -1291,18 +1313,17 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     }
                     pc.count(PH_LEAF, (unsigned long long)lpx);
                     const bool s2 = s2p || (C.pivot_ipx && s2x);
-                    // cliques found here (at most two), as (size, member sum)
-                    int nq = 0, sz0 = 0, sz1 = 0;
-                    uint64_t m0 = 0, m1 = 0;
+                    // at most two cliques: R u {v, u1, u2}, R u {v, u_j}, or both R u {v, u1}
+                    // and R u {v, u2}
                     const uint64_t mv = G.mixid[p0[v]];
+                    const bool lead = g.gl == 0;
+                    auto id_of = [&](int x) -> int32_t { return listing ? G.order[p0[x]] : 0; };
                     if (e12) {
                         if (!s2) {
                             t_nodes += 2;
-                            if (!s2x) {
-                                nq = 1;
-                                sz0 = l + 4;
-                                m0 = mv + G.mixid[p0[u1]] + G.mixid[p0[u2]];
-                            }
+                            if (!s2x && lead)
+                                record(l + 4, S + mv + G.mixid[p0[u1]] + G.mixid[p0[u2]], 3, id_of(v), id_of(u1),
+                                       id_of(u2));
                         }
                     } else if (!s2) {
                         // the first score-1 candidate: X_X' rows first (IPX), then X_P'
@@ -1324,42 +1345,14 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             const int uj = touch == 1 ? u2 : u1;
                             const uint32_t aj = touch == 1 ? a2 : a1;
                             const bool xj = touch == 1 ? x2 : x1;
-                            if (!xj && !grp_or(g, red, (cx & aj) != 0u)) {
-                                nq = 1;
-                                sz0 = l + 3;
-                                m0 = mv + G.mixid[p0[uj]];
-                            }
+                            if (!xj && !grp_or(g, red, (cx & aj) != 0u) && lead)
+                                record(l + 3, S + mv + G.mixid[p0[uj]], 2, id_of(v), id_of(uj), 0);
                         } else {
                             // no candidate is adjacent to u1 or u2: two leaves, and only
                             // the X_X' rows (not candidates under IP) can block them
                             t_nodes += 2;
-                            if (!x1) {
-                                sz0 = l + 3;
-                                m0 = mv + G.mixid[p0[u1]];
-                                nq = 1;
-                            }
-                            if (!x2) {
-                                if (nq) {
-                                    sz1 = l + 3;
-                                    m1 = mv + G.mixid[p0[u2]];
-                                } else {
-                                    sz0 = l + 3;
-                                    m0 = mv + G.mixid[p0[u2]];
-                                }
-                                nq++;
-                            }
-                        }
-                    }
-                    if (nq && g.gl == 0) {
-                        t_cnt += nq;
-                        t_hash += mix64(S + m0 + (uint64_t)sz0 * kPhi);
-                        if (block_hist) atomicAdd(&hist[sz0], 1ull);
-                        else hist[sz0] += 1ull;
-                        acc_maxsz = max(acc_maxsz, sz0);
-                        if (nq == 2) {
-                            t_hash += mix64(S + m1 + (uint64_t)sz1 * kPhi);
-                            if (block_hist) atomicAdd(&hist[sz1], 1ull);
-                            else hist[sz1] += 1ull;
+                            if (!x1 && lead) record(l + 3, S + mv + G.mixid[p0[u1]], 2, id_of(v), id_of(u1), 0);
+                            if (!x2 && lead) record(l + 3, S + mv + G.mixid[p0[u2]], 2, id_of(v), id_of(u2), 0);
                         }
                     }
                     pc.stop(PH_LEAF);
@@ -1421,6 +1414,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             m[1] = (uint32_t)(l + 1);
                             m[2] = (uint32_t)out;
                             m[3] = 0u;
+                            if (listing) {
+                                for (int qd = 0; qd <= l; qd++) ra.rid[qd] = rid[qd];
+                                ra.rid[l + 1] = (uint32_t)G.order[p0[v]];
+                            }
                         }
                         __threadfence();
                         g.sync();
@@ -1463,6 +1460,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     lpx = out;
                     npend += others_here ? 1 : 0;
                     S += G.mixid[p0[v]];
+                    if (listing && g.gl == 0) rid[l + 1] = (uint32_t)G.order[p0[v]];
                 }
                 l++;
                 enter = true;

@@ -107,6 +107,8 @@ def library():
         lib.mce_model_gradient.argtypes = [vp, vp, vp, i32, f32p, f32p]
         lib.mce_model_train_step.argtypes = [vp, vp, vp, i32, ctypes.c_float, f32p]
         lib.mce_predict_priority.argtypes = [vp, vp, i32, vp]
+        lib.mce_run_list.argtypes = [vp, ctypes.POINTER(mce_opts), vp, i64, ctypes.POINTER(ctypes.c_int64),
+                                     ctypes.POINTER(mce_result)]
         lib.mce_model_destroy.argtypes = [vp]
         lib.mce_model_destroy.restype = None
         lib.mce_destroy.argtypes = [vp]
@@ -446,6 +448,69 @@ def mce_destroy(h: Handle):
     if h is not None and h.ptr:
         library().mce_destroy(h.ptr)
         h.ptr = ctypes.c_void_p()
+
+
+def mce_run_list(h: Handle, buf=None, opts: Optional[mce_opts] = None):
+    """List the maximal cliques into `buf` (a CUDA int32 tensor; None: only
+    size the list) as records [k, id_1, ..., id_k] (see include/mce.h).
+    Returns (Result, words needed). Raises MCEError(MCE_ERANGE) when the list
+    does not fit; the records that fit are written."""
+    lib = library()
+    words = ctypes.c_int64(0)
+    r = mce_result()
+    if buf is not None:
+        import torch
+        if not (isinstance(buf, torch.Tensor) and buf.is_cuda and buf.dtype == torch.int32 and buf.is_contiguous()):
+            raise TypeError("buf must be a contiguous CUDA int32 tensor")
+        ptr, cap = buf.data_ptr(), buf.numel()
+    else:
+        ptr, cap = None, 0
+    _check(lib.mce_run_list(h.ptr, ctypes.byref(opts) if opts is not None else None, ptr, cap,
+                            ctypes.byref(words), ctypes.byref(r)))
+    return _result(r), int(words.value)
+
+
+def decode_clique_records(flat) -> List[np.ndarray]:
+    """Split a list of records [k, id_1, ..., id_k] (numpy int32) into arrays."""
+    out, i, n = [], 0, len(flat)
+    while i < n:
+        k = int(flat[i])
+        out.append(np.asarray(flat[i + 1:i + 1 + k]))
+        i += 1 + k
+    return out
+
+
+def list_maximal_cliques(row_ptr, col, max_words: int = 1 << 26, **opt_fields) -> List[np.ndarray]:
+    """One-shot listing of every maximal clique (input vertex ids), produced
+    root subset by root subset so that no buffer exceeds max_words words."""
+    import torch
+    h = mce_create(row_ptr, col)
+    try:
+        _, need = mce_run_list(h, None, mce_default_opts(**opt_fields))
+        pieces = []
+
+        def go(roots):
+            opts = mce_default_opts(**opt_fields)
+            keep = None
+            if roots is not None:
+                keep = torch.as_tensor(np.ascontiguousarray(roots, dtype=np.int32)).cuda()
+                opts.roots = keep.data_ptr()
+                opts.n_roots = len(keep)
+            _, w = mce_run_list(h, None, opts)
+            if w <= max_words or (roots is not None and len(roots) == 1):
+                buf = torch.empty(max(w, 1), dtype=torch.int32, device="cuda")
+                _, w2 = mce_run_list(h, buf, opts)
+                pieces.extend(decode_clique_records(buf[:w2].cpu().numpy()))
+                return
+            ids = np.arange(h.n, dtype=np.int32) if roots is None else np.asarray(roots)
+            half = len(ids) // 2
+            go(ids[:half])
+            go(ids[half:])
+
+        go(None if need <= max_words else np.arange(h.n, dtype=np.int32))
+        return pieces
+    finally:
+        mce_destroy(h)
 
 
 def enumerate_maximal_cliques(row_ptr, col, per_root: bool = False, roots=None, **opt_fields):
