@@ -12,6 +12,7 @@ import numpy as np
 from . import build as _build
 
 PIVOT_FULL, PIVOT_IP, NO_PIVOT = 0, 1, 2
+SECOND_LEVEL = 8  # or-ed into a mode: one subtree per edge (Algorithm 4)
 
 _lib = None
 
@@ -85,8 +86,11 @@ def peel(row_ptr, col):
 
 
 def mce(row_ptr, col, mode: int = PIVOT_FULL, threads: int = 0, per_root: bool = False,
-        roots=None, hist_len: int = 0) -> Result:
-    """All maximal cliques (or those of the listed roots' first-level subtrees)."""
+        roots=None, hist_len: int = 0, level: int = 1) -> Result:
+    """All maximal cliques (or those of the listed roots' subtrees). level 2:
+    one subtree per edge (Algorithm 4); per-root values sum a vertex's edges."""
+    if level == 2:
+        mode |= SECOND_LEVEL
     rp, rpp = _i32(row_ptr)
     c, cp = _i32(col if len(col) else np.zeros(1, np.int32))
     n = len(rp) - 1

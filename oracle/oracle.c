@@ -125,7 +125,8 @@ typedef struct {
     const int32_t *ap;    /* relabelled adjacency offsets, [n+1] */
     const int32_t *adj;   /* neighbours of rank r as sorted ranks */
     const int32_t *order; /* rank -> input id */
-    int32_t mode;
+    int32_t mode;         /* pivot rule */
+    int32_t second_level; /* one subtree per edge (Algorithm 4) */
 } graph_t;
 
 typedef struct {
@@ -274,6 +275,51 @@ static void first_level(walk_t *w, int32_t r) {
     free(XP);
 }
 
+/*
+ * Algorithm 4 for the vertex of rank r: one subtree per later neighbour v_j,
+ * with R = {r, v_j}, P = the common neighbours after v_j, X = the common
+ * neighbours before v_j (held as XP = those after r, XX = those before r).
+ * Every maximal clique with two or more vertices lies under the edge of its
+ * two earliest vertices; an isolated vertex is a maximal clique of its own and
+ * has no subtree. Tree nodes count the edge subtrees' nodes only.
+ */
+static void second_level(walk_t *w, int32_t r) {
+    const graph_t *g = w->g;
+    const int32_t *row = g->adj + g->ap[r];
+    int32_t deg = g->ap[r + 1] - g->ap[r];
+    int32_t split = 0;
+    while (split < deg && row[split] < r) split++;
+    const int32_t np = deg - split;
+    const int32_t *later = row + split;
+    w->words = (np + 31) / 32;
+    w->root = r;
+    w->rlen = 0;
+    w->R[w->rlen++] = r;
+    if (deg == 0) {
+        report(w);
+        return;
+    }
+    int32_t *P = (int32_t *)malloc((size_t)(np + 1) * sizeof(int32_t));
+    int32_t *XP = (int32_t *)malloc((size_t)(np + 1) * sizeof(int32_t));
+    int32_t *XX = (int32_t *)malloc((size_t)(split + 1) * sizeof(int32_t));
+    for (int32_t j = 0; j < np; j++) {
+        const int32_t vj = later[j];
+        int32_t nP = 0, nXP = 0, nXX = 0;
+        for (int32_t k = j + 1; k < np; k++)
+            if (adjacent(g, vj, later[k])) P[nP++] = later[k];
+        for (int32_t k = 0; k < j; k++)
+            if (adjacent(g, vj, later[k])) XP[nXP++] = later[k];
+        for (int32_t k = 0; k < split; k++)
+            if (adjacent(g, vj, row[k])) XX[nXX++] = row[k];
+        w->R[w->rlen++] = vj;
+        bk(w, P, nP, XP, nXP, XX, nXX);
+        w->rlen--;
+    }
+    free(P);
+    free(XP);
+    free(XX);
+}
+
 typedef struct {
     const graph_t *g;
     const int32_t *roots; /* ranks to process */
@@ -310,7 +356,8 @@ static void *worker(void *arg) {
         if (i >= job->n_roots) break;
         int32_t r = job->roots[i];
         uint64_t c0 = w.count, h0 = w.hash, n0 = w.nodes, k0 = w.work;
-        first_level(&w, r);
+        if (job->g->second_level) second_level(&w, r);
+        else first_level(&w, r);
         int32_t id = job->g->order[r];
         if (job->root_count) job->root_count[id] = w.count - c0;
         if (job->root_hash) job->root_hash[id] = w.hash - h0;
@@ -337,6 +384,8 @@ static int run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mo
                uint64_t *hist, int32_t hist_len, int32_t *max_size, uint64_t *root_count,
                uint64_t *root_hash, uint64_t *root_nodes, uint64_t *root_work) {
     if (oracle_validate(n, row_ptr, col)) return 1;
+    const int32_t second = (mode & ORACLE_SECOND_LEVEL) != 0;
+    mode &= ~ORACLE_SECOND_LEVEL;
     if (mode < 0 || mode > 2) return 1;
     int32_t *rank = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
     int32_t *order = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
@@ -368,7 +417,7 @@ static int run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mo
         for (int32_t r = 0; r < n; r++) roots[r] = r;
         n_roots = n;
     }
-    graph_t g = {ap, adj, order, mode};
+    graph_t g = {ap, adj, order, mode, second};
     job_t job;
     memset(&job, 0, sizeof(job));
     job.g = &g;

@@ -35,7 +35,10 @@ extern "C" {
 enum {
     ORACLE_PIVOT_FULL = 0, /* Tomita: pivot from P u X (Sec. II-C) */
     ORACLE_PIVOT_IP = 1,   /* pivot from P u X_P only (Sec. III-E, partial induced subgraph) */
-    ORACLE_NO_PIVOT = 2    /* Algorithm 1 */
+    ORACLE_NO_PIVOT = 2,   /* Algorithm 1 */
+    /* flag, or-ed into a mode: one independent subtree per edge {v_i, v_j}
+     * (Algorithm 4, Sec. III-B) instead of one per vertex (Algorithm 3) */
+    ORACLE_SECOND_LEVEL = 8
 };
 
 /* 0 if (row_ptr, col) is a canonical simple undirected CSR over n vertices */

@@ -221,6 +221,40 @@ def test_node_counts_complete_graph(n):
     assert ip.root_count.tolist() == [1] + [0] * (n - 1)
 
 
+@pytest.mark.parametrize("n", [2, 3, 6, 10])
+def test_second_level_node_counts_complete_graph(n):
+    # K_n, one subtree per edge (i, j), i < j (Algorithm 4): X = {0..j-1} - {i}.
+    # Full Tomita: only edge (0, 1) has X empty and walks a chain of n - 1
+    # calls; every other edge node has a pivot in X adjacent to all of P.
+    g = gen.complete(n)
+    full = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_FULL, per_root=True, level=2)
+    assert int(full.root_nodes.sum()) == n * (n - 1) // 2 + n - 2
+    assert full.root_nodes[0] == (n - 1) + (n - 2)  # edges (0, 1) .. (0, n-1)
+    # pivot from P u X_P: edge (j-1, j) has X_P empty and walks n - j calls,
+    # the others stop at once: (n-1)^2 in all
+    ip = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=True, level=2)
+    assert int(ip.root_nodes.sum()) == (n - 1) ** 2
+    assert ip.root_nodes.tolist() == [(n - 1 - j - 1 + 1) + (n - 2 - j) for j in range(n - 1)] + [0]
+    # no pivot: edge (i, j) spans all 2^(n-1-j) subsets of the vertices after j
+    nop = oracle.mce(g.row_ptr, g.col, mode=oracle.NO_PIVOT, per_root=True, level=2)
+    assert int(nop.root_nodes.sum()) == 2 ** n - n - 1
+    for o in (full, ip, nop):
+        assert o.count == 1 and o.root_count.tolist() == [1] + [0] * (n - 1)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_second_level_same_cliques(seed):
+    # edge subtrees partition M(G) minus the isolated vertices, which are
+    # cliques of their own: every result equals the first-level walk's
+    g = gen.disjoint_union([gen.small_gnp(35, 0.25, seed), gen.empty(3), gen.moon_moser(3)])
+    for mode in (oracle.PIVOT_FULL, oracle.PIVOT_IP, oracle.NO_PIVOT):
+        a = oracle.mce(g.row_ptr, g.col, mode=mode, per_root=True)
+        b = oracle.mce(g.row_ptr, g.col, mode=mode, per_root=True, level=2)
+        assert (a.count, a.hash, a.max_size) == (b.count, b.hash, b.max_size)
+        assert np.array_equal(a.hist, b.hist)
+        assert np.array_equal(a.root_count, b.root_count) and np.array_equal(a.root_hash, b.root_hash)
+
+
 # ------------------------------------------------------------ degeneracy peel
 
 def naive_cores(g):
