@@ -112,7 +112,10 @@ typedef struct {
     const int32_t *roots;
     int64_t n_roots;
     int32_t tuned;         /* 1 = use the per-width-class settings mce_autotune chose for this handle */
-    int32_t reserved;
+    int32_t subtree_level; /* independent subtrees per vertex (0 or 1, Algorithm 3) or per edge
+                            (2, Algorithm 4: R = {v_i, v_j}, no pivot step at the vertex level);
+                            results are the same, tree nodes differ; opts.roots then selects
+                            the edges of those vertices */
 } mce_opts;
 
 typedef struct {

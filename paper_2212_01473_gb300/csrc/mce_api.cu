@@ -59,7 +59,9 @@ static cudaError_t launch_class_wp(const ClassLaunch &L, const DevGraph &g, cons
 
 // Roots with no later neighbours (|P0| = 0): the subtree is the root call
 // alone; {r} is a maximal clique iff r has no earlier neighbour either.
-__global__ void k_trivial_roots(DevGraph G, DevOut O, const int32_t *roots, int n_roots) {
+// At level 2 (one subtree per edge) these vertices have no subtree and add no
+// tree node; an isolated one is still a maximal clique.
+__global__ void k_trivial_roots(DevGraph G, DevOut O, const int32_t *roots, int n_roots, int level2) {
     unsigned long long cnt = 0, hsh = 0;
     const int lane = threadIdx.x & 31;
     const int64_t lim = ((int64_t)n_roots + 31) / 32 * 32;
@@ -72,7 +74,7 @@ __global__ void k_trivial_roots(DevGraph G, DevOut O, const int32_t *roots, int 
             clique = G.in_ptr[r + 1] == G.in_ptr[r];
             const int id = G.order[r];
             uint64_t h = clique ? mix64(G.mixid[r] + kPhi) : 0ull;
-            if (O.root_nodes) O.root_nodes[id] += 1ull;
+            if (O.root_nodes && !level2) O.root_nodes[id] += 1ull;
             if (clique && O.root_count) O.root_count[id] += 1ull;
             if (clique && O.root_hash) O.root_hash[id] += h;
             if (clique && O.list) {
@@ -106,7 +108,7 @@ __global__ void k_trivial_roots(DevGraph G, DevOut O, const int32_t *roots, int 
         atomicAdd(&O.hash[0], hsh);
         if (O.hist_len > 1) atomicAdd(&O.hist[1], cnt);
     }
-    if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(O.nodes, (unsigned long long)n_roots);
+    if (blockIdx.x == 0 && threadIdx.x == 0 && !level2) atomicAdd(O.nodes, (unsigned long long)n_roots);
 }
 
 __global__ void k_last_core(const int32_t *order, const int32_t *core, int n, int *out) {
@@ -501,6 +503,7 @@ struct RunPlan {
     } cls[kNumClasses];
     int ncls = 0;
     int merged_top = -1, merged_xcap = 0, merged_wp_min = 0;  // one-warp classes sharing one launch
+    bool level2 = false;  // one subtree per edge (Algorithm 4)
     unsigned trivial_blocks = 0;
     std::vector<void *> tmp;
     std::vector<cudaEvent_t> ev;  // [0] start, [1] end, then one pair per launch
@@ -546,8 +549,10 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     else if (opts.donate_policy < 0 || opts.donate_policy > 2) rc = fail(MCE_EINVAL, "bad opts.donate_policy");
     else if (opts.roots && opts.n_roots < 0) rc = fail(MCE_EINVAL, "opts.n_roots < 0");
     else if (opts.tuned && !g->tuned_valid) rc = fail(MCE_EINVAL, "opts.tuned set but mce_autotune has not run on this handle");
+    else if (opts.subtree_level < 0 || opts.subtree_level > 2) rc = fail(MCE_EINVAL, "bad opts.subtree_level");
     if (rc != MCE_OK) { delete P; return rc; }
     if (opts.timeout_ms <= 0) opts.timeout_ms = 60000;
+    P->level2 = opts.subtree_level == 2;
     const int G = g->G;
     P->G = G;
     P->HL = g->d + 2;  // every maximal clique has at most d + 1 vertices
@@ -714,6 +719,26 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         k.a.mail_flag = (int *)(k.a.idle_bits + idle_words);
         k.a.mail = (uint32_t *)(k.a.mail_flag + flag_words);
     }
+    for (int i = 0; i < P->ncls; i++) {
+        RunPlan::Cls &k = P->cls[i];
+        k.a.level2 = P->level2 ? 1 : 0;
+        k.a.eoff = nullptr;
+        k.a.n_tasks = k.a.n_roots;
+        if (!P->level2) continue;
+        // tasks are the roots' edges to later neighbours: eoff[i] = sum of |P0| before root i
+        int32_t *deg = (int32_t *)dalloc(g, ((size_t)k.a.n_roots + 1) * 4);
+        int32_t *eo = (int32_t *)dalloc(g, ((size_t)k.a.n_roots + 1) * 4);
+        int32_t *stmp = (int32_t *)dalloc(g, (size_t)scan_tmp_words((int64_t)k.a.n_roots + 1) * 4);
+        for (void *q : {(void *)deg, (void *)eo, (void *)stmp}) P->tmp.push_back(q);
+        if (!deg || !eo || !stmp) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+        CK(launch_gather_outdeg(k.a.roots, k.a.n_roots, g->outdeg, deg, g->stream));
+        CK(exclusive_scan(deg, eo, k.a.n_roots, stmp, g->stream));
+        int32_t tot = 0;
+        CK(cudaMemcpyAsync(&tot, eo + k.a.n_roots, 4, cudaMemcpyDeviceToHost, g->stream));
+        CK(cudaStreamSynchronize(g->stream));
+        k.a.eoff = eo;
+        k.a.n_tasks = tot;
+    }
     {
         const int nev = 2 + 2 * (P->ncls + (P->trivial_blocks ? 1 : 0));
         for (int i = 0; i < nev; i++) {
@@ -745,7 +770,7 @@ static int enqueue_run(mce_graph *g, RunPlan *P) {
     if (P->trivial_blocks) {
         CK(record(P->ev[e++], s, P->capturing));
         k_trivial_roots<<<P->trivial_blocks, 256, 0, s>>>(P->dg, P->dout, P->lists[kNumClasses],
-                                                          P->counts[kNumClasses]);
+                                                          P->counts[kNumClasses], P->level2 ? 1 : 0);
         count_launch();
         CK(cudaGetLastError());
         CK(record(P->ev[e++], s, P->capturing));

@@ -178,6 +178,9 @@ struct ClassArgs {
     int32_t donate_min_p;
     int32_t donate_policy;  // MCE_DONATE_*
     int32_t root_chunk;     // roots claimed per atomic
+    int32_t level2;         // 1: one task per edge (Algorithm 4), decoded through eoff
+    const int32_t *eoff;    // level2: [n_roots + 1] exclusive prefix of the roots' |P0|
+    int64_t n_tasks;        // roots, or edges when level2
     int32_t stats;          // 1: collect per-phase cycle counters
     uint64_t timeout_ns;
     // scratch (device), sized by the host for groups = blocks * warps_per_block / gw

@@ -792,6 +792,19 @@ cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const in
     return cudaGetLastError();
 }
 
+__global__ void k_gather_outdeg(const int32_t *roots, int64_t k, const int32_t *outdeg, int32_t *out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = outdeg[roots[i]];
+}
+
+cudaError_t launch_gather_outdeg(const int32_t *roots, int64_t k, const int32_t *outdeg, int32_t *out,
+                                 cudaStream_t s) {
+    if (k <= 0) return cudaSuccess;
+    k_gather_outdeg<<<grid_for(k, 256, 65536), 256, 0, s>>>(roots, k, outdeg, out);
+    count_launch();
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t *gid,
                            const int32_t *graph_ptr, int G, cudaStream_t s) {
     if (n == 0) return cudaSuccess;

@@ -30,6 +30,9 @@ cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s);
 cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &b, int sm_count,
                         uint64_t timeout_ns, cudaStream_t s);
 cudaError_t exclusive_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s);
+// out[i] = outdeg[roots[i]] for i < k
+cudaError_t launch_gather_outdeg(const int32_t *roots, int64_t k, const int32_t *outdeg, int32_t *out,
+                                 cudaStream_t s);
 int64_t scan_tmp_words(int64_t n);
 cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const int32_t *order,
                           const int32_t *rank, int32_t *outdeg, int32_t *indeg, int32_t *out_ptr,

@@ -27,11 +27,13 @@ cudaError_t plan_wp(int rows, int sm_count, int max_smem_optin, int requested_bl
     L->warps_per_block = gpb * GW;
     L->smem = smem_bytes(lay, gpb);
     L->a_global = AG;
-    auto kern = k_traverse<WP, GW, AG, false>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
-    if (e != cudaSuccess) return e;
-    e = cudaFuncSetAttribute(k_traverse<WP, GW, AG, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
-    if (e != cudaSuccess) return e;
+    auto kern = k_traverse<WP, GW, AG, false, false>;
+    for (auto variant : {k_traverse<WP, GW, AG, false, false>, k_traverse<WP, GW, AG, true, false>,
+                         k_traverse<WP, GW, AG, false, true>, k_traverse<WP, GW, AG, true, true>}) {
+        cudaError_t e = cudaFuncSetAttribute(variant, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
+        if (e != cudaSuccess) return e;
+    }
+    cudaError_t e = cudaSuccess;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, L->warps_per_block * 32, L->smem);
     if (e != cudaSuccess) return e;
@@ -47,12 +49,12 @@ cudaError_t launch_wp(const ClassLaunch &L, const DevGraph &g, const DevOut &o, 
                       int rows, cudaStream_t s) {
     constexpr int GW = group_warps(WP);
     constexpr bool AG = a_in_global(WP);
-    if (o.list)
-        k_traverse<WP, GW, AG, true><<<L.blocks, L.warps_per_block * 32, L.smem, s>>>(g, o, a, rows,
-                                                                                     stack_in_smem(WP) ? 1 : 0);
-    else
-        k_traverse<WP, GW, AG, false><<<L.blocks, L.warps_per_block * 32, L.smem, s>>>(g, o, a, rows,
-                                                                                      stack_in_smem(WP) ? 1 : 0);
+    const dim3 grid(L.blocks), block(L.warps_per_block * 32);
+    const int ss = stack_in_smem(WP) ? 1 : 0;
+    if (o.list && a.level2) k_traverse<WP, GW, AG, true, true><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
+    else if (o.list) k_traverse<WP, GW, AG, true, false><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
+    else if (a.level2) k_traverse<WP, GW, AG, false, true><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
+    else k_traverse<WP, GW, AG, false, false><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     return cudaGetLastError();
 }
 

@@ -22,7 +22,8 @@
 // index reaching it is then the argmax, so the pivot is the same as a full scan.
 //
 // Template parameters: WP padded words per row, GW warps per group, AG true
-// when A lives in the global arena, LIST true when cliques are listed.
+// when A lives in the global arena, LIST true when cliques are listed, L2
+// true when tasks are edges.
 #pragma once
 #include "mce_internal.cuh"
 
@@ -139,6 +140,9 @@ __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, 
     a.rid = a.xcomp + xcap;
     return a;
 }
+
+// Edge tasks (Algorithm 4) claimed per atomic.
+constexpr int kEdgeChunk = 16;
 
 __device__ __forceinline__ int find_in(const int32_t *a, int lo, int hi, int32_t key) {
     while (lo < hi) {
@@ -313,8 +317,9 @@ struct PhaseClock {
 };
 
 // LIST: the variant that also writes each clique's members (mce_run_list);
-// the counting variant carries none of that code.
-template <int WP, int GW, bool AG, bool LIST>
+// L2: the variant whose tasks are edges (Algorithm 4). The plain counting
+// variant carries none of that code.
+template <int WP, int GW, bool AG, bool LIST, bool L2>
 __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArgs C, int rows_cap, int stack_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int GT = 32 * GW;
@@ -393,14 +398,49 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
         if (!block_hist)
             for (int i = g.gl; i < rows_cap + 2; i += GT) hist[i] = 0;
         g.sync();
+        int cached_r = -1, cached_nx = 0;  // level 2: the root whose P0, A and X rows are loaded
+        int ch_i = 0, ch_j = 0, ch_left = 0;  // level 2, thread 0: the claimed run of edges
         for (;;) {
             // --------------------------------------------------- get a task
             if (g.gl == 0) {
-                int r = -1, mail = 0;
-                int idx = atomicAdd(&C.ctl[CTL_NEXT_ROOT], 1);
-                if (idx < C.n_roots) {
-                    r = C.roots[idx];
-                } else if (C.worker_list) {
+                int r = -1, mail = 0, ej = -1;
+                bool have = false;
+                if (L2) {
+                    // edges are claimed kEdgeChunk at a time, consecutive edges of a
+                    // root staying with one group so that its A is built once
+                    if (ch_left == 0) {
+                        const int idx = atomicAdd(&C.ctl[CTL_NEXT_ROOT], kEdgeChunk);
+                        if (idx < C.n_tasks) {
+                            // root i is the last with eoff[i] <= idx
+                            int lo = 0, hi = C.n_roots - 1;
+                            while (lo < hi) {
+                                const int mid = (lo + hi + 1) >> 1;
+                                if (C.eoff[mid] <= idx) lo = mid;
+                                else hi = mid - 1;
+                            }
+                            ch_i = lo;
+                            ch_j = idx - C.eoff[lo];
+                            ch_left = (int)min((int64_t)kEdgeChunk, C.n_tasks - idx);
+                        }
+                    }
+                    if (ch_left > 0) {
+                        r = C.roots[ch_i];
+                        ej = ch_j;
+                        have = true;
+                        ch_left--;
+                        if (++ch_j == C.eoff[ch_i + 1] - C.eoff[ch_i]) {
+                            ch_i++;
+                            ch_j = 0;
+                        }
+                    }
+                } else {
+                    const int idx = atomicAdd(&C.ctl[CTL_NEXT_ROOT], 1);
+                    if (idx < C.n_tasks) {
+                        r = C.roots[idx];
+                        have = true;
+                    }
+                }
+                if (!have && C.worker_list) {
                     // join the worker list and wait for a donated subtree (Sec. III-C)
                     pc.start();
                     atomicOr(&C.idle_bits[gg >> 5], 1u << (gg & 31));
@@ -433,10 +473,12 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 }
                 misc[0] = r;
                 misc[1] = mail;
+                misc[5] = ej;
             }
             g.sync();
             const int r = misc[0];
             const bool have_mail = misc[1] != 0;
+            const int ej = misc[5];  // level 2: the edge's later end, as a local index of P0
             g.sync();
             if (r < 0) break;
 
@@ -465,11 +507,18 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             // over the index space, [36..68) its local indices, [68] P, [69] X_P,
             // [70..72) the hash sum of R; its X_X rows are in the arena's xcomp.
             const uint32_t *mb = C.mail + (size_t)gg * C.mail_words;
-            const int l0 = have_mail ? (int)mb[1] : 0;
+            const bool edge = L2 && !have_mail;  // a task of one edge {r, P0[ej]}
+            const int l0 = have_mail ? (int)mb[1] : (edge ? 1 : 0);
             const bool cmail = GW == 1 && have_mail && mb[3] != 0u;
-            for (int i = g.gl; i < n0; i += GT) p0[i] = prow[i];
+            // consecutive edge tasks of one root reuse its P0, A and X rows (an
+            // edge task changes none of them; a received subtree does)
+            const bool reuse = edge && r == cached_r;
+            if (!reuse)
+                for (int i = g.gl; i < n0; i += GT) p0[i] = prow[i];
             int nx = 0;
-            if (have_mail) {
+            if (reuse) {
+                nx = cached_nx;
+            } else if (have_mail) {
                 // the donor wrote the A rows of P' u X_P' into the arena's A region
                 // and the surviving X_X rows into the arena's X rows: nothing to
                 // rebuild. Every row the subtree reads (candidates, branches) is
@@ -592,6 +641,12 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     base_slot += tot;
                 }
                 nx = base_slot;
+            }
+            if (edge) {
+                cached_r = r;
+                cached_nx = nx;
+            } else {
+                cached_r = -1;
             }
             __threadfence_block();
             g.sync();
@@ -743,7 +798,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             // (xcomp). Entered from a wide descent, at a root with |P0| <= 32, or
             // from a donated compact subtree; when the subtree is done the wide
             // loop backtracks as from any child.
-            bool kstart = GW == 1 && !have_mail && n0 <= 32;  // the root itself
+            bool kstart = GW == 1 && !have_mail && !L2 && n0 <= 32;  // the root itself
             bool kmode = false, kcentr = false, kpend = false;
             // In compact mode the node's P, X_P, branch set, X_X end and hash sum
             // reuse the wide registers: the wide node is on the stack meanwhile.
@@ -752,6 +807,30 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             uint64_t &kS = S;
             uint32_t kRow = 0u;
             int kL = 0, kd = 0, kbase = 0;
+            if (edge) {
+                // Algorithm 4: R = {r, v_j}; P = the common neighbours after v_j,
+                // X = those before it: X_P from P0, X_X = the rows holding j
+                const int j = ej, jw = j >> 5;
+                const uint32_t jb = 1u << (j & 31);
+                const uint32_t aj = own ? Arow[(size_t)j * WP + g.gl] : 0u;
+                const uint32_t above = g.gl > jw ? 0xffffffffu : (g.gl == jw ? ~((jb << 1) - 1u) : 0u);
+                p = aj & above;
+                xp = aj & ~above;
+                if (lpx > 0) lpx = partition(lpx, [&](uint32_t e) { return (xrows[(size_t)e * WP + jw] & jb) != 0u; });
+                S += G.mixid[p0[j]];
+                if (g.gl == 0) stk[Lvl<WP>::VSEL] = (uint32_t)j;  // level 0's branch, for donated paths
+                if (listing && g.gl == 0) rid[1] = (uint32_t)G.order[p0[j]];
+                const int np_e = grp_sum(g, red, __popc(p));
+                if (np_e == 0) {
+                    // a leaf: {r, v_j} is maximal iff X is empty
+                    t_nodes++;
+                    if (!grp_or(g, red, xp != 0u) && lpx == 0 && g.gl == 0) record(2, S, 0, 0, 0, 0);
+                    b = 0u;
+                    enter = false;
+                } else if (GW == 1 && np_e + grp_sum(g, red, __popc(xp)) <= 32) {
+                    kstart = true;
+                }
+            }
             if (cmail) {
                 kRow = mb[4 + g.lane];
                 kL = (int)mb[36 + g.lane];

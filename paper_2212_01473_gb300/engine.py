@@ -47,7 +47,7 @@ class mce_opts(ctypes.Structure):
                 ("timeout_ms", ctypes.c_int64), ("root_count", ctypes.c_void_p),
                 ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
                 ("root_priority", ctypes.c_void_p), ("roots", ctypes.c_void_p),
-                ("n_roots", ctypes.c_int64), ("tuned", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("n_roots", ctypes.c_int64), ("tuned", ctypes.c_int32), ("subtree_level", ctypes.c_int32)]
 
 
 class mce_result(ctypes.Structure):

@@ -131,6 +131,47 @@ def test_deep_balanced_tree_split(blocks, donate, pivot):
         assert r.donations > 0
 
 
+def check_level2(g, pivot, **opts):
+    o = oracle.mce(g.row_ptr, g.col, mode=ORACLE_MODE[pivot], per_root=True, level=2)
+    r, (rc, rh, rn) = run(g, per_root=True, pivot=pivot, subtree_level=2, **opts)
+    same(r, o)
+    assert np.array_equal(rc, o.root_count)
+    assert np.array_equal(rh, o.root_hash)
+    assert np.array_equal(rn, o.root_nodes)
+    assert r.tree_nodes == int(o.root_nodes.sum())
+    return r
+
+
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
+@pytest.mark.parametrize("make", [lambda: gen.complete(12), lambda: gen.worked_example(),
+                                  lambda: gen.disjoint_union([gen.gnp(300, 0.05, 11), gen.empty(4), gen.complete(40)]),
+                                  lambda: gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5),
+                                  lambda: gen.moon_moser(8)])
+def test_second_level_subtrees(make, pivot):
+    # one subtree per edge (Algorithm 4): results as always, tree nodes per
+    # root (summed over its edges) as the oracle's second-level walk
+    check_level2(make(), pivot)
+
+
+@pytest.mark.parametrize("pivot", PIVOTS, ids=["IP", "IPX"])
+@pytest.mark.parametrize("blocks,donate", [(1, 1), (3, 2), (8, 10)])
+def test_second_level_under_donations(blocks, donate, pivot):
+    g = gen.disjoint_union([gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5), gen.moon_moser(9)])
+    check_level2(g, pivot, blocks=blocks, donate_min_p=donate)
+
+
+def test_second_level_listing():
+    g = gen.disjoint_union([gen.gnp(250, 0.06, 5), gen.empty(2), gen.moon_moser(5)])
+    o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP)
+    cl = mce.list_maximal_cliques(g.row_ptr, g.col, subtree_level=2)
+    assert len(cl) == o.count
+    assert len({tuple(sorted(c.tolist())) for c in cl}) == o.count
+    tot = 0
+    for c in cl:
+        tot = (tot + h_clique([int(x) for x in c])) & M64
+    assert tot == o.hash
+
+
 def test_worker_list_donates():
     g = gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5)
     r = run(g, blocks=2, donate_min_p=1)
