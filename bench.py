@@ -136,7 +136,7 @@ def cpu_baseline(g, frac, seed=12345):
     t0 = time.perf_counter()
     r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=threads, roots=roots)
     dt = time.perf_counter() - t0
-    return {"value": r.count / dt, "unit": "cliques/s", "cores": threads, "kind": "oracle",
+    return {"value": r.count / dt, "unit": "cliques/s", "cores": threads, "kind": "oracle", "seconds": dt,
             "sample": "%d of %d roots (%.1f%%, seed %d), %d cliques in %.2f s incl. validation, "
                       "peel and relabelling" % (k, g.n, 100.0 * frac, seed, r.count, dt)}
 
@@ -148,17 +148,18 @@ def run_reference(args):
     import gen
     g = gen.workload(args.workload)
     frac = args.cpu_sample
-    vals = []
+    vals, secs = [], []
     info = None
     for it in range(args.warmup + args.steps):
         b = cpu_baseline(g, frac)
         if it >= args.warmup:
             vals.append(b["value"])
+            secs.append(b["seconds"])
             info = b
     value = statistics.mean(vals)
     line = {"impl": "reference", "metric": "maximal cliques/sec", "value": value, "unit": "cliques/s",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": None, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "ms_per_step": 1e3 * statistics.mean(secs), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
             "config": {"workload": args.workload, "step": "CPU oracle on a seeded %.0f%% sample of roots" % (100 * frac)},
             "cpu_baseline": {"kind": "oracle", "cores": info["cores"], "sample": info["sample"], "value": value,
