@@ -1305,138 +1305,6 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     pc.stop(PH_LEAF);
                     continue;
                 }
-                if (pcnt == 1) {
-                    // The child's P' is one vertex u: its subtree is resolved here
-                    // without a descent, node for node as Algorithm 2 would walk it.
-                    // The child's pivot scores are 1 for an excluded candidate
-                    // adjacent to u and 0 for everything else (u itself included).
-                    // With a score-1 pivot the branch set P' - N(pivot) is empty;
-                    // otherwise it is {u}, whose child has P'' = X_P'' = {} and is
-                    // a leaf, maximal iff no excluded row of X_X' contains u.
-                    t_nodes++;
-                    const int u = (int)grp_max(g, red, cp ? (unsigned)(g.gl * 32 + __ffs(cp)) : 0u) - 1;
-                    const int uw = u >> 5;
-                    const uint32_t ub = 1u << (u & 31);
-                    const uint32_t au = own ? Arow[(size_t)u * WP + g.gl] : 0u;
-                    // some vertex of X_P' = X_P n N(v) adjacent to u
-                    if (!grp_or(g, red, (cx & au) != 0u)) {
-                        // some row of X_X' = the prefix rows holding v, that also holds u
-                        int found = 0, it = 0;
-                        for (; it < lpx && !found; it += GT) {
-                            const int idx = it + g.gl;
-                            int hit = 0;
-                            if (idx < lpx) {
-                                const uint32_t *xr = xrows + (size_t)xidx[idx] * WP;
-                                hit = (xr[vw] & vb) != 0u && (xr[uw] & ub) != 0u;
-                            }
-                            found = grp_or(g, red, hit);
-                        }
-                        pc.count(PH_LEAF, (unsigned long long)min(it, lpx));
-                        // IP scores P' u X_P' only: the leaf exists and X_X' decides
-                        // maximality. IPX also scores X_X': an adjacent row there is
-                        // a score-1 pivot and the leaf does not exist.
-                        if (!found || !C.pivot_ipx) t_nodes++;
-                        if (!found && g.gl == 0)
-                            record(l + 3, S + G.mixid[p0[v]] + G.mixid[p0[u]], 2, listing ? G.order[p0[v]] : 0,
-                                   listing ? G.order[p0[u]] : 0, 0);
-                    }
-                    pc.stop(PH_LEAF);
-                    continue;
-                }
-                if (pcnt == 2) {
-                    // The child's P' is two vertices u1 < u2: its subtree is again
-                    // resolved here. An excluded candidate x scores a(x) = the number
-                    // of u1, u2 it is adjacent to; u1 and u2 score 1 if adjacent to
-                    // each other, else 0. Candidates compare by score, then IPX's X_X
-                    // rows by rank, then local index (Algorithm 2, ties to rank).
-                    //  * u1 ~ u2: a score-2 pivot leaves no branch. Otherwise one
-                    //    branch b in {u1, u2}, whose child has P = {the other} and no
-                    //    excluded vertex adjacent to both, so it has one leaf child:
-                    //    3 nodes, clique R u {v, u1, u2} unless an X_X' row has both.
-                    //  * u1 !~ u2: a score-2 pivot leaves no branch; else the first
-                    //    score-1 candidate, adjacent to u_i only, leaves the single
-                    //    branch u_j (a leaf); else both branches are leaves.
-                    t_nodes++;
-                    const int u1 = (int)~grp_max(g, red, cp ? ~(unsigned)(g.gl * 32 + __ffs(cp) - 1) : 0u);
-                    const int u2 = (int)grp_max(g, red, cp ? (unsigned)(g.gl * 32 + 32 - __clz(cp)) : 0u) - 1;
-                    const int u1w = u1 >> 5, u2w = u2 >> 5;
-                    const uint32_t u1b = 1u << (u1 & 31), u2b = 1u << (u2 & 31);
-                    const uint32_t a1 = own ? Arow[(size_t)u1 * WP + g.gl] : 0u;
-                    const uint32_t a2 = own ? Arow[(size_t)u2 * WP + g.gl] : 0u;
-                    const bool e12 = grp_or(g, red, g.gl == u2w && (a1 & u2b) != 0u);
-                    // X_P' = cx: adjacent to both, to exactly one, to u1, to u2
-                    const bool s2p = grp_or(g, red, (cx & a1 & a2) != 0u);
-                    const uint32_t one = cx & (a1 ^ a2);
-                    // X_X' = prefix rows holding v
-                    bool s2x = false, x1 = false, x2 = false;
-                    unsigned firstx = 0u;  // IPX: lowest-rank X_X' row adjacent to exactly one
-                    int it = 0;
-                    for (; it < lpx; it += GT) {
-                        const int idx = it + g.gl;
-                        bool h1 = false, h2 = false;
-                        unsigned key = 0u;
-                        if (idx < lpx) {
-                            const uint32_t e = xidx[idx];
-                            const uint32_t *xr = xrows + (size_t)e * WP;
-                            if (xr[vw] & vb) {
-                                h1 = (xr[u1w] & u1b) != 0u;
-                                h2 = (xr[u2w] & u2b) != 0u;
-                                if (C.pivot_ipx && h1 != h2)
-                                    key = ((0x7fffffffu - xrank[e]) << 1) | (h1 ? 1u : 0u);
-                            }
-                        }
-                        s2x |= grp_or(g, red, h1 && h2) != 0;
-                        x1 |= grp_or(g, red, h1) != 0;
-                        x2 |= grp_or(g, red, h2) != 0;
-                        if (C.pivot_ipx) firstx = max(firstx, grp_max(g, red, key));
-                    }
-                    pc.count(PH_LEAF, (unsigned long long)lpx);
-                    const bool s2 = s2p || (C.pivot_ipx && s2x);
-                    // at most two cliques: R u {v, u1, u2}, R u {v, u_j}, or both R u {v, u1}
-                    // and R u {v, u2}
-                    const uint64_t mv = G.mixid[p0[v]];
-                    const bool lead = g.gl == 0;
-                    auto id_of = [&](int x) -> int32_t { return listing ? G.order[p0[x]] : 0; };
-                    if (e12) {
-                        if (!s2) {
-                            t_nodes += 2;
-                            if (!s2x && lead)
-                                record(l + 4, S + mv + G.mixid[p0[u1]] + G.mixid[p0[u2]], 3, id_of(v), id_of(u1),
-                                       id_of(u2));
-                        }
-                    } else if (!s2) {
-                        // the first score-1 candidate: X_X' rows first (IPX), then X_P'
-                        int touch = 0;  // 1: adjacent to u1 only, 2: to u2 only, 0: none
-                        if (firstx) {
-                            touch = (firstx & 1u) ? 1 : 2;
-                        } else {
-                            const unsigned okey = one ? ~(unsigned)(g.gl * 32 + __ffs(one) - 1) : 0u;
-                            const unsigned ox = grp_max(g, red, okey);
-                            if (ox) {
-                                const int xs = (int)~ox;
-                                const bool to1 = grp_or(g, red, g.gl == (xs >> 5) && (a1 >> (xs & 31)) & 1u);
-                                touch = to1 ? 1 : 2;
-                            }
-                        }
-                        if (touch) {
-                            // one leaf R u {v, u_j}, u_j the vertex the pivot misses
-                            t_nodes++;
-                            const int uj = touch == 1 ? u2 : u1;
-                            const uint32_t aj = touch == 1 ? a2 : a1;
-                            const bool xj = touch == 1 ? x2 : x1;
-                            if (!xj && !grp_or(g, red, (cx & aj) != 0u) && lead)
-                                record(l + 3, S + mv + G.mixid[p0[uj]], 2, id_of(v), id_of(uj), 0);
-                        } else {
-                            // no candidate is adjacent to u1 or u2: two leaves, and only
-                            // the X_X' rows (not candidates under IP) can block them
-                            t_nodes += 2;
-                            if (!x1 && lead) record(l + 3, S + mv + G.mixid[p0[u1]], 2, id_of(v), id_of(u1), 0);
-                            if (!x2 && lead) record(l + 3, S + mv + G.mixid[p0[u2]], 2, id_of(v), id_of(u2), 0);
-                        }
-                    }
-                    pc.stop(PH_LEAF);
-                    continue;
-                }
                 const int others_here = grp_or(g, red, b != 0u);
                 // ------------------------------ donation (Sec. III-C)
                 const bool may_donate = C.donate_policy == MCE_DONATE_ANY ||
