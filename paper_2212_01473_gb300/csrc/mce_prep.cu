@@ -640,9 +640,11 @@ __global__ void k_class_flags(int n, const int32_t *outdeg, int c, int32_t *flag
     }
 }
 
-__global__ void k_scatter_flagged(int n, const int32_t *flags, const int32_t *pos, int32_t *out) {
+// the flagged ranks in descending order (pos[n] = their number)
+__global__ void k_scatter_flagged_desc(int n, const int32_t *flags, const int32_t *pos, int32_t *out) {
+    const int32_t total = pos[n];
     for (int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-        if (flags[r]) out[pos[r]] = (int32_t)r;
+        if (flags[r]) out[total - 1 - pos[r]] = (int32_t)r;
 }
 
 __global__ void k_mark_roots(const int32_t *ids, int64_t k, const int32_t *rank, int n, int32_t *mask,
@@ -862,7 +864,9 @@ cudaError_t launch_class_list(int n, const int32_t *outdeg, int c, int32_t *flag
     count_launch();
     cudaError_t e = exclusive_scan(flags, pos, n, scan_tmp, s);
     if (e != cudaSuccess) return e;
-    k_scatter_flagged<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, flags, pos, out);
+    // Descending rank: later vertices of the degeneracy order sit in denser
+    // cores and tend to carry the heavier subtrees, so they start first.
+    k_scatter_flagged_desc<<<grid_for(n, 256, 65536), 256, 0, s>>>(n, flags, pos, out);
     count_launch();
     return cudaGetLastError();
 }
