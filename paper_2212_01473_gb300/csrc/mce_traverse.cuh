@@ -13,13 +13,22 @@
 //   X_P  = excluded vertices that came from P0: one bitset per level.
 // A node is (P, X_P, X_X prefix). Pivot: u in P u X_P maximising
 // |P n N(u)| (Sec. III-E restricts the pivot to X_P u P for partial induced
-// subgraphs), ties to the smallest local index = smallest rank. Branches:
-// P - N(u) in ascending rank. R is maximal when P, X_P and X_X are all empty.
+// subgraphs; with IPX, Sec. IV-D, X_X rows are candidates too), ties to the
+// smallest rank. Branches: P - N(u) in ascending rank. R is maximal when P,
+// X_P and X_X are all empty.
 //
 // The pivot scan visits candidates in ascending index, 32*GW at a time, and
 // stops after the first chunk whose best score equals the largest score any
 // candidate can have (|P| if X_P is non-empty, else |P| - 1): the smallest
 // index reaching it is then the argmax, so the pivot is the same as a full scan.
+//
+// Two walks share the kernel. The wide walk above keeps a node's sets one word
+// per thread over P0. Once a node has |P| + |X_P| <= 32 (and at roots with
+// |P0| <= 32) its whole subtree runs in compact mode: one-word sets over that
+// node's P u X_P, with one- and two-vertex children resolved in closed form.
+// Both walk Algorithm 2's tree node for node, so tree-node counts, cliques and
+// hashes do not depend on where the switch happens. Idle groups take subtrees
+// of either kind from busy ones (the worker list, Sec. III-C).
 //
 // Template parameters: WP padded words per row, GW warps per group, AG true
 // when A lives in the global arena, LIST true when cliques are listed, L2
