@@ -110,6 +110,21 @@ def traversal_source_hash():
     return h.hexdigest()
 
 
+def replica_throughput(count, steps, total_ms, dist=None, device="cpu"):
+    """Whole-job rate of N independent replicas (the path does not shard: each
+    rank enumerates the same graph). Every rank ran `steps` steps of `count`
+    cliques; the job lasts as long as its slowest rank. Returns (cliques/s
+    over all ranks, the slowest rank's total ms)."""
+    world = 1
+    if dist is not None:
+        import torch
+        world = dist.get_world_size()
+        t = torch.tensor([float(total_ms)], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    return count * steps * world / (total_ms / 1e3), total_ms
+
+
 def load_golden(name):
     p = os.path.join(ROOT, "tests", "golden", name + ".json")
     if os.path.exists(p):
@@ -319,14 +334,9 @@ def run_ours(args):
     torch.cuda.synchronize()
     barrier()
     clk = clocks.stop()
-    total_ms = sum(ms)
-    if dist is not None:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
     count = results[-1].count
     assert all(r.count == count and r.hash == results[-1].hash for r in results)
-    value = count * args.steps * world / (total_ms / 1e3)
+    value, total_ms = replica_throughput(count, args.steps, sum(ms), dist, "cuda")
 
     st = stats[-1]
 
