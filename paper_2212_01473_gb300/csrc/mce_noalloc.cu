@@ -79,6 +79,7 @@ extern "C" int mce_peel_noalloc(const int32_t *row_ptr, const int32_t *col, int3
     q += kNoAllocMaxN / 32 + 32;
     pb.blocksums = (int *)q;
     q += kNoAllocMaxBlocks;
+    static_assert(sizeof(PeelCtl) <= 64 * sizeof(uint32_t), "PeelCtl outgrew its scratch slot");
     pb.ctl = (PeelCtl *)q;
     q += 64;
     pb.status = (int *)q;

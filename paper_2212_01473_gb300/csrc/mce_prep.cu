@@ -152,8 +152,10 @@ __device__ void block_bitonic(int *a, int len) {
 // = k) and appended to the next sub-round's segment of `order` by the thread
 // whose decrement took its degree from k + 1 to k, so nothing needs a second
 // pass. Decrements are unconditional: a removed vertex already has degree
-// <= k and never reaches k + 1 again. The three sub-round counters form a
-// ring, so the one that is reset is never the one being read or filled.
+// <= k and never reaches k + 1 again. The three counters of S sizes form a
+// ring that every pass and sub-round advances: a phase fills one slot while
+// the size filled by the phase before is still being read, and resets the
+// third, whose readers all passed the last barrier.
 // Segments longer than kSmallSort are put in id order here through a bitmap;
 // shorter ones, and all final ranks, are done by k_peel_rank afterwards.
 //
@@ -200,20 +202,48 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     if (!barrier()) return;
 
     // every block keeps the same copies of these
-    int k = 0, next = 0, nrem = n, t = 0, L = 0;
+    // t counts sub-rounds (segments of `order`), r every pass and sub-round,
+    // L every level-start pass
+    int k = 0, next = 0, nrem = n, t = 0, r = 0, L = 0;
     bool remsel = false;
+    // A level start is one pass and one barrier. The pass builds S for a
+    // guessed k while it reduces the smallest live degree and the live degree
+    // sum. After a level at k every live degree is above k, so the guess k + 1
+    // is right whenever a live vertex has degree k + 1. Otherwise S comes out
+    // empty, the pass has only compacted the remaining list, and the next pass
+    // takes the reduced minimum. The first level guesses 0.
+    int guess = 0;
     while (next < n) {
         const int32_t *rem = remsel ? remB : remA;
         int32_t *rem2 = remsel ? remA : remB;
-        // level start: smallest live degree and the live degree sum
+        const int ls = L % 3;  // this level's slot of nrem2, minval and sumdeg
         int lmin = INT_MAX;
         long long lsum = 0;
-        for (int64_t i = tid; i < nrem; i += nth) {
-            const int v = rem[i];
-            if (rank[v] < 0) {
-                const int d = deg[v];
-                lmin = min(lmin, d);
-                lsum += d;
+        {
+            // S of the level into order[next..), the rest into the next remaining list
+            int *cnt = &ctl->cnt[r % 3];
+            const int64_t lim = (nrem + 31) / 32 * 32;
+            for (int64_t i = tid; i < lim; i += nth) {
+                bool live = false, inS = false;
+                int v = 0;
+                if (i < nrem) {
+                    v = rem[i];
+                    live = rank[v] < 0;
+                    if (live) {
+                        const int d = deg[v];
+                        lmin = min(lmin, d);
+                        lsum += d;
+                        inS = d <= guess;
+                    }
+                }
+                const int ps = warp_push(cnt, inS);
+                if (inS) {
+                    rank[v] = 0;
+                    core[v] = guess;
+                    order[next + ps] = v;
+                }
+                const int pk = warp_push(&ctl->nrem2[ls], live && !inS);
+                if (live && !inS) rem2[pk] = v;
             }
         }
         lmin = block_reduce_min<kPeelThreads>(lmin, sh);
@@ -223,18 +253,33 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         if (threadIdx.x == 0) {
             long long bs = 0;
             for (int w = 0; w < kPeelThreads / 32; w++) bs += shl[w];
-            if (lmin != INT_MAX) atomicMin(&ctl->minval[L & 1], lmin);
-            if (bs) atomicAdd(&ctl->sumdeg[L & 1], (unsigned long long)bs);
-            // read by every block before the previous level's second barrier
+            if (lmin != INT_MAX) atomicMin(&ctl->minval[ls], lmin);
+            if (bs) atomicAdd(&ctl->sumdeg[ls], (unsigned long long)bs);
+            // slot (L + 1) % 3 was last read after level L - 2's barrier, and
+            // every block has since passed level L - 1's
             if (bid == 0) {
-                ctl->minval[(L + 1) & 1] = INT_MAX;
-                ctl->sumdeg[(L + 1) & 1] = 0ull;
+                const int lz = (L + 1) % 3;
+                ctl->minval[lz] = INT_MAX;
+                ctl->sumdeg[lz] = 0ull;
+                ctl->nrem2[lz] = 0;
+                ctl->cnt[(r + 1) % 3] = 0;
             }
         }
         if (!barrier()) return;
-        k = max(k, vload(&ctl->minval[L & 1]));
+        nrem = vload(&ctl->nrem2[ls]);
+        remsel = !remsel;
+        L++;
+        int ns = vload(&ctl->cnt[r % 3]);
+        r++;
+        if (ns == 0) {
+            // no live vertex has degree `guess`: the level is at the smallest live degree
+            guess = vload(&ctl->minval[ls]);
+            continue;
+        }
+        k = guess;
+        guess = k + 1;
         // every block reads the same sum after the barrier and decides alike
-        const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[L & 1];
+        const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[ls];
         if (!solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && live > kSoloDegrees) {
             if (blockIdx.x >= kNarrowBlocks) return;
             nbar = kNarrowBlocks;
@@ -254,43 +299,13 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             nblocks = 1;
             bid = 0;
         }
-        {
-            // S of the level into order[next..), the rest into the next remaining list
-            int *cnt = &ctl->cnt[t % 3];
-            const int64_t lim = (nrem + 31) / 32 * 32;
-            for (int64_t i = tid; i < lim; i += nth) {
-                bool live = false, inS = false;
-                int v = 0;
-                if (i < nrem) {
-                    v = rem[i];
-                    live = rank[v] < 0;
-                    inS = live && deg[v] <= k;
-                }
-                const int ps = warp_push(cnt, inS);
-                if (inS) {
-                    rank[v] = 0;
-                    core[v] = k;
-                    order[next + ps] = v;
-                }
-                const int pk = warp_push(&ctl->nrem2[L & 1], live && !inS);
-                if (live && !inS) rem2[pk] = v;
-            }
-            // read by every block before this level's first barrier
-            if (bid == 0 && threadIdx.x == 0) ctl->nrem2[(L + 1) & 1] = 0;
-        }
-        if (!barrier()) return;
-        nrem = vload(&ctl->nrem2[L & 1]);
-        remsel = !remsel;
-        L++;
 
         // sub-rounds at level k
         for (;;) {
-            const int ns = vload(&ctl->cnt[t % 3]);
-            if (ns == 0) break;
             if (bid == 0 && threadIdx.x == 0) {
-                // cnt[(t+2)%3] held the previous sub-round's size, read by every block
+                // cnt[(r+1)%3] held the size read two phases ago, by every block
                 // before the last barrier
-                ctl->cnt[(t + 2) % 3] = 0;
+                ctl->cnt[(r + 1) % 3] = 0;
                 segstart[t] = next;
             }
             int32_t *S = order + next;
@@ -331,7 +346,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             // remove S: the vertices whose degree falls to k form the next sub-round.
             // A vertex of degree <= kHeavyDeg is one warp's work (two 32-edge
             // chunks in flight); a longer adjacency list is strided over a block.
-            int *cn = &ctl->cnt[(t + 1) % 3];
+            int *cn = &ctl->cnt[r % 3];
             int32_t *S2 = S + ns;
             auto remove_edge = [&](bool valid, int j) {
                 bool push = false;
@@ -382,6 +397,9 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             if (!barrier()) return;
             next += ns;
             t++;
+            ns = vload(&ctl->cnt[r % 3]);
+            r++;
+            if (ns == 0) break;
         }
     }
     if (bid == 0 && threadIdx.x == 0) {
@@ -751,7 +769,7 @@ __global__ void k_peel_init(PeelCtl *ctl, int n) {
     ctl->next = 0;
     ctl->rounds = 0;
     for (int i = 0; i < 3; i++) ctl->cnt[i] = 0;
-    for (int i = 0; i < 2; i++) {
+    for (int i = 0; i < 3; i++) {
         ctl->nrem2[i] = 0;
         ctl->minval[i] = INT_MAX;
         ctl->sumdeg[i] = 0ull;

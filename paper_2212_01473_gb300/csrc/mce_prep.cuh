@@ -7,9 +7,9 @@ namespace mce {
 struct PeelCtl {
     int k, next, rounds;  // written at the end of the peel
     int cnt[3];           // sub-round sizes, a ring indexed by sub-round % 3
-    int nrem2[2];         // next remaining-list size, by level parity
-    int minval[2];        // smallest live degree at a level start, by level parity
-    unsigned long long sumdeg[2];  // live degree sum at a level start, by level parity
+    int nrem2[3];         // next remaining-list size, a ring indexed by level % 3
+    int minval[3];        // smallest live degree at a level start, by level % 3
+    unsigned long long sumdeg[3];  // live degree sum at a level start, by level % 3
     GridBar bar;
 };
 
