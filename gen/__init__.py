@@ -255,3 +255,13 @@ def stats(g: Graph) -> dict:
     deg = g.degrees()
     return {"n": g.n, "m": g.m, "max_deg": int(deg.max()) if g.n else 0,
             "isolated": int((deg == 0).sum()), "mean_deg": float(deg.mean()) if g.n else 0.0}
+
+
+def peel_stages(seed: int = 21) -> Graph:
+    """G(n, m) with n = 300,000 and m = 2.2M, plus K_60, K_120 and K_181.
+
+    The live degree sum falls from 4.45M through 50,400 to 32,580 as the
+    peel goes. The smallest live degree jumps past k + 1 four times: at the
+    first level, and at each clique.
+    """
+    return disjoint_union([er(300000, 2200000, seed), complete(60), complete(120), complete(181)])

@@ -87,7 +87,8 @@ def test_chunglu_small_per_root(pivot):
 
 @pytest.mark.parametrize("maker", [lambda: gen.workload("er_2000"), lambda: gen.gnp(3000, 0.01, 3),
                                    lambda: gen.moon_moser(8), lambda: gen.random_forest(500, 2),
-                                   lambda: gen.chung_lu(20000, 8.0, 2.1, 500.0, 5, 8, 16, 11)])
+                                   lambda: gen.chung_lu(20000, 8.0, 2.1, 500.0, 5, 8, 16, 11),
+                                   lambda: gen.peel_stages()])
 def test_peel_matches_oracle(maker):
     g = maker()
     core_o, rank_o, order_o, _ = oracle.peel(g.row_ptr, g.col)

@@ -394,3 +394,23 @@ def test_multipartite_enumeration(k, size, first):
     r = oracle.mce(shifted.row_ptr, shifted.col, roots=np.arange(first, first + g.n, dtype=np.int32))
     c, h = oracle.multipartite(first, k, size)
     assert c == size ** k == r.count and h == r.hash
+
+
+def test_peel_stages_graph_spans_every_stage():
+    # The GPU peel runs on the full grid while the live degree sum at a level
+    # start is above 2^22, on 16 blocks down to 32,768, then on one block. A
+    # level start guesses k + 1 and makes one more pass when no live vertex
+    # has that degree. gen.peel_stages() must reach all three stages and make
+    # that extra pass in each: the live degree sum at level k is twice the
+    # number of edges whose ends both have core number >= k.
+    g = gen.peel_stages()
+    core, rank, order, rounds = oracle.peel(g.row_ptr, g.col)
+    src = np.repeat(np.arange(g.n), g.degrees())
+    lo = np.minimum(core[src], core[g.col])
+    ks = np.unique(core)
+    live = np.array([(lo >= k).sum() for k in ks])
+    stage = np.where(live > (1 << 22), 0, np.where(live > 32768, 1, 2))
+    jump = np.concatenate([[ks[0] > 0], np.diff(ks) > 1])
+    assert set(stage.tolist()) == {0, 1, 2}
+    assert {int(s) for s in stage[jump]} == {0, 1, 2}
+    assert ks.tolist()[-3:] == [59, 119, 180] and int(g.degrees().min()) > 0

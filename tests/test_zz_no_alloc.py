@@ -55,6 +55,13 @@ def test_noalloc_peel_equals_allocating_path_on_consecutive_calls():
             assert np.array_equal(a, b)
 
 
+def test_noalloc_peel_across_every_peel_stage():
+    # full grid, 16 blocks and one block, with a k jump in each stage
+    g = gen.peel_stages()
+    for a, b in zip(noalloc_order(g), reference_order(g)):
+        assert np.array_equal(a, b)
+
+
 def test_noalloc_peel_rejects_graphs_beyond_its_capacity():
     lib = mce.library()
     n = (1 << 20) + 1
