@@ -5,7 +5,7 @@ feature), standardised by (x - mean) / std; 16 -> 64 (ReLU) -> 64 (ReLU) -> 1;
 every weight rounded to bfloat16 (round to nearest, ties to even) before use;
 biases unrounded. Loss: mean squared error; gradients with respect to the
 unrounded weights (the rounding passes gradients straight through).
-Everything here is float64 so that it can judge the GPU's float32 arithmetic.
+Everything here is float64 so that it can check the GPU's float32 arithmetic.
 """
 import numpy as np
 
