@@ -258,10 +258,10 @@ def stats(g: Graph) -> dict:
 
 
 def peel_stages(seed: int = 21) -> Graph:
-    """G(n, m) with n = 300,000 and m = 2.2M, plus K_60, K_120 and K_181.
+    """G(n, m) with n = 300,000 and m = 2.2M, plus K_30, K_50, K_60 and K_170.
 
-    The live degree sum falls from 4.45M through 50,400 to 32,580 as the
-    peel goes. The smallest live degree jumps past k + 1 four times: at the
-    first level, and at each clique.
+    Once G(n, m) is peeled, 410 vertices remain, with live degree sums
+    35,590, 34,720, 32,270 and 28,730 at the cliques' levels. The smallest
+    live degree jumps past k + 1 at the first level and at each clique.
     """
-    return disjoint_union([er(300000, 2200000, seed), complete(60), complete(120), complete(181)])
+    return disjoint_union([er(300000, 2200000, seed), complete(30), complete(50), complete(60), complete(170)])

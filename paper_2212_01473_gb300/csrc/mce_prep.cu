@@ -159,14 +159,22 @@ __device__ void block_bitonic(int *a, int len) {
 // Segments longer than kSmallSort are put in id order here through a bitmap;
 // shorter ones, and all final ranks, are done by k_peel_rank afterwards.
 //
-// As the remaining graph shrinks, fewer blocks go on: when the live degree sum
-// at a level start is at most kNarrowDegrees, blocks kNarrowBlocks and up
-// return and the rest meet at cheaper barriers (the dense core's many short
-// sub-rounds are barrier-bound); at most kSoloDegrees, block 0 finishes alone
-// with block barriers. Removal order and core numbers are the same either way.
+// As the remaining graph shrinks, fewer blocks go on. A level start may narrow
+// the grid when the live degree sum, the live vertices and the level's S are
+// all small: at most kNarrowDegrees, kNarrowLive and kNarrowS. Blocks
+// kNarrowBlocks and up then return, and the rest meet at cheaper barriers (the
+// dense core's many short sub-rounds are barrier-bound). Within kSoloDegrees,
+// kSoloLive and kSoloS, block 0 finishes alone with block barriers. A warp
+// removes one vertex at a time, so the stage must not start while S sets of
+// thousands of vertices can still come: the live vertices bound every later
+// S. Removal order and core numbers are the same either way.
 constexpr long long kNarrowDegrees = 1ll << 22;
 constexpr int kNarrowBlocks = 16;
+constexpr int kNarrowLive = 2 * kNarrowBlocks * kPeelThreads;
+constexpr int kNarrowS = 2 * kNarrowBlocks * (kPeelThreads / 32);
 constexpr long long kSoloDegrees = 32768;
+constexpr int kSoloLive = 2 * kPeelThreads;
+constexpr int kSoloS = 2 * (kPeelThreads / 32);
 // adjacency lists longer than this are removed by a whole block
 constexpr int kHeavyDeg = 64;
 
@@ -280,7 +288,10 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         guess = k + 1;
         // every block reads the same sum after the barrier and decides alike
         const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[ls];
-        if (!solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && live > kSoloDegrees) {
+        const int nlive = nrem + ns;
+        const bool to_solo = !solo && live <= kSoloDegrees && nlive <= kSoloLive && ns <= kSoloS;
+        if (!solo && !to_solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && nlive <= kNarrowLive &&
+            ns <= kNarrowS) {
             if (blockIdx.x >= kNarrowBlocks) return;
             nbar = kNarrowBlocks;
             nblocks = kNarrowBlocks;
@@ -289,7 +300,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             gwarp = tid >> 5;
             nwarps = nth >> 5;
         }
-        if (!solo && live <= kSoloDegrees) {
+        if (to_solo) {
             if (blockIdx.x != 0) return;
             solo = true;
             tid = threadIdx.x;

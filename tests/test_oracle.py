@@ -396,21 +396,50 @@ def test_multipartite_enumeration(k, size, first):
     assert c == size ** k == r.count and h == r.hash
 
 
-def test_peel_stages_graph_spans_every_stage():
-    # The GPU peel runs on the full grid while the live degree sum at a level
-    # start is above 2^22, on 16 blocks down to 32,768, then on one block. A
-    # level start guesses k + 1 and makes one more pass when no live vertex
-    # has that degree. gen.peel_stages() must reach all three stages and make
-    # that extra pass in each: the live degree sum at level k is twice the
-    # number of edges whose ends both have core number >= k.
-    g = gen.peel_stages()
-    core, rank, order, rounds = oracle.peel(g.row_ptr, g.col)
+def peel_stage_passes(g):
+    """The GPU peel's stage at every level-start pass of g, from the oracle.
+
+    A level start of the GPU peel narrows the grid to 16 blocks when the live
+    degree sum is at most 2^22, the live vertices at most 32,768 and its S at
+    most 1,024 vertices; it goes to one block (checked first) at most 32,768,
+    2,048 and 64. It guesses k + 1; when no live vertex has that degree, one
+    more pass runs first, in the stage of the level before. At level k the
+    live vertices are those of core number >= k, and S holds those with at
+    most k live neighbours. Returns (stage of each level, stage of each extra
+    pass); 0, 1, 2 = full grid, 16 blocks, one block.
+    """
+    core = oracle.peel(g.row_ptr, g.col)[0]
     src = np.repeat(np.arange(g.n), g.degrees())
-    lo = np.minimum(core[src], core[g.col])
-    ks = np.unique(core)
-    live = np.array([(lo >= k).sum() for k in ks])
-    stage = np.where(live > (1 << 22), 0, np.where(live > 32768, 1, 2))
-    jump = np.concatenate([[ks[0] > 0], np.diff(ks) > 1])
-    assert set(stage.tolist()) == {0, 1, 2}
-    assert {int(s) for s in stage[jump]} == {0, 1, 2}
-    assert ks.tolist()[-3:] == [59, 119, 180] and int(g.degrees().min()) > 0
+    stage, levels, extra, prev = 0, [], [], -1
+    for k in np.unique(core):
+        live_v = core >= k
+        both = live_v[src] & live_v[g.col]
+        ldeg = np.bincount(src[both], minlength=g.n)
+        live_sum, nlive = int(both.sum()), int(live_v.sum())
+        s_size = int((live_v & (ldeg <= k)).sum())
+        if k > prev + 1:
+            extra.append(stage)
+        if stage < 2 and live_sum <= 32768 and nlive <= 2048 and s_size <= 64:
+            stage = 2
+        elif stage == 0 and live_sum <= (1 << 22) and nlive <= 32768 and s_size <= 1024:
+            stage = 1
+        levels.append(stage)
+        prev = int(k)
+    return levels, extra
+
+
+def test_peel_stages_graph_spans_every_stage():
+    # gen.peel_stages() must run levels in all three stages of the GPU peel
+    # and make the extra level-start pass in each
+    g = gen.peel_stages()
+    levels, extra = peel_stage_passes(g)
+    assert set(levels) == {0, 1, 2}
+    assert set(extra) == {0, 1, 2}
+    assert int(g.degrees().min()) > 0
+
+
+def test_peel_stage_model_on_small_graphs():
+    # the grid narrows only once the live vertices bound every later S:
+    # never on G(n, m), whose every level still holds most of its vertices
+    levels, _ = peel_stage_passes(gen.er(200000, 1500000, 5))
+    assert set(levels) == {0}
