@@ -303,6 +303,26 @@ def test_worked_example_order():
     assert order.tolist() == [4, 5, 0, 1, 2, 3]
 
 
+@pytest.mark.parametrize("edges,n,order,rounds", [
+    # a path peels from both ends inward, two vertices per sub-round
+    ([(i, i + 1) for i in range(6)], 7, [0, 6, 1, 5, 2, 4, 3], 4),
+    # a star's leaves go first; the centre follows in the next sub-round
+    # although its id is the smallest
+    ([(0, i) for i in range(1, 6)], 6, [1, 2, 3, 4, 5, 0], 2),
+    # every vertex of a cycle or a clique leaves in the first sub-round
+    ([(i, (i + 1) % 8) for i in range(8)], 8, list(range(8)), 1),
+    ([(i, j) for i in range(5) for j in range(i + 1, 5)], 5, list(range(5)), 1),
+])
+def test_peel_order_closed_forms(edges, n, order, rounds):
+    # Sec. II-C's peel, level-synchronous: a sub-round removes every vertex
+    # whose remaining degree is at most k, in ascending id
+    g = gen.from_edges(n, edges)
+    core, rank, got, got_rounds = oracle.peel(g.row_ptr, g.col)
+    assert got.tolist() == order
+    assert got_rounds == rounds
+    assert np.array_equal(rank[got], np.arange(n))
+
+
 # ----------------------------------------------------------------- validation
 
 @pytest.mark.parametrize("bad", ["unsorted", "asym", "loop", "dup", "range", "rowptr"])
