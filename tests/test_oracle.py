@@ -221,6 +221,30 @@ def test_node_counts_complete_graph(n):
     assert ip.root_count.tolist() == [1] + [0] * (n - 1)
 
 
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 7])
+def test_node_counts_moon_moser(k):
+    # K_{3x k} is regular, so the peel keeps ids as ranks. Root v of part
+    # p = v // 3 has P0 = the later parts, X0 = the earlier parts. With P a
+    # K_{3x m} and X_P empty, the pivot is P's first vertex and its part gives
+    # three branches, each again K_{3x (m-1)} with X_P empty (a part's
+    # vertices are not adjacent): T(m) = 1 + 3 T(m-1), T(0) = 1.
+    T = lambda m: (3 ** (m + 1) - 1) // 2
+    g = gen.moon_moser(k)
+    # full Tomita: an earlier part's vertex is adjacent to all of P, so every
+    # root past part 0 stops at once
+    full = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_FULL, per_root=True)
+    assert full.root_nodes.tolist() == [T(k - 1) if v < 3 else 1 for v in range(3 * k)]
+    # pivot from P u X_P: the earlier parts (X_X) never become pivots
+    ip = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=True)
+    assert ip.root_nodes.tolist() == [T(k - 1 - v // 3) for v in range(3 * k)]
+    # no pivot: one call per clique of the later parts, 4 choices per part
+    nop = oracle.mce(g.row_ptr, g.col, mode=oracle.NO_PIVOT, per_root=True)
+    assert nop.root_nodes.tolist() == [4 ** (k - 1 - v // 3) for v in range(3 * k)]
+    assert int(nop.root_nodes.sum()) == 4 ** k - 1
+    for o in (full, ip, nop):
+        assert o.count == 3 ** k
+
+
 @pytest.mark.parametrize("n", [2, 3, 6, 10])
 def test_second_level_node_counts_complete_graph(n):
     # K_n, one subtree per edge (i, j), i < j (Algorithm 4): X = {0..j-1} - {i}.
