@@ -245,6 +245,43 @@ def test_node_counts_moon_moser(k):
         assert o.count == 3 ** k
 
 
+def _words(p):
+    return (p + 31) // 32
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 33, 70])
+def test_work_counter_complete_graph(n):
+    # The roofline's numerator: per node with P non-empty, W = ceil(|P0|/32)
+    # word-ops per pivot candidate scanned (ascending rank, up to the first
+    # that reaches the largest possible score), W for the branch set and 2W
+    # per branch. K_n, pivot from P u X_P: root r walks a chain of
+    # p0 = n - 1 - r nodes whose first candidate reaches |P| - 1 and leaves
+    # one branch: 4W each. Full Tomita: a later root scans vertex 0 of X_X,
+    # which reaches |P| and leaves no branch: 2W.
+    g = gen.complete(n)
+    _, ip = oracle.work(g.row_ptr, g.col, mode=oracle.PIVOT_IP)
+    _, full = oracle.work(g.row_ptr, g.col, mode=oracle.PIVOT_FULL)
+    chain = [4 * (n - 1 - r) * _words(n - 1 - r) for r in range(n)]
+    assert ip.tolist() == chain
+    assert full.tolist() == chain[:1] + [2 * _words(n - 1 - r) for r in range(1, n)]
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 5, 12])
+def test_work_counter_moon_moser(k):
+    # K_{3x k}: at a node whose P is a K_{3x m} (X_P empty), every candidate
+    # scores 3m - 3, short of the bound 3m - 1, so all 3m are scanned; the
+    # pivot's part gives 3 branches: W (3m + 7). A root of part p has 3^d
+    # such nodes at depth d with m = k - 1 - p - d. Full Tomita: roots past
+    # part 0 scan one vertex of X_X and stop (2W).
+    def tree(m):
+        return _words(3 * m) * sum(3 ** d * (3 * (m - d) + 7) for d in range(m))
+    g = gen.moon_moser(k)
+    _, ip = oracle.work(g.row_ptr, g.col, mode=oracle.PIVOT_IP)
+    _, full = oracle.work(g.row_ptr, g.col, mode=oracle.PIVOT_FULL)
+    assert ip.tolist() == [tree(k - 1 - v // 3) for v in range(3 * k)]
+    assert full.tolist() == [tree(k - 1) if v < 3 else 2 * _words(3 * (k - 1 - v // 3)) for v in range(3 * k)]
+
+
 @pytest.mark.parametrize("n", [2, 3, 6, 10])
 def test_second_level_node_counts_complete_graph(n):
     # K_n, one subtree per edge (i, j), i < j (Algorithm 4): X = {0..j-1} - {i}.
