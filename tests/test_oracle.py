@@ -245,6 +245,60 @@ def test_node_counts_moon_moser(k):
         assert o.count == 3 ** k
 
 
+def _py_tomita_nodes(g, mode):
+    """Per input vertex: (calls, maximal cliques) of its first-level subtree.
+
+    Independent of oracle.c: Algorithm 2 written over Python sets, taking
+    only the degeneracy order from the (separately pinned) oracle peel. The
+    pivot maximises |P n N(u)| over P u X_P, or over all of X too under full
+    Tomita; ties go to the smallest rank; branches run in ascending rank."""
+    _, rank, order, _ = oracle.peel(g.row_ptr, g.col)
+    n = g.n
+    adj = [set() for _ in range(n)]
+    for v in range(n):
+        for u in g.col[g.row_ptr[v]:g.row_ptr[v + 1]]:
+            adj[rank[v]].add(int(rank[u]))
+    calls = np.zeros(n, np.int64)
+    found = np.zeros(n, np.int64)
+
+    def walk(root, P, XP, XX):
+        calls[root] += 1
+        if not P and not XP and not XX:
+            found[root] += 1
+            return
+        if not P:
+            return
+        cands = P | XP | (XX if mode == oracle.PIVOT_FULL else set())
+        pivot, best = None, -1
+        for u in sorted(cands):
+            score = len(P & adj[u])
+            if score > best:
+                pivot, best = u, score
+        for v in sorted(P - adj[pivot]):
+            walk(root, P & adj[v], XP & adj[v], XX & adj[v])
+            P = P - {v}
+            XP = XP | {v}
+
+    for r in range(n):
+        walk(r, {u for u in adj[r] if u > r}, set(), {u for u in adj[r] if u < r})
+    by_id_calls, by_id_found = np.zeros(n, np.int64), np.zeros(n, np.int64)
+    by_id_calls[order] = calls
+    by_id_found[order] = found
+    return by_id_calls, by_id_found
+
+
+@pytest.mark.parametrize("mode", [oracle.PIVOT_FULL, oracle.PIVOT_IP])
+@pytest.mark.parametrize("n,p,seed", [(14, 0.4, 1), (24, 0.3, 2), (30, 0.5, 3), (40, 0.2, 4)])
+def test_node_counts_match_python_tomita(n, p, seed, mode):
+    # pins the tie rule and the pivot domains on irregular graphs, where the
+    # closed forms above cannot reach
+    g = gen.small_gnp(n, p, seed)
+    calls, found = _py_tomita_nodes(g, mode)
+    o = oracle.mce(g.row_ptr, g.col, mode=mode, per_root=True)
+    assert o.root_nodes.astype(np.int64).tolist() == calls.tolist()
+    assert o.root_count.astype(np.int64).tolist() == found.tolist()
+
+
 def _words(p):
     return (p + 31) // 32
 
