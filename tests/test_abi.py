@@ -60,3 +60,32 @@ def test_no_oracle_on_product_path():
         if f.endswith((".py", ".cu", ".cuh", ".h")):
             txt = open(f).read()
             assert "import oracle" not in txt and "liboracle" not in txt, f
+
+
+def test_ctypes_structs_match_the_c_header(tmp_path):
+    # The binding's ctypes structs must lay out exactly as include/mce.h:
+    # gcc compiles a probe that prints sizeof and every field's offsetof.
+    import ctypes
+    import shutil
+    import subprocess
+    from paper_2212_01473_gb300 import engine
+    if shutil.which("gcc") is None:
+        pytest.skip("needs gcc")
+    structs = [engine.mce_allocator, engine.mce_opts, engine.mce_result, engine.mce_stats]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "mce.h"', "int main(void) {"]
+    for st in structs:
+        t = st.__name__
+        lines.append('    printf("%s sizeof %%zu\\n", sizeof(%s));' % (t, t))
+        for name, _ in st._fields_:
+            lines.append('    printf("%s %s %%zu\\n", offsetof(%s, %s));' % (t, name, t, name))
+    lines += ["    return 0;", "}"]
+    (tmp_path / "probe.c").write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "probe"
+    subprocess.check_call(["gcc", "-std=c11", "-I", os.path.join(ROOT, "include"), str(tmp_path / "probe.c"),
+                           "-o", str(exe)])
+    got = dict(line.rsplit(" ", 1) for line in subprocess.check_output([str(exe)], text=True).splitlines())
+    for st in structs:
+        t = st.__name__
+        assert int(got[t + " sizeof"]) == ctypes.sizeof(st), t
+        for name, _ in st._fields_:
+            assert int(got["%s %s" % (t, name)]) == getattr(st, name).offset, (t, name)
