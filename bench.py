@@ -140,6 +140,15 @@ def wp_of_words(w):
     return None
 
 
+def launch_word_ops(word_ops_by_W, wp_lo, wp_hi):
+    """Word-ops of the roots whose rows fall in width classes wp_lo..wp_hi.
+
+    word_ops_by_W maps str(W) -> the oracle's word-op count of the roots with
+    W = ceil(|P0| / 32) words per row (W = 0: roots without later
+    neighbours, which no traversal launch runs)."""
+    return sum(v for w, v in word_ops_by_W.items() if int(w) > 0 and wp_lo <= wp_of_words(int(w)) <= wp_hi)
+
+
 def cpu_baseline(g, frac, seed=12345):
     """The CPU oracle as it stands, on a seeded uniform sample of roots."""
     import numpy as np
@@ -390,8 +399,7 @@ def run_ours(args):
     if golden and golden.get("count") == count and r_ip.tree_nodes == golden.get("tree_nodes"):
         # the launch runs the roots of every width class from wp_min to wp
         lo = dom.get("wp_min") or dom["wp"]
-        words = sum(v for w, v in golden["word_ops_by_W"].items()
-                    if int(w) > 0 and lo <= wp_of_words(int(w)) <= dom["wp"])
+        words = launch_word_ops(golden["word_ops_by_W"], lo, dom["wp"])
         achieved = words / (avg_ms / 1e3) / 1e9
         roofline["achieved"] = achieved
         roofline["frac"] = achieved / peak_gops
