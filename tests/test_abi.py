@@ -89,3 +89,18 @@ def test_ctypes_structs_match_the_c_header(tmp_path):
         assert int(got[t + " sizeof"]) == ctypes.sizeof(st), t
         for name, _ in st._fields_:
             assert int(got["%s %s" % (t, name)]) == getattr(st, name).offset, (t, name)
+
+
+def test_kernels_never_trap_or_assert():
+    # A failed wait or check must return an error status that the host reads,
+    # never fault the GPU: no trap instruction and no device-side assert in
+    # the CUDA sources (static_assert is compile-time and allowed).
+    srcs = glob.glob(os.path.join(ROOT, "paper_2212_01473_gb300", "csrc", "*.cu*"))
+    assert srcs
+    for path in srcs:
+        src = open(path).read()
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        assert "__trap" not in src, path
+        assert not re.search(r"\btrap\b", src), path
+        assert not re.search(r"(?<!static_)\bassert\s*\(", src), path
