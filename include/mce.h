@@ -69,7 +69,7 @@ extern "C" {
 #define MCE_DONATE_ANY 2   /* ... always (the donor may become idle right after) */
 
 /* root ordering */
-#define MCE_ORDER_PLAIN 0   /* roots in degeneracy order within each width class */
+#define MCE_ORDER_PLAIN 0   /* roots by descending degeneracy rank within each width class */
 #define MCE_ORDER_PRIORITY 1/* roots by descending opts.root_priority (e.g. learned work estimate) */
 
 typedef struct mce_graph mce_graph; /* opaque; owns its device copies */
