@@ -172,11 +172,6 @@ int mce_batch_create(const int32_t *graph_ptr, int32_t G, const int32_t *row_ptr
 int mce_run(mce_graph *g, const mce_opts *opts, mce_result *out, uint64_t *hist, int32_t hist_len);
 
 /*
- * Batched run: per_graph[G] results and hist[G * hist_len] (row g is graph
- * g's histogram), both HOST buffers; hist may be NULL. `total`, when not
- * NULL, receives the sums over all graphs.
- */
-/*
  * mce_run_list -- every maximal clique of a single-graph handle, listed.
  * The paper's kernels only count the cliques they find; this call also writes
  * each clique C to buf as one record [|C|, id_1, ..., id_|C|] of int32 words (input
@@ -195,13 +190,19 @@ int mce_run(mce_graph *g, const mce_opts *opts, mce_result *out, uint64_t *hist,
 int mce_run_list(mce_graph *g, const mce_opts *opts, int32_t *buf, int64_t cap_words, int64_t *words,
                  mce_result *out);
 
+/*
+ * Batched run: per_graph[G] results and hist[G * hist_len] (row g is graph
+ * g's histogram), both HOST buffers; hist may be NULL. `total`, when not
+ * NULL, receives the sums over all graphs.
+ */
 int mce_run_batch(mce_graph *g, const mce_opts *opts, mce_result *per_graph, uint64_t *hist,
                   int32_t hist_len, mce_result *total);
 
 /*
  * Autotuner: for every width class, times the whole class with a few launch
- * settings (donation threshold |P0|max/16, /8, /4; donation rule EITHER,
- * PAPER, ANY; full or one-block-per-SM grid) within about budget_ms of device
+ * settings (donation threshold max(10, |P0|max/10), max(10, |P0|max/20) and
+ * max(10, |P0|max/5); donation rule EITHER, PAPER, ANY; full or
+ * one-block-per-SM grid) within about budget_ms of device
  * time, and keeps the fastest per class in the handle. Runs with
  * opts.tuned = 1 then use them. Results are never affected.
  */
