@@ -205,6 +205,18 @@ def test_wide_rows_closed_form(n, t):
     assert r.hist[n - t] == 2 ** t and int(r.hist.sum()) == 2 ** t
 
 
+def test_degeneracy_above_the_limit_is_unsupported():
+    # K_4098 has degeneracy 4097, one above MCE_MAX_DEGENERACY (4096): create
+    # reports MCE_EUNSUPPORTED after the peel instead of running out of row width
+    n = 4098
+    idx = np.arange(n * n, dtype=np.int64)
+    col = (idx % n)[idx % (n + 1) != 0].astype(np.int32)  # row i: every j != i, ascending
+    row_ptr = (np.arange(n + 1, dtype=np.int64) * (n - 1)).astype(np.int32)
+    with pytest.raises(mce.MCEError) as e:
+        mce.mce_create(row_ptr, col)
+    assert e.value.code == mce.MCE_EUNSUPPORTED
+
+
 def test_complete_graph_node_counts():
     # K_n, pivot from P u X_P: root r walks a chain of n - r calls
     n = 200
