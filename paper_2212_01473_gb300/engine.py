@@ -471,10 +471,15 @@ def mce_run_list(h: Handle, buf=None, opts: Optional[mce_opts] = None):
 
 
 def decode_clique_records(flat) -> List[np.ndarray]:
-    """Split a list of records [k, id_1, ..., id_k] (numpy int32) into arrays."""
+    """Split a list of records [k, id_1, ..., id_k] (numpy int32) into arrays.
+
+    Raises ValueError on a record of size < 1 or one that runs past the end:
+    every record mce_run_list writes holds a clique of at least one vertex."""
     out, i, n = [], 0, len(flat)
     while i < n:
         k = int(flat[i])
+        if k < 1 or i + 1 + k > n:
+            raise ValueError("malformed clique record at word %d (size %d, %d words left)" % (i, k, n - i - 1))
         out.append(np.asarray(flat[i + 1:i + 1 + k]))
         i += 1 + k
     return out

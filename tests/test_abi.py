@@ -104,3 +104,14 @@ def test_kernels_never_trap_or_assert():
         assert "__trap" not in src, path
         assert not re.search(r"\btrap\b", src), path
         assert not re.search(r"(?<!static_)\bassert\s*\(", src), path
+
+
+def test_decode_clique_records_without_gpu():
+    import numpy as np
+    from paper_2212_01473_gb300 import decode_clique_records
+    got = decode_clique_records(np.array([2, 5, 7, 1, 3, 3, 0, 1, 2], np.int32))
+    assert [c.tolist() for c in got] == [[5, 7], [3], [0, 1, 2]]
+    assert decode_clique_records(np.zeros(0, np.int32)) == []
+    for bad in ([3, 1, 2], [0], [1, 4, -1]):
+        with pytest.raises(ValueError):
+            decode_clique_records(np.array(bad, np.int32))
