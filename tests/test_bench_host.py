@@ -51,3 +51,24 @@ def test_chunglu_1m_golden_covers_the_merged_launch():
     total = sum(v for w, v in by_w.items() if int(w) > 0)
     assert total == gold["word_ops"]
     assert bench.launch_word_ops(by_w, 1, 12) == total
+
+
+def test_reference_arm_prints_the_contract_line():
+    # bench.py --impl reference times the CPU oracle and prints one JSON line
+    # with the keys the benchmark contract names (run here on a small graph)
+    import subprocess
+    import sys
+    p = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0", "--workload", "er_2000", "--cpu-sample", "0.5"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert p.returncode == 0, p.stderr[-2000:]
+    lines = [l for l in p.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in d, key
+    assert d["impl"] == "reference" and d["metric"] == "maximal cliques/sec" and d["value"] > 0
+    assert d["config"]["workload"] == "er_2000"
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
+    assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
