@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--cpu-sample", type=float, default=0.05,
                     help="fraction of roots (seeded) the CPU oracle runs for its baseline")
     ap.add_argument("--pivot", default="auto", choices=["auto", "ip", "ipx"],
-                    help="pivot rule of the timed steps (auto = the Sec. IV-D heuristic)")
+                    help="pivot rule of the timed steps (auto = the Sec. IV-E heuristic)")
     ap.add_argument("--no-forms", action="store_true",
                     help="skip the learned-order and batched comparisons")
     return ap.parse_args()
@@ -423,7 +423,7 @@ def run_ours(args):
             "config": {"workload": args.workload, "n": g.n, "m": g.m, "degeneracy": results[-1].degeneracy,
                        "maximal_cliques": count, "hash": "0x%016x" % results[-1].hash,
                        "tree_nodes": results[-1].tree_nodes, "donations": results[-1].donations,
-                       "pivot": {"auto": "AUTO (Sec. IV-D: IPX when max degree / degeneracy <= 200)",
+                       "pivot": {"auto": "AUTO (Sec. IV-E: IPX when max degree / degeneracy <= 200)",
                                  "ip": "IP (pivot from P u X_P)",
                                  "ipx": "IPX (pivot from P u X)"}[args.pivot],
                        "ms_prep": results[-1].ms_prep, "ms_traverse": results[-1].ms_traverse,

@@ -47,9 +47,10 @@ extern "C" {
 #define MCE_EINVAL 1       /* bad argument or non-canonical graph */
 #define MCE_ENOMEM 2       /* device or host allocation failed */
 #define MCE_ECUDA 3        /* a CUDA call failed (message has the CUDA error) */
-#define MCE_ETIMEOUT 4     /* a device wait exceeded opts.timeout_ms; results discarded */
+#define MCE_ETIMEOUT 4     /* a device wait saw no progress for opts.timeout_ms; results discarded */
 #define MCE_ERANGE 5       /* hist_len <= max clique size; out->max_size is still set */
 #define MCE_EUNSUPPORTED 6 /* graph beyond the engine's limits (degeneracy > MCE_MAX_DEGENERACY) */
+#define MCE_EBUDGET 7      /* the run exceeded opts.run_budget_ms; results discarded */
 
 /* largest degeneracy (= largest per-root candidate set |P|) the engine handles */
 #define MCE_MAX_DEGENERACY 4096
@@ -57,8 +58,8 @@ extern "C" {
 /* create flags */
 #define MCE_FLAG_DEVICE_PTRS 1u /* row_ptr/col (and graph_ptr) are device pointers */
 
-/* pivot selection (Sec. III-D, III-E, IV-D) */
-#define MCE_PIVOT_AUTO 0 /* IP when max_degree/degeneracy > 200, else IPX (Sec. IV-D heuristic) */
+/* pivot selection (Sec. III-D, III-E, IV-E) */
+#define MCE_PIVOT_AUTO 0 /* IP when max_degree/degeneracy > 200, else IPX (Sec. IV-E heuristic) */
 #define MCE_PIVOT_IP 1   /* pivot from P u X_P (partial induced subgraph) */
 #define MCE_PIVOT_IPX 2  /* pivot from P u X_P u X_X (full induced subgraph) */
 
@@ -96,7 +97,9 @@ typedef struct {
     int32_t blocks;        /* persistent blocks per width class; 0 = all that fit on the GPU */
     int32_t donate_policy; /* which busy groups may donate a child (Sec. III-C): MCE_DONATE_* */
     int32_t stats;         /* 1 = collect per-phase SM cycle counters (see mce_stats); slows the run */
-    int64_t timeout_ms;    /* give-up bound for every device-side wait (default 60000) */
+    int64_t timeout_ms;    /* bound of every device-side wait (default 60000): an idle worker gives up
+                              when no donation, no end of the launch and no heartbeat of a busy
+                              worker has come for this long; work itself is never timed */
     /* optional DEVICE buffers, indexed by input vertex id, length n: the
      * clique count, hash sum and Bron-Kerbosch call count (tree nodes, root
      * call included) of each vertex's first-level subtree. */
@@ -116,6 +119,8 @@ typedef struct {
                             (2, Algorithm 4: R = {v_i, v_j}, no pivot step at the vertex level);
                             results are the same, tree nodes differ; opts.roots then selects
                             the edges of those vertices */
+    int64_t run_budget_ms; /* 0 = none; else the traversal stops once this much time has passed
+                              since its first launch and the run fails with MCE_EBUDGET */
 } mce_opts;
 
 typedef struct {
@@ -130,7 +135,8 @@ typedef struct {
 } mce_result;
 
 /* Fill *opts with defaults (IP/IPX auto, plain order, worker list on,
- * donate_min_p 0 = automatic, donate_policy MCE_DONATE_EITHER, timeout 60 s). */
+ * donate_min_p 0 = automatic, donate_policy MCE_DONATE_EITHER, timeout 60 s,
+ * no run budget). */
 void mce_default_opts(mce_opts *opts);
 
 /*
@@ -269,11 +275,10 @@ int mce_get_stats(const mce_graph *g, mce_stats *out);
  * order), for callers that must not allocate device memory. The paper has no
  * counterpart; it is a deployment variant of the same kernel.
  *
- * Who needs it: code whose device memory is budgeted by someone else -- a
- * serving process whose pool reserves the whole GPU up front, a plug-in
- * running inside another framework's allocator, or a stage that must not call
- * cudaMalloc because cudaMalloc can synchronise the device and is not allowed
- * while a stream is being captured into a CUDA graph.
+ * Who needs it: code whose device memory is owned by someone else -- a
+ * serving process whose memory pool reserves the whole GPU up front (a
+ * cudaMalloc of its own would fail or fragment the pool), or a plug-in that
+ * runs inside another framework and may only use the buffers it is handed.
  *
  * It allocates nothing: its scratch is one file-scope static device array of
  * (5 * MCE_NOALLOC_MAX_VERTICES + MCE_NOALLOC_MAX_VERTICES / 32 + 1184) 32-bit
@@ -283,12 +288,15 @@ int mce_get_stats(const mce_graph *g, mce_stats *out);
  *   row_ptr, col  DEVICE CSR (canonical, as for mce_create); n vertices, m edges
  *   core, rank    DEVICE int32[n], by input id: core number, position in the order
  *   order         DEVICE int32[n]: order[r] = the vertex of rank r
- *   stream        cudaStream_t (NULL = default stream); synchronous on return
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture. Every call on a device shares the same array and
- * the call clears what must start at zero, so calls that overlap on the GPU
- * (two streams, two threads) race and must be serialised by the caller.
+ *   stream        cudaStream_t of the current device (NULL = default stream);
+ *                 a stream of another device fails with MCE_EINVAL
+ * Each call looks up the array's device address (cudaGetSymbolAddress) for
+ * the current device, clears the parts that must start at zero, runs the
+ * validation and the peel on `stream`, and synchronises that stream three
+ * times to read the status words back: the call is synchronous on return.
+ * Every call on a device shares the same array, so calls that overlap on the
+ * GPU (two streams, two threads) race and must be serialised by the caller.
+ * Each grid-barrier wait of the peel gives up after 60 s (MCE_ETIMEOUT).
  * Results equal mce_create's order (mce_get_order). Errors: MCE_EINVAL,
  * MCE_EUNSUPPORTED, MCE_ETIMEOUT, MCE_ECUDA; message in mce_last_error().
  */
@@ -352,6 +360,20 @@ void mce_destroy(mce_graph *g);
 
 /* Message for the last failing call on this thread (never NULL). */
 const char *mce_last_error(void);
+
+/*
+ * Self-test of the engine's device-side waits (no counterpart in the paper:
+ * it checks that every wait is bounded, without faulting the GPU). It runs
+ * one of the waits on its own, on `stream`, with a bound of timeout_ms
+ * (1..10000) and returns what the engine would report:
+ *   which 0  the worker list's idle wait on a flag nothing sets, one worker
+ *            counted as busy, no heartbeat          -> MCE_ETIMEOUT
+ *   which 1  the peel's grid barrier, one block short -> MCE_ETIMEOUT
+ *   which 2  the idle wait with a busy worker posting heartbeats for three
+ *            bounds, then ending the launch          -> MCE_OK
+ * Synchronous on return; the context stays usable in every case.
+ */
+int mce_selftest_waits(int32_t which, int64_t timeout_ms, void *stream);
 
 #ifdef __cplusplus
 }

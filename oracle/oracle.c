@@ -5,7 +5,8 @@
  *
  * Everything is written for a reader checking it against the paper:
  * sets are sorted int arrays, adjacency is a binary search in a sorted row,
- * the recursion is Algorithm 2 (or 1) verbatim, and roots follow
+ * the recursion is a plain restatement of Bron-Kerbosch with Tomita pivoting
+ * (Sec. II-B, Algorithm 2; without a pivot, Algorithm 1), and roots follow
  * Algorithm 3 over the degeneracy order. No blocking, bitsets or fusion.
  */
 #include "oracle.h"

@@ -377,7 +377,7 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
             !pb.bitmap || !pb.blocksums || !pb.ctl) { rc = fail(MCE_ENOMEM, "device allocation for the peel failed"); goto cleanup; }
         CK(cudaMemsetAsync(pb.bitmap, 0, (((size_t)n + 31) / 32 + 1) * 4, g->stream));
         CK(launch_peel_init(pb.ctl, n, g->stream));
-        if (n > 0) CK(launch_peel(n, d_rp, d_col, pb, g->sm_count, 30ull * 1000000000ull, g->stream));
+        if (n > 0) CK(launch_peel(n, d_rp, d_col, pb, g->sm_count, kPeelWaitNs, g->stream));
         CK(cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, g->stream));
         PeelCtl hctl{};
         CK(cudaMemcpyAsync(&hctl, pb.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, g->stream));
@@ -482,8 +482,13 @@ static int grow_scratch(mce_graph *g, size_t bytes) {
 // (device work only: memsets and kernels, so it can be captured into a CUDA
 // graph), then collected (results copied back and checked).
 
-__global__ void k_init_ctl(int *ctl, int groups) {
-    if (threadIdx.x == 0 && blockIdx.x == 0) ctl[CTL_ACTIVE] = groups;
+// t0: the run's start for its time budget, taken by the first launch of the
+// run (the outputs, t0 included, are zeroed when the run is enqueued)
+__global__ void k_init_ctl(int *ctl, int groups, unsigned long long *t0) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        ctl[CTL_ACTIVE] = groups;
+        if (*t0 == 0ull) *t0 = globaltimer_ns();
+    }
 }
 
 struct RunPlan {
@@ -550,6 +555,7 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     else if (opts.roots && opts.n_roots < 0) rc = fail(MCE_EINVAL, "opts.n_roots < 0");
     else if (opts.tuned && !g->tuned_valid) rc = fail(MCE_EINVAL, "opts.tuned set but mce_autotune has not run on this handle");
     else if (opts.subtree_level < 0 || opts.subtree_level > 2) rc = fail(MCE_EINVAL, "bad opts.subtree_level");
+    else if (opts.run_budget_ms < 0) rc = fail(MCE_EINVAL, "opts.run_budget_ms < 0");
     if (rc != MCE_OK) { delete P; return rc; }
     if (opts.timeout_ms <= 0) opts.timeout_ms = 60000;
     P->level2 = opts.subtree_level == 2;
@@ -558,7 +564,7 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     P->HL = g->d + 2;  // every maximal clique has at most d + 1 vertices
     P->launch_base = launch_counter();
     // outputs: count[G], hash[G], hist[G*HL], nodes, donations | max_size, status, phase counters
-    const size_t out_words64 = (size_t)2 * G + (size_t)G * P->HL + 4 + 2 * kNumPhases;
+    const size_t out_words64 = (size_t)2 * G + (size_t)G * P->HL + 4 + 2 * kNumPhases + 1;
     P->obuf_bytes = out_words64 * 8 + 64;
     P->obuf = (unsigned long long *)dalloc(g, P->obuf_bytes);
     if (!P->obuf) { free_plan(g, P); return fail(MCE_ENOMEM, "device allocation of outputs failed"); }
@@ -583,6 +589,7 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     dout.status = dout.max_size + 1;
     dout.phase_cycles = dout.nodes + 4;
     dout.phase_counts = dout.phase_cycles + kNumPhases;
+    dout.t0 = dout.phase_counts + kNumPhases;
     dout.root_count = (unsigned long long *)opts.root_count;
     dout.root_hash = (unsigned long long *)opts.root_hash;
     dout.root_nodes = (unsigned long long *)opts.root_nodes;
@@ -691,7 +698,7 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         a.n_roots = P->counts[c];
         a.rows_cap = k.rows;
         a.x_cap = k.x_cap;
-        // IPX: pivots may also come from X_X; AUTO follows the Sec. IV-D rule
+        // IPX: pivots may also come from X_X; AUTO follows the Sec. IV-E rule
         // (partial induced subgraphs when max degree / degeneracy > 200)
         a.pivot_ipx = opts.pivot == MCE_PIVOT_IPX ||
                       (opts.pivot == MCE_PIVOT_AUTO && g->d > 0 && (double)g->max_deg / g->d <= 200.0);
@@ -704,6 +711,7 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         a.root_chunk = 1;
         a.stats = opts.stats ? 1 : 0;
         a.timeout_ns = (uint64_t)opts.timeout_ms * 1000000ull;
+        a.budget_ns = (uint64_t)opts.run_budget_ms * 1000000ull;
         a.arena_words_per_group = aw;
         a.mail_words = mail_words;
     }
@@ -780,7 +788,7 @@ static int enqueue_run(mce_graph *g, RunPlan *P) {
         const size_t idle_words = ((size_t)k.groups + 31) / 32;
         const size_t flag_words = (size_t)k.groups * kMailFlagStride;
         CK(cudaMemsetAsync(k.a.ctl, 0, (CTL_NCTL + idle_words + flag_words) * 4, s));
-        k_init_ctl<<<1, 32, 0, s>>>(k.a.ctl, k.groups);
+        k_init_ctl<<<1, 32, 0, s>>>(k.a.ctl, k.groups, P->dout.t0);
         count_launch();
         CK(record(P->ev[e++], s, P->capturing));
         CK(launch_class_wp(k.L, P->dg, P->dout, k.a, k.rows, s));
@@ -842,7 +850,8 @@ static int collect_run(mce_graph *g, RunPlan *P, mce_result *per_graph, uint64_t
     st.kernel_launches = g->create_launches + (P->replay ? 0 : P->plan_launches) + P->run_launches;
     st.peel_rounds = g->peel_rounds;
     g->last = st;
-    if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms", (long long)P->opts.timeout_ms); goto cleanup; }
+    if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms with no progress", (long long)P->opts.timeout_ms); goto cleanup; }
+    if (hflags[1] & ST_BUDGET) { rc = fail(MCE_EBUDGET, "the run exceeded its time budget of %lld ms", (long long)P->opts.run_budget_ms); goto cleanup; }
     if (hflags[1] & ST_OVERFLOW) { rc = fail(MCE_ECUDA, "internal capacity exceeded in the traversal"); goto cleanup; }
     {
         float ms = 0;

@@ -14,6 +14,7 @@ enum : int {
     ST_TIMEOUT = 1,   // a bounded wait gave up
     ST_OVERFLOW = 2,  // an internal capacity was exceeded (engine bug guard)
     ST_BADGRAPH = 4,  // validation failed
+    ST_BUDGET = 8,    // the run's time budget (opts.run_budget_ms) ran out
 };
 
 // Golden-ratio increment of the clique hash (h(C) in mce.h).
@@ -53,11 +54,57 @@ __device__ __forceinline__ int ld_relaxed(const int *p) {
     asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
     return v;
 }
+__device__ __forceinline__ unsigned long long ld_relaxed_u64(const unsigned long long *p) {
+    unsigned long long v;
+    asm volatile("ld.relaxed.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned long long v) {
+    asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
+}
+
+// The worker-list wait of an idle group (one thread). It returns 1 when a
+// donated subtree arrived (*flag was set; it is cleared), 0 when the launch
+// is over (no active group left), and -1 when it gave up. It gives up with
+// ST_TIMEOUT once timeout_ns have passed since the later of its own start and
+// the last heartbeat a busy group posted in *beat (globaltimer ns), so a wait
+// ends only when nothing has moved for that long; it gives up with ST_BUDGET
+// past budget_end, and at once when another group has set either bit.
+__device__ inline int idle_wait(int *flag, const int *active, int *status, const unsigned long long *beat,
+                                uint64_t timeout_ns, uint64_t budget_end) {
+    const uint64_t w0 = globaltimer_ns();
+    unsigned ns = 64;
+    for (unsigned spin = 1;; spin++) {
+        if (ld_acquire(flag)) {
+            *flag = 0;
+            return 1;
+        }
+        // the shared termination word and the clock are read less often
+        if ((spin & 7u) == 0) {
+            if (ld_acquire(active) == 0) return 0;
+            if (ld_relaxed(status) & (ST_TIMEOUT | ST_BUDGET)) return -1;
+            const uint64_t now = globaltimer_ns();
+            const uint64_t hb = ld_relaxed_u64(beat);
+            const uint64_t since = hb > w0 ? hb : w0;
+            if (now > since && now - since > timeout_ns) {
+                atomicOr(status, ST_TIMEOUT);
+                return -1;
+            }
+            if (now > budget_end) {
+                atomicOr(status, ST_BUDGET);
+                return -1;
+            }
+        }
+        __nanosleep(ns);
+        if (ns < 1024) ns <<= 1;
+    }
+}
 
 // Grid-wide barrier for a cooperatively launched (all blocks co-resident)
-// kernel. Every wait is bounded by `deadline` (globaltimer ns); on expiry the
-// status word gets ST_TIMEOUT and the barrier returns false in every block
-// that sees it, so the kernel can return instead of hanging.
+// kernel. Each wait is bounded: a block that has waited timeout_ns since it
+// arrived (globaltimer ns) sets ST_TIMEOUT in the status word, and the barrier
+// returns false in every block that sees it, so the kernel can return
+// instead of hanging. Work between barriers is never timed.
 struct GridBar {
     unsigned count;
     unsigned gen;
@@ -65,7 +112,7 @@ struct GridBar {
 
 // nblk: the number of blocks taking part (gridDim.x, or fewer once the others
 // have returned for good).
-__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t deadline, unsigned nblk) {
+__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t timeout_ns, unsigned nblk) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
@@ -80,11 +127,12 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
         } else {
             // poll the generation word back to back; the status word and the
             // clock are read every 64 polls, and long waits back off
+            const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
             while (ld_acquire_u(&bar->gen) == g) {
                 if ((++spins & 63u) == 0) {
                     if (ld_relaxed(status) & ST_TIMEOUT) { ok = 0; break; }
-                    if (globaltimer_ns() > deadline) {
+                    if (globaltimer_ns() - t0 > timeout_ns) {
                         atomicOr(status, ST_TIMEOUT);
                         ok = 0;
                         break;
@@ -156,6 +204,7 @@ struct DevOut {
     int32_t *list;                     // optional clique records [k, id_1 .. id_k]
     unsigned long long list_cap;       // words of list
     unsigned long long *list_used;     // [1] words the complete list needs
+    unsigned long long *t0;            // [1] globaltimer at the run's first launch (set by k_init_ctl)
 };
 
 // Host-side launch of one width class of the traversal (mce_traverse*.cu).
@@ -182,7 +231,8 @@ struct ClassArgs {
     const int32_t *eoff;    // level2: [n_roots + 1] exclusive prefix of the roots' |P0|
     int64_t n_tasks;        // roots, or edges when level2
     int32_t stats;          // 1: collect per-phase cycle counters
-    uint64_t timeout_ns;
+    uint64_t timeout_ns;    // bound of each wait (see idle_wait)
+    uint64_t budget_ns;     // run time budget from *DevOut::t0; 0 = none
     // scratch (device), sized by the host for groups = blocks * warps_per_block / gw
     uint32_t *arena;        // per-group: stack, X rows, X index lists, (A if a_global)
     size_t arena_words_per_group;
@@ -194,8 +244,9 @@ struct ClassArgs {
 };
 
 // Control words of a traversal launch, each on its own 128-byte line so that
-// polling one does not slow atomics on another.
-enum CtlSlot { CTL_NEXT_ROOT = 0, CTL_ACTIVE = 32, CTL_IDLE = 64, CTL_NCTL = 96 };
+// polling one does not slow atomics on another. CTL_BEAT holds a 64-bit
+// heartbeat (globaltimer ns) that busy groups post for the idle wait.
+enum CtlSlot { CTL_NEXT_ROOT = 0, CTL_ACTIVE = 32, CTL_IDLE = 64, CTL_BEAT = 96, CTL_NCTL = 128 };
 constexpr int kMailFlagStride = 8;  // ints between two groups' mail flags (32 bytes)
 
 // Width classes: padded words per row. A row stride w with w/4 odd keeps

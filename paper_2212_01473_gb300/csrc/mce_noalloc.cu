@@ -2,7 +2,6 @@
 // that cannot allocate device memory. All scratch lives in one file-scope
 // static device array; the caller passes the graph and the output buffers.
 #include <cstdio>
-#include <mutex>
 
 #include "mce_prep.cuh"
 
@@ -24,10 +23,6 @@ using namespace mce;
 
 namespace {
 
-constexpr int kMaxDevices = 64;
-std::mutex g_setup_mu;
-uint32_t *g_scratch_addr[kMaxDevices] = {};  // device address of g_noalloc_scratch, per device
-
 int noalloc_fail(int code, const char *msg) {
     char buf[256];
     snprintf(buf, sizeof buf, "mce_peel_noalloc: %s", msg);
@@ -45,19 +40,22 @@ extern "C" int mce_peel_noalloc(const int32_t *row_ptr, const int32_t *col, int3
     if (n == 0) return MCE_OK;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices)
-        return noalloc_fail(MCE_ECUDA, "cudaGetDevice failed");
+    if (cudaGetDevice(&dev) != cudaSuccess) return noalloc_fail(MCE_ECUDA, "cudaGetDevice failed");
+    if (s) {
+        // the array and the launch belong to the current device: the stream must too
+        int sdev = -1;
+        if (cudaStreamGetDevice(s, &sdev) != cudaSuccess) return noalloc_fail(MCE_ECUDA, "cudaStreamGetDevice failed");
+        if (sdev != dev) return noalloc_fail(MCE_EINVAL, "the stream belongs to another device than the current one");
+    }
+    // The array's device address in the current context, looked up on every
+    // call (no allocation): a cached address would go stale if the context
+    // were destroyed and created again (cudaDeviceReset).
     uint32_t *base = nullptr;
     {
-        // once per device, with that device current: the array's device address
-        std::lock_guard<std::mutex> lock(g_setup_mu);
-        if (!g_scratch_addr[dev]) {
-            void *p = nullptr;
-            if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
-                return noalloc_fail(MCE_ECUDA, "cudaGetSymbolAddress failed");
-            g_scratch_addr[dev] = (uint32_t *)p;
-        }
-        base = g_scratch_addr[dev];
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p)
+            return noalloc_fail(MCE_ECUDA, "cudaGetSymbolAddress failed");
+        base = (uint32_t *)p;
     }
     int sm_count = 0;
     if (cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
@@ -106,12 +104,12 @@ extern "C" int mce_peel_noalloc(const int32_t *row_ptr, const int32_t *col, int3
 
     PeelCtl hctl{};
     if (launch_peel_init(pb.ctl, n, s) != cudaSuccess ||
-        launch_peel(n, row_ptr, col, pb, sm_count, 30ull * 1000000000ull, s) != cudaSuccess ||
+        launch_peel(n, row_ptr, col, pb, sm_count, kPeelWaitNs, s) != cudaSuccess ||
         cudaMemcpyAsync(&h_status, pb.status, sizeof(int), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaMemcpyAsync(&hctl, pb.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess)
         return noalloc_fail(MCE_ECUDA, "peel launch failed");
-    if (h_status & ST_TIMEOUT) return noalloc_fail(MCE_ETIMEOUT, "peel timed out");
+    if (h_status & ST_TIMEOUT) return noalloc_fail(MCE_ETIMEOUT, "a grid-barrier wait of the peel exceeded 60 s");
     if (hctl.next != n) return noalloc_fail(MCE_ECUDA, "peel ended early");
     return MCE_OK;
 }

@@ -185,7 +185,6 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                                                        PeelCtl *ctl, int *status, uint64_t timeout_ns) {
     __shared__ int sh[64];
     __shared__ long long shl[32];
-    const uint64_t deadline = globaltimer_ns() + timeout_ns;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -199,7 +198,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             __syncthreads();
             return true;
         }
-        return grid_barrier(gbar, status, deadline, nbar);
+        return grid_barrier(gbar, status, timeout_ns, nbar);
     };
 
     for (int64_t v = tid; v < n; v += nth) {

@@ -27,6 +27,8 @@ struct PeelBufs {
 cudaError_t launch_validate(int n, const int32_t *rp, const int32_t *col, int64_t m2, int *status,
                             cudaStream_t s, bool cols);
 cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s);
+// bound of each grid-barrier wait of the peel (mce_create, mce_peel_noalloc)
+constexpr uint64_t kPeelWaitNs = 60ull * 1000000000ull;
 cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &b, int sm_count,
                         uint64_t timeout_ns, cudaStream_t s);
 cudaError_t exclusive_scan(const int32_t *in, int32_t *out, int64_t n, int32_t *tmp, cudaStream_t s);

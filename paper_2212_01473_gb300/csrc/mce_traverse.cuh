@@ -13,7 +13,7 @@
 //   X_P  = excluded vertices that came from P0: one bitset per level.
 // A node is (P, X_P, X_X prefix). Pivot: u in P u X_P maximising
 // |P n N(u)| (Sec. III-E restricts the pivot to X_P u P for partial induced
-// subgraphs; with IPX, Sec. IV-D, X_X rows are candidates too), ties to the
+// subgraphs; with IPX, Sec. IV-E, X_X rows are candidates too), ties to the
 // smallest rank. Branches: P - N(u) in ascending rank. R is maximal when P,
 // X_P and X_X are all empty.
 //
@@ -372,7 +372,22 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
     uint32_t *rid = ar.rid;
     constexpr bool listing = LIST;
 
-    const uint64_t deadline = globaltimer_ns() + C.timeout_ns;
+    // Only waits are timed (idle_wait); busy groups post a heartbeat for them
+    // at most every timeout/8. Work itself is bounded only by the optional run
+    // budget, checked with the heartbeat every 1024 loop iterations.
+    unsigned long long *const beat = reinterpret_cast<unsigned long long *>(C.ctl + CTL_BEAT);
+    const uint64_t beat_every = C.timeout_ns / 8 > 100000ull ? C.timeout_ns / 8 : 100000ull;
+    const uint64_t budget_end = C.budget_ns ? *O.t0 + C.budget_ns : ~0ull;
+    uint64_t last_beat = 0;
+    // thread 0 of a group: post the heartbeat when due; true past the budget
+    auto tick = [&]() -> bool {
+        const uint64_t now = globaltimer_ns();
+        if (now - last_beat > beat_every) {
+            st_relaxed_u64(beat, now);
+            last_beat = now;
+        }
+        return now > budget_end;
+    };
     PhaseClock pc{};
     pc.on = C.stats != 0 && g.gl == 0;
 
@@ -456,26 +471,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     atomicAdd(&C.ctl[CTL_IDLE], 1);
                     __threadfence();
                     atomicSub(&C.ctl[CTL_ACTIVE], 1);
-                    unsigned ns = 64;
-                    int* const flag = &C.mail_flag[(size_t)gg * kMailFlagStride];
-                    for (unsigned spin = 1;; spin++) {
-                        if (ld_acquire(flag)) {
-                            *flag = 0;
-                            mail = 1;
-                            r = (int)C.mail[(size_t)gg * C.mail_words + 0];
-                            break;
-                        }
-                        // the shared termination word and the clock are read less often
-                        if ((spin & 7u) == 0) {
-                            if (ld_acquire(&C.ctl[CTL_ACTIVE]) == 0) break;
-                            if (ld_relaxed(O.status) & ST_TIMEOUT) break;
-                            if (globaltimer_ns() > deadline) {
-                                atomicOr(O.status, ST_TIMEOUT);
-                                break;
-                            }
-                        }
-                        __nanosleep(ns);
-                        if (ns < 1024) ns <<= 1;
+                    int *const flag = &C.mail_flag[(size_t)gg * kMailFlagStride];
+                    if (idle_wait(flag, &C.ctl[CTL_ACTIVE], O.status, beat, C.timeout_ns, budget_end) > 0) {
+                        mail = 1;
+                        r = (int)C.mail[(size_t)gg * C.mail_words + 0];
                     }
                     pc.stop(PH_IDLE);
                     pc.count(PH_IDLE, mail);
@@ -703,7 +702,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             uint32_t *curP = cur;
             int l = l0;
             bool enter = true;
-            bool timed_out = false;
+            bool over_budget = false;
             // one maximal clique of sz vertices: R's first sz - nx ids (rid) and up
             // to three more (x1..x3); sum = the sum of its members' hash ids
             auto record = [&](int sz, uint64_t sum, int nx, int32_t x1, int32_t x2, int32_t x3) {
@@ -856,8 +855,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             while (true) {
                 if ((++iters & 1023u) == 0) {
                     // group-uniform decision (every thread must leave together)
-                    if (grp_or(g, red, g.gl == 0 && globaltimer_ns() > deadline)) {
-                        timed_out = true;
+                    if (grp_or(g, red, g.gl == 0 && tick())) {
+                        over_budget = true;
                         break;
                     }
                 }
@@ -928,8 +927,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     uint32_t ksP = 0u, ksX = 0u, ksB = 0u, ksL = 0u;
                     uint64_t ksS = 0ull;
                     for (;;) {
-                        if ((++iters & 1023u) == 0 && __any_sync(FULL, g.lane == 0 && globaltimer_ns() > deadline)) {
-                            timed_out = true;
+                        if ((++iters & 1023u) == 0 && __any_sync(FULL, g.lane == 0 && tick())) {
+                            over_budget = true;
                             break;
                         }
                         if (kcentr) {
@@ -1165,7 +1164,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     // the compact subtree is done; the wide loop backtracks (the
                     // branch set is empty, and words no thread owns are 0)
                     kmode = false;
-                    if (timed_out) break;
+                    if (over_budget) break;
                     if (!own) {
                         p = 0u;
                         xp = 0u;
@@ -1429,9 +1428,9 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     enter = false;
                 }
             }
-            if (timed_out && g.gl == 0) atomicOr(O.status, ST_TIMEOUT);
+            if (over_budget && g.gl == 0) atomicOr(O.status, ST_BUDGET);
             g.sync();
-            if (ld_relaxed(O.status) & (ST_TIMEOUT | ST_OVERFLOW)) break;
+            if (ld_relaxed(O.status) & (ST_TIMEOUT | ST_OVERFLOW | ST_BUDGET)) break;
             // --------------------------------------------------- task done
             if (g.gl == 0) {
                 acc_nodes += t_nodes;

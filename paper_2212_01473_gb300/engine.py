@@ -15,7 +15,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "libmce.so")
 
-MCE_OK, MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETIMEOUT, MCE_ERANGE, MCE_EUNSUPPORTED = range(7)
+MCE_OK, MCE_EINVAL, MCE_ENOMEM, MCE_ECUDA, MCE_ETIMEOUT, MCE_ERANGE, MCE_EUNSUPPORTED, MCE_EBUDGET = range(8)
 MCE_FLAG_DEVICE_PTRS = 1
 MCE_PIVOT_AUTO, MCE_PIVOT_IP, MCE_PIVOT_IPX = 0, 1, 2
 MCE_ORDER_PLAIN, MCE_ORDER_PRIORITY = 0, 1
@@ -23,7 +23,8 @@ MCE_DONATE_PAPER, MCE_DONATE_EITHER, MCE_DONATE_ANY = 0, 1, 2
 MCE_MAX_DEGENERACY = 4096
 
 _NAMES = {MCE_EINVAL: "MCE_EINVAL", MCE_ENOMEM: "MCE_ENOMEM", MCE_ECUDA: "MCE_ECUDA",
-          MCE_ETIMEOUT: "MCE_ETIMEOUT", MCE_ERANGE: "MCE_ERANGE", MCE_EUNSUPPORTED: "MCE_EUNSUPPORTED"}
+          MCE_ETIMEOUT: "MCE_ETIMEOUT", MCE_ERANGE: "MCE_ERANGE", MCE_EUNSUPPORTED: "MCE_EUNSUPPORTED",
+          MCE_EBUDGET: "MCE_EBUDGET"}
 
 
 class MCEError(RuntimeError):
@@ -47,7 +48,8 @@ class mce_opts(ctypes.Structure):
                 ("timeout_ms", ctypes.c_int64), ("root_count", ctypes.c_void_p),
                 ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
                 ("root_priority", ctypes.c_void_p), ("roots", ctypes.c_void_p),
-                ("n_roots", ctypes.c_int64), ("tuned", ctypes.c_int32), ("subtree_level", ctypes.c_int32)]
+                ("n_roots", ctypes.c_int64), ("tuned", ctypes.c_int32), ("subtree_level", ctypes.c_int32),
+                ("run_budget_ms", ctypes.c_int64)]
 
 
 class mce_result(ctypes.Structure):
@@ -99,6 +101,7 @@ def library():
         lib.mce_prepare.argtypes = [vp, ctypes.POINTER(mce_opts)]
         lib.mce_run_prepared.argtypes = [vp, ctypes.POINTER(mce_result), u64p, i32, ctypes.POINTER(mce_result)]
         lib.mce_peel_noalloc.argtypes = [vp, vp, i32, i64, vp, vp, vp, vp]
+        lib.mce_selftest_waits.argtypes = [i32, i64, vp]
         f32p = ctypes.POINTER(ctypes.c_float)
         lib.mce_root_features.argtypes = [vp, vp, vp]
         lib.mce_model_create.argtypes = [f32p, ctypes.POINTER(mce_allocator), vp, ctypes.POINTER(vp)]
@@ -363,6 +366,14 @@ def mce_peel_noalloc(row_ptr, col, core, rank, order, stream: Optional[int] = No
 
 MCE_NUM_FEATURES = 16
 MCE_MODEL_PARAMS = 64 * 16 + 64 + 64 * 64 + 64 + 64 + 1 + 16 + 16
+
+
+def mce_selftest_waits(which: int, timeout_ms: int = 100, stream: Optional[int] = None) -> int:
+    """Run one of the engine's device-side waits on its own (include/mce.h):
+    returns the MCE_* status it ends with (MCE_ETIMEOUT for which 0 and 1,
+    MCE_OK for which 2) instead of raising."""
+    s = _current_stream()[0] if stream is None else stream
+    return int(library().mce_selftest_waits(int(which), int(timeout_ms), ctypes.c_void_p(s)))
 
 
 def mce_root_features(h: Handle, raw: bool = False):

@@ -331,15 +331,38 @@ def test_root_subset_empty_and_bad():
     assert ei.value.code == mce.MCE_EINVAL
 
 
-def test_timeout_is_reported_and_context_survives():
-    # every device wait is bounded: a 1 ms bound on a run that needs more makes
-    # the kernels give up and return MCE_ETIMEOUT; the next run is unaffected
-    g = gen.chung_lu(20000, 16.0, 2.1, 2000.0, 5, 25, 40, 3)
+def test_device_waits_give_up_and_context_survives():
+    # each kind of device wait, run on its own with a 50 ms bound: a wait that
+    # nothing releases gives up with MCE_ETIMEOUT (no fault, no hang), and a
+    # wait kept alive by heartbeats outlasts its bound and ends normally
+    assert mce.mce_selftest_waits(0, 50) == mce.MCE_ETIMEOUT  # idle wait, flag never set
+    assert mce.mce_selftest_waits(1, 50) == mce.MCE_ETIMEOUT  # grid barrier one block short
+    assert mce.mce_selftest_waits(2, 50) == mce.MCE_OK        # heartbeats for 150 ms, then released
+    g = gen.gnp(300, 0.1, 2)
+    same(run(g), oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP))
+
+
+def test_long_subtree_is_not_timed():
+    # one group walks a Moon-Moser root for far longer than the 20 ms wait
+    # bound (no donations), while the other groups wait in the worker list:
+    # the heartbeat keeps their waits alive, so only waits are ever timed
+    g = gen.moon_moser(15)
+    h = mce.mce_create(g.row_ptr, g.col)
+    r = mce.mce_run(h, mce.mce_default_opts(timeout_ms=20, blocks=1, donate_min_p=100000,
+                                            pivot=mce.MCE_PIVOT_IP))
+    ref = mce.mce_run(h)
+    mce.mce_destroy(h)
+    assert r.count == 3 ** 15 and r.max_size == 15 and r.hist[15] == 3 ** 15
+    assert (r.count, r.hash) == (ref.count, ref.hash)
+    assert r.ms_traverse > 20.0  # the walk really outlasted the wait bound
+
+
+def test_run_budget_stops_the_run_and_context_survives():
+    g = gen.moon_moser(15)
     h = mce.mce_create(g.row_ptr, g.col)
     with pytest.raises(mce.MCEError) as ei:
-        mce.mce_run(h, mce.mce_default_opts(timeout_ms=1, blocks=1, pivot=mce.MCE_PIVOT_IP))
-    assert ei.value.code == mce.MCE_ETIMEOUT
+        mce.mce_run(h, mce.mce_default_opts(run_budget_ms=2, blocks=1, donate_min_p=100000))
+    assert ei.value.code == mce.MCE_EBUDGET
     r = mce.mce_run(h)
     mce.mce_destroy(h)
-    o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP)
-    same(r, o)
+    assert r.count == 3 ** 15

@@ -1,9 +1,9 @@
 """mce_peel_noalloc: the degeneracy peel for callers that cannot allocate
-device memory (their memory is budgeted by another pool, or they run where
-cudaMalloc is not allowed, such as during stream capture). Its scratch is a
-static device array inside the library; its results must equal those of the
-allocating path (mce_create + mce_get_order), call after call, since every
-call reuses the same array.
+device memory (their memory is owned by a pool that reserves the GPU up
+front, or they only get the buffers another framework hands them). Its
+scratch is a static device array inside the library; its results must equal
+the CPU oracle's peel and those of the allocating path (mce_create +
+mce_get_order), call after call, since every call reuses the same array.
 
 The file name keeps this module last in pytest's collection order, so a run
 that stops at the first failure has already run every other test.
@@ -20,6 +20,7 @@ torch = pytest.importorskip("torch")
 if not torch.cuda.is_available():
     pytest.skip("needs a CUDA device", allow_module_level=True)
 
+import oracle  # noqa: E402
 import paper_2212_01473_gb300 as mce  # noqa: E402
 
 
@@ -43,10 +44,17 @@ def noalloc_order(g):
     return [t.cpu().numpy() for t in outs]
 
 
-def test_noalloc_peel_equals_allocating_path_on_consecutive_calls():
+def oracle_order(g):
+    core, rank, order, _ = oracle.peel(g.row_ptr, g.col)
+    return core, rank, order
+
+
+def test_noalloc_peel_equals_oracle_and_allocating_path_on_consecutive_calls():
     big = gen.workload("chunglu_200k")
     small = gen.workload("er_2000")
-    ref_big, ref_small = reference_order(big), reference_order(small)
+    ref_big, ref_small = oracle_order(big), oracle_order(small)
+    for a, b in zip(reference_order(big), ref_big):
+        assert np.array_equal(a, b)
     # two calls in a row on one graph, then another graph, then the first again:
     # whatever the previous call left in the shared array must not leak through
     for g, ref in ((big, ref_big), (big, ref_big), (small, ref_small), (big, ref_big)):
@@ -58,8 +66,9 @@ def test_noalloc_peel_equals_allocating_path_on_consecutive_calls():
 def test_noalloc_peel_across_every_peel_stage():
     # full grid, 16 blocks and one block, with a k jump in each stage
     g = gen.peel_stages()
-    for a, b in zip(noalloc_order(g), reference_order(g)):
-        assert np.array_equal(a, b)
+    ref = oracle_order(g)
+    for a, b, c in zip(noalloc_order(g), reference_order(g), ref):
+        assert np.array_equal(a, c) and np.array_equal(b, c)
 
 
 def test_noalloc_peel_rejects_graphs_beyond_its_capacity():
