@@ -27,7 +27,12 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 WP_CLASSES = [1, 2, 4, 12, 20, 28, 36, 68, 132]
-POPC_PER_SM_CLK = 16  # 32-bit population counts per SM per clock (integer pipe)
+WORK_TEXT = ("bitset word-ops of the oracle-counted Bron-Kerbosch tree (pivot rule IP), counted as one op per "
+             "32-bit word intersected and counted (AND + POPC + the accumulating add); the pivot scan is counted "
+             "up to the first candidate that reaches the largest score possible, as the kernel stops there")
+BYTES_TEXT = ("algorithmic bytes: per root v of the launch, 4 x (deg(v) + sum over u in N(v) of |later(u)|), "
+              "the oriented adjacency lists that building the root's bitset rows A and X_X reads, "
+              "each once per root, with no reuse across roots")
 
 
 def parse():
@@ -149,20 +154,104 @@ def launch_word_ops(word_ops_by_W, wp_lo, wp_hi):
     return sum(v for w, v in word_ops_by_W.items() if int(w) > 0 and wp_lo <= wp_of_words(int(w)) <= wp_hi)
 
 
-def cpu_baseline(g, frac, seed=12345):
-    """The CPU oracle as it stands, on a seeded uniform sample of roots."""
+def launch_bytes(g, outd, wp_lo, wp_hi):
+    """Algorithmic bytes (BYTES_TEXT) of the roots whose row width falls in
+    width classes wp_lo..wp_hi (roots with |P0| = 0 run in no launch)."""
+    import numpy as np
+    deg = np.diff(g.row_ptr).astype(np.int64)
+    src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
+    per_root = deg + np.bincount(src, weights=outd[g.col].astype(np.float64), minlength=g.n).astype(np.int64)
+    W = (outd.astype(np.int64) + 31) // 32
+    cls = np.array([wp_of_words(int(w)) or 0 for w in range(int(W.max()) + 1)])
+    wp = cls[W]
+    sel = (outd > 0) & (wp >= wp_lo) & (wp <= wp_hi)
+    return 4 * int(per_root[sel].sum())
+
+
+def measure_peaks():
+    """The roofline's denominators, measured on this GPU by the library's
+    microbenchmarks (mce_microbench) with the SM clock seen meanwhile, plus
+    the measured HBM copy bandwidth of MEASURED_PEAKS.json."""
+    import paper_2212_01473_gb300 as mce
+    wo, lop, l2 = (mce.mce_microbench(i) for i in range(3))
+    hbm = None
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            hbm = json.load(f).get("hbm_gbs")
+    return {"word_ops_per_s": wo["rate"], "word_ops_sm_mhz": wo["sm_mhz"], "lop3_per_s": lop["rate"],
+            "lop3_sm_mhz": lop["sm_mhz"], "l2_read_gbs": l2["rate"] / 1e9, "l2_sm_mhz": l2["sm_mhz"],
+            "hbm_gbs": hbm, "hbm_source": "MEASURED_PEAKS.json (driver-measured copy)" if hbm else None,
+            "how": "mce_microbench: word-ops = AND+POPC+add over independent register pairs, 4 x 256 threads "
+                   "per SM; L2 = 40 passes over 64 MiB with ld.global.cg; each timed by CUDA events after a warm-up"}
+
+
+def roofline_legs(words, nbytes, ms, peaks):
+    """Integer-pipe, HBM and L2 legs of one launch; the binding one is the
+    leg with the largest fraction of its peak."""
+    sec = ms / 1e3
+    legs = {}
+    if words is not None:
+        a = words / sec / 1e9
+        legs["alu"] = {"achieved": a, "peak": peaks["word_ops_per_s"] / 1e9, "unit": "G word-ops/s",
+                       "frac": a / (peaks["word_ops_per_s"] / 1e9), "work": words}
+    if nbytes is not None:
+        a = nbytes / sec / 1e9
+        if peaks.get("hbm_gbs"):
+            legs["hbm"] = {"achieved": a, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                           "frac": a / peaks["hbm_gbs"], "bytes": nbytes}
+        legs["l2"] = {"achieved": a, "peak": peaks["l2_read_gbs"], "unit": "GB/s",
+                      "frac": a / peaks["l2_read_gbs"], "bytes": nbytes}
+    bound = max(legs, key=lambda k: legs[k]["frac"]) if legs else None
+    return bound, legs
+
+
+def dominant_launch_ms(mce, h, opts, steps, flush_buf):
+    """Runs `opts` 1 + steps times (L2 flushed before each); returns the
+    longest launch of the last run, its mean duration over the timed runs (CUDA
+    events on the handle's stream) and the last result."""
+    import statistics
+    lst, r = [], None
+    for _ in range(1 + steps):
+        flush_buf.zero_()
+        r = mce.mce_run(h, opts)
+        st = mce.mce_get_stats(h)
+        lst.append(max(st["classes"], key=lambda c: c["ms"]))
+    dom = lst[-1]
+    same = [c["ms"] for c in lst[1:] if c["wp"] == dom["wp"]]
+    return dom, statistics.mean(same), r
+
+
+def cpu_baseline(g, frac, seed=12345, reps=3, single_frac=None):
+    """The CPU oracle as it stands, on a seeded uniform sample of roots: the
+    median of `reps` runs on every host core, and one single-threaded run on a
+    smaller sample (single_frac, default frac / 10)."""
     import numpy as np
     import oracle
     rs = np.random.default_rng(seed)
     k = max(1, int(round(frac * g.n)))
     roots = np.sort(rs.choice(g.n, size=k, replace=False)).astype(np.int32)
     threads = oracle.default_threads()
-    t0 = time.perf_counter()
-    r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=threads, roots=roots)
-    dt = time.perf_counter() - t0
-    return {"value": r.count / dt, "unit": "cliques/s", "cores": threads, "kind": "oracle", "seconds": dt,
-            "sample": "%d of %d roots (%.1f%%, seed %d), %d cliques in %.2f s incl. validation, "
-                      "peel and relabelling" % (k, g.n, 100.0 * frac, seed, r.count, dt)}
+    secs, r = [], None
+    for _ in range(max(1, reps)):
+        t0 = time.perf_counter()
+        r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=threads, roots=roots)
+        secs.append(time.perf_counter() - t0)
+    dt = statistics.median(secs)
+    out = {"value": r.count / dt, "unit": "cliques/s", "cores": threads, "kind": "oracle", "seconds": dt,
+           "sample": "%d of %d roots (%.1f%%, seed %d), %d cliques; median of %d runs of %.2f s each incl. "
+                     "validation, peel and relabelling" % (k, g.n, 100.0 * frac, seed, r.count, len(secs), dt)}
+    sf = frac / 10 if single_frac is None else single_frac
+    if sf > 0:
+        k1 = max(1, int(round(sf * g.n)))
+        roots1 = np.sort(np.random.default_rng(seed + 1).choice(g.n, size=k1, replace=False)).astype(np.int32)
+        t0 = time.perf_counter()
+        r1 = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=1, roots=roots1)
+        d1 = time.perf_counter() - t0
+        out["single_thread"] = {"value": r1.count / d1, "unit": "cliques/s", "cores": 1, "seconds": d1,
+                                "sample": "%d of %d roots (%.2f%%, seed %d), %d cliques" % (
+                                    k1, g.n, 100.0 * sf, seed + 1, r1.count)}
+    return out
 
 
 def run_reference(args):
@@ -175,7 +264,7 @@ def run_reference(args):
     vals, secs = [], []
     info = None
     for it in range(args.warmup + args.steps):
-        b = cpu_baseline(g, frac)
+        b = cpu_baseline(g, frac, reps=1, single_frac=0)
         if it >= args.warmup:
             vals.append(b["value"])
             secs.append(b["seconds"])
@@ -193,7 +282,23 @@ def run_reference(args):
     return 0
 
 
-def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf):
+def form_roofline(mce, h, opts, g, golden, peaks, steps, flush_buf, nodes_key="tree_nodes"):
+    """Roofline legs of the dominant launch of `opts` (pivot rule IP) on handle h."""
+    _, _, outd = mce.mce_get_order(h)
+    dom, kms, r = dominant_launch_ms(mce, h, opts, steps, flush_buf)
+    lo = dom.get("wp_min") or dom["wp"]
+    words = None
+    if golden and golden.get("word_ops_by_W") and r.tree_nodes == golden.get(nodes_key):
+        words = launch_word_ops(golden["word_ops_by_W"], lo, dom["wp"])
+    bound, legs = roofline_legs(words, launch_bytes(g, outd, lo, dom["wp"]), kms, peaks)
+    top = legs[bound]
+    return {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+            "frac": top["frac"], "kernel_ms": kms, "legs": legs,
+            "kernel": "k_traverse<WP=%d,GW=%d> (pivot rule IP; width classes %d..%d words)" % (
+                dom["wp"], dom["group_warps"], lo, dom["wp"])}
+
+
+def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf, g=None, peaks=None):
     """Learned root order on the same workload, and the 4096-graph batch run
     batched (one set of persistent launches, replayed from a CUDA graph) versus
     graph by graph, all on this GPU."""
@@ -235,6 +340,16 @@ def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf):
     forms["learned"] = {"value": count * args.steps / (sum(ms) / 1e3), "unit": "cliques/s",
                         "ms_per_step": sum(ms) / len(ms), "vs_plain": count * args.steps / (sum(ms) / 1e3) / value_plain,
                         "model": "paper_2212_01473_gb300/work_model.json (%s)" % meta.get("train", "")}
+    if peaks is not None:
+        golden = load_golden(args.workload)
+        h = mce.mce_create(rp_d, col_d)
+        pr = learn.priority(model, h)
+        o = mce.mce_default_opts(order=mce.MCE_ORDER_PRIORITY, pivot=mce.MCE_PIVOT_IP)
+        o.root_priority = pr.data_ptr()
+        forms["learned"]["roofline"] = form_roofline(mce, h, o, g, golden, peaks, args.steps, flush_buf)
+        forms["plain"]["roofline"] = form_roofline(mce, h, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP), g, golden,
+                                                   peaks, args.steps, flush_buf)
+        mce.mce_destroy(h)
     model.close()
 
     # batched versus graph by graph
@@ -255,6 +370,10 @@ def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf):
     mce.mce_run_prepared(hb)
     ms_r, rr = timed(lambda: mce.mce_run_prepared(hb)[2], 2)
     assert rr.count == tot.count and rr.hash == tot.hash
+    b_roof = None
+    if peaks is not None:
+        b_roof = form_roofline(mce, hb, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP), b, load_golden("batch_4096"),
+                               peaks, 2, flush_buf, nodes_key="tree_nodes_ip")
     mce.mce_destroy(hb)
     parts = []
     for i in range(len(b.graph_ptr) - 1):
@@ -284,6 +403,8 @@ def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf):
                         "tuning": tune,
                         "one_by_one_value": v_1, "one_by_one_ms": ms_1[0],
                         "vs_one_by_one": v_b / v_1}
+    if b_roof is not None:
+        forms["batched"]["roofline"] = b_roof
     return forms
 
 
@@ -369,52 +490,44 @@ def run_ours(args):
     e2e = {"value": count * args.steps * world / sum(e2e_s), "unit": "cliques/s",
            "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
 
-    # ---- roofline of the dominant traversal launch (integer pipe). The
-    # oracle counts algorithmic work on the tree of the partial-induced-
-    # subgraph pivot rule (IP), so the roofline is taken on IP runs of the same
-    # workload; the timed steps above use the default rule (AUTO).
-    ip_ms, ip_stats = [], None
+    # ---- roofline of the dominant traversal launch: integer-pipe leg
+    # (oracle word-ops) and memory legs (algorithmic bytes) against peaks
+    # measured here. The oracle counts work on the tree of the partial-
+    # induced-subgraph pivot rule (IP), so the roofline is taken on IP runs of
+    # the same workload; the timed steps above use the default rule (AUTO).
+    peaks = measure_peaks()
     h = mce.mce_create(rp_d, col_d)
-    for _ in range(1 + args.steps):
-        flush_buf.zero_()
-        r_ip = mce.mce_run(h, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP))
-        ip_stats = mce.mce_get_stats(h)
-        ip_ms.append(max(ip_stats["classes"], key=lambda c: c["ms"]))
+    _, _, outd = mce.mce_get_order(h)
+    dom, kms, r_ip = dominant_launch_ms(mce, h, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP), args.steps,
+                                        flush_buf)
     mce.mce_destroy(h)
-    dom = ip_ms[-1]
-    avg_ms = statistics.mean(c["ms"] for c in ip_ms[1:])
     golden = load_golden(args.workload)
-    props = torch.cuda.get_device_properties(local)
-    sm_count = props.multi_processor_count
-    max_mhz = clk.get("sm_max_mhz") or 2070.0
-    peak_gops = sm_count * POPC_PER_SM_CLK * max_mhz * 1e6 / 1e9
-    roofline = {"bound": "alu", "achieved": None, "peak": peak_gops, "unit": "Gop/s", "frac": None,
-                "traffic": None, "kernel": "k_traverse<WP=%d,GW=%d> (pivot rule IP; roots of width classes %d..%d words)" % (
-                    dom["wp"], dom["group_warps"], dom.get("wp_min") or dom["wp"], dom["wp"]),
-                "kernel_ms": avg_ms,
-                "peak_basis": "derived: %d SMs x %d POPC/clk x %.0f MHz (max SM clock)" % (
-                    sm_count, POPC_PER_SM_CLK, max_mhz),
-                "work": "bitset word AND+POPC operations of the oracle-counted Bron-Kerbosch tree (pivot rule IP; "
-                        "tests/golden/%s.json word_ops_by_W) for the roots of this launch" % args.workload}
+    lo = dom.get("wp_min") or dom["wp"]
+    words = None
     if golden and golden.get("count") == count and r_ip.tree_nodes == golden.get("tree_nodes"):
-        # the launch runs the roots of every width class from wp_min to wp
-        lo = dom.get("wp_min") or dom["wp"]
         words = launch_word_ops(golden["word_ops_by_W"], lo, dom["wp"])
-        achieved = words / (avg_ms / 1e3) / 1e9
-        roofline["achieved"] = achieved
-        roofline["frac"] = achieved / peak_gops
-        prof = os.path.join(ROOT, "profiles", "traffic_%s.json" % args.workload)
-        if os.path.exists(prof):
-            with open(prof) as f:
-                tr = json.load(f)
-            # counters taken on another build of the kernel do not describe this one
-            if tr.get("kernel_wp") == dom["wp"] and tr.get("source_sha256") == traversal_source_hash():
-                roofline["traffic"] = tr.get("dram_bytes_per_launch")
-                roofline["traffic_note"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (%s)" % (
-                    os.path.relpath(prof, ROOT))
-            else:
-                roofline["traffic_note"] = "null: the traversal kernel changed since %s was captured" % (
-                    os.path.relpath(prof, ROOT))
+    nbytes = launch_bytes(g, outd, lo, dom["wp"])
+    bound, legs = roofline_legs(words, nbytes, kms, peaks)
+    top = legs[bound]
+    roofline = {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
+                "frac": top["frac"], "traffic": None,
+                "kernel": "k_traverse<WP=%d,GW=%d> (pivot rule IP; roots of width classes %d..%d words)" % (
+                    dom["wp"], dom["group_warps"], lo, dom["wp"]),
+                "kernel_ms": kms, "legs": legs, "peaks": peaks,
+                "peak_basis": "measured on this GPU by mce_microbench (alu, l2); HBM from MEASURED_PEAKS.json",
+                "work": WORK_TEXT + " (tests/golden/%s.json word_ops_by_W)" % args.workload, "bytes": BYTES_TEXT}
+    prof = os.path.join(ROOT, "profiles", "traffic_%s.json" % args.workload)
+    if os.path.exists(prof):
+        with open(prof) as f:
+            tr = json.load(f)
+        # counters taken on another build of the kernel do not describe this one
+        if tr.get("kernel_wp") == dom["wp"] and tr.get("source_sha256") == traversal_source_hash():
+            roofline["traffic"] = tr.get("dram_bytes_per_launch")
+            roofline["traffic_note"] = "ncu dram__bytes_read.sum + dram__bytes_write.sum of one launch (%s)" % (
+                os.path.relpath(prof, ROOT))
+        else:
+            roofline["traffic_note"] = "null: the traversal kernel changed since %s was captured" % (
+                os.path.relpath(prof, ROOT))
 
     line = {"metric": "maximal cliques/sec", "value": value, "unit": "cliques/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
@@ -437,7 +550,7 @@ def run_ours(args):
     if golden:
         line["config"]["oracle_match"] = golden.get("count") == count and golden.get("hash") == "0x%016x" % results[-1].hash
     if rank == 0 and world == 1 and not args.no_forms:
-        line["forms"] = measure_forms(args, rp_d, col_d, count, value, flush_buf)
+        line["forms"] = measure_forms(args, rp_d, col_d, count, value, flush_buf, g, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_sample)
     if rank == 0:

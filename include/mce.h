@@ -375,6 +375,21 @@ const char *mce_last_error(void);
  */
 int mce_selftest_waits(int32_t which, int64_t timeout_ms, void *stream);
 
+/*
+ * Microbenchmarks for the roofline's denominators (no counterpart in the
+ * paper, which quotes utilisation only): the chip's rate for the traversal's
+ * unit of work measured on its own, at full occupancy (4 blocks of 256
+ * threads per SM), on `stream`, synchronous on return.
+ *   which 0  bitset word-ops: AND + POPC + the add that accumulates it, over
+ *            independent register pairs       -> *rate in word-ops per second
+ *   which 1  three-input logic ops (LOP3)      -> *rate in ops per second
+ *   which 2  L2 reads: 40 passes over a 64 MiB buffer with 128-bit loads that
+ *            bypass L1                         -> *rate in bytes per second
+ * *sm_mhz (may be NULL): the SM clock during the timed launch (SM cycles over
+ * globaltimer); *ms (may be NULL): the launch's duration.
+ */
+int mce_microbench(int32_t which, double *rate, double *sm_mhz, double *ms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

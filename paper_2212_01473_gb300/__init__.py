@@ -8,7 +8,7 @@ from .engine import (mce_predict_priority, mce_autotune, mce_prepare, mce_run_pr
                      MCE_FLAG_DEVICE_PTRS, MCE_OK, MCE_ORDER_PLAIN, MCE_ORDER_PRIORITY, MCE_PIVOT_AUTO,
                      MCE_PIVOT_IP, MCE_PIVOT_IPX, MCEError, Result, enumerate_maximal_cliques, library,
                      mce_batch_create, mce_create, mce_default_opts, mce_destroy, mce_get_order,
-                     mce_get_stats, mce_graph_info, mce_peel_noalloc, mce_selftest_waits, mce_root_features, mce_run, mce_run_batch,
+                     mce_get_stats, mce_graph_info, mce_peel_noalloc, mce_selftest_waits, mce_microbench, mce_root_features, mce_run, mce_run_batch,
                      mce_run_list, decode_clique_records, list_maximal_cliques,
                      Model, MCE_MODEL_PARAMS, MCE_NUM_FEATURES)
 

@@ -102,6 +102,8 @@ def library():
         lib.mce_run_prepared.argtypes = [vp, ctypes.POINTER(mce_result), u64p, i32, ctypes.POINTER(mce_result)]
         lib.mce_peel_noalloc.argtypes = [vp, vp, i32, i64, vp, vp, vp, vp]
         lib.mce_selftest_waits.argtypes = [i32, i64, vp]
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.mce_microbench.argtypes = [i32, dp, dp, dp, vp]
         f32p = ctypes.POINTER(ctypes.c_float)
         lib.mce_root_features.argtypes = [vp, vp, vp]
         lib.mce_model_create.argtypes = [f32p, ctypes.POINTER(mce_allocator), vp, ctypes.POINTER(vp)]
@@ -374,6 +376,16 @@ def mce_selftest_waits(which: int, timeout_ms: int = 100, stream: Optional[int] 
     MCE_OK for which 2) instead of raising."""
     s = _current_stream()[0] if stream is None else stream
     return int(library().mce_selftest_waits(int(which), int(timeout_ms), ctypes.c_void_p(s)))
+
+
+def mce_microbench(which: int, stream: Optional[int] = None) -> dict:
+    """One of the roofline microbenchmarks (include/mce.h): 0 word-ops/s,
+    1 LOP3 ops/s, 2 L2 read bytes/s; with the SM clock seen meanwhile."""
+    s = _current_stream()[0] if stream is None else stream
+    rate, mhz, ms = ctypes.c_double(), ctypes.c_double(), ctypes.c_double()
+    _check(library().mce_microbench(int(which), ctypes.byref(rate), ctypes.byref(mhz), ctypes.byref(ms),
+                                    ctypes.c_void_p(s)))
+    return {"rate": rate.value, "sm_mhz": mhz.value, "ms": ms.value}
 
 
 def mce_root_features(h: Handle, raw: bool = False):

@@ -6,6 +6,7 @@ fingerprint of the graph so that a test can confirm the generator produced the
 same graph on another machine.
 
     python tests/golden/make_golden.py er_2000 chunglu_1m ...
+    python tests/golden/make_golden.py work batch_4096   # adds per-width work to a batch file
 
 Batched workloads (batch_*) store per-graph count, hash, largest size and
 histogram instead (see make_batch). Per single-graph workload, <name>.json holds: fingerprint (n, m, sha256 of row_ptr and
@@ -126,8 +127,61 @@ def make_batch(name, threads=0):
     print(name, total_c, out["hash"], "%.1fs" % out["oracle_seconds"], flush=True)
 
 
+def add_batch_work(name, threads=0):
+    """Add the oracle's tree nodes and bitset word-ops per row width W to a
+    stored batch file (pivot from P u X_P): the G(n,p) parts by one oracle
+    walk over their roots; each Moon-Moser block by a walk of one block of
+    that size alone, times the number of such blocks (a block's subtrees do
+    not depend on where its ids start: its peel order is the same)."""
+    b = gen.workload(name)
+    gp, mm = b.graph_ptr, b.mm_sizes
+    G = len(gp) - 1
+    path = os.path.join(HERE, name + ".json")
+    with open(path) as f:
+        out = json.load(f)
+    assert out["fingerprint"] == fingerprint(b)
+    t0 = time.time()
+    gnp_roots = np.concatenate([np.arange(gp[i], gp[i + 1] - mm[i], dtype=np.int32) for i in range(G)])
+    core, rank, order, rounds = oracle.peel(b.row_ptr, b.col)
+    rn, rw = oracle.work(b.row_ptr, b.col, mode=oracle.PIVOT_IP, threads=threads, roots=gnp_roots)
+    W = (later_degree(b, rank) + 31) // 32
+    by_w_nodes, by_w_work = {}, {}
+
+    def add(w, nodes, work):
+        by_w_nodes[w] = by_w_nodes.get(w, 0) + int(nodes)
+        by_w_work[w] = by_w_work.get(w, 0) + int(work)
+
+    sel = np.zeros(b.n, bool)
+    sel[gnp_roots] = True
+    for w in np.unique(W[sel]):
+        s = sel & (W == w)
+        add(int(w), rn[s].astype(np.uint64).sum(), rw[s].astype(np.uint64).sum())
+    for size in sorted(set(int(x) for x in mm if x)):
+        blk = gen.moon_moser(size // 3)
+        bn, bw = oracle.work(blk.row_ptr, blk.col, mode=oracle.PIVOT_IP, threads=threads)
+        _, brank, _, _ = oracle.peel(blk.row_ptr, blk.col)
+        bW = (later_degree(blk, brank) + 31) // 32
+        times = int((mm == size).sum())
+        for w in np.unique(bW):
+            s = bW == w
+            add(int(w), int(bn[s].astype(np.uint64).sum()) * times, int(bw[s].astype(np.uint64).sum()) * times)
+    out["tree_nodes_ip"] = sum(by_w_nodes.values())
+    out["word_ops"] = sum(by_w_work.values())
+    out["nodes_by_W"] = {str(k): v for k, v in sorted(by_w_nodes.items())}
+    out["word_ops_by_W"] = {str(k): v for k, v in sorted(by_w_work.items())}
+    out["work_seconds"] = round(time.time() - t0, 1)
+    with open(path, "w") as f:
+        json.dump(out, f)
+    print(name, "tree nodes", out["tree_nodes_ip"], "word-ops", out["word_ops"], "%.1fs" % out["work_seconds"])
+
+
 if __name__ == "__main__":
-    for name in sys.argv[1:]:
+    args = sys.argv[1:]
+    if args and args[0] == "work":
+        for name in args[1:]:
+            add_batch_work(name)
+        sys.exit(0)
+    for name in args:
         if name.startswith("batch_"):
             make_batch(name)
         else:
