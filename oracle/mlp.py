@@ -4,7 +4,9 @@ Same definition the engine documents in include/mce.h: input log2(1 + raw
 feature), standardised by (x - mean) / std; 16 -> 64 (ReLU) -> 64 (ReLU) -> 1;
 every weight rounded to bfloat16 (round to nearest, ties to even) before use;
 biases unrounded. Loss: mean squared error; gradients with respect to the
-unrounded weights (the rounding passes gradients straight through).
+unrounded weights (the rounding passes gradients straight through). Training
+step: Adam (Kingma and Ba, 2015) with bias correction on every trained entry
+(all but the standardisation's mean and std).
 Everything here is float64 so that it can check the GPU's float32 arithmetic.
 """
 import numpy as np
@@ -74,3 +76,22 @@ def loss_and_grad(params, feat, label, rounded=True):
     g[OW1:OB1] = (d1.T @ x).ravel()
     g[OB1:OW2] = d1.sum(0)
     return loss, g
+
+
+ADAM_B1, ADAM_B2, ADAM_EPS = 0.9, 0.999, 1e-8
+
+
+def adam_step(params, grad, m, v, t, lr):
+    """One Adam step (t = 1, 2, ...) in float64: the moment estimates
+    m <- b1 m + (1 - b1) g and v <- b2 v + (1 - b2) g^2, their bias-corrected
+    forms m / (1 - b1^t) and v / (1 - b2^t), and the update
+    theta <- theta - lr * m_hat / (sqrt(v_hat) + eps) on the trained entries.
+    Returns new (params, m, v); the inputs are not modified."""
+    p = np.array(params, dtype=np.float64)
+    g = np.asarray(grad, dtype=np.float64)[:OMEAN]
+    m = ADAM_B1 * np.asarray(m, np.float64) + (1.0 - ADAM_B1) * g
+    v = ADAM_B2 * np.asarray(v, np.float64) + (1.0 - ADAM_B2) * g * g
+    m_hat = m / (1.0 - ADAM_B1 ** t)
+    v_hat = v / (1.0 - ADAM_B2 ** t)
+    p[:OMEAN] -= lr * m_hat / (np.sqrt(v_hat) + ADAM_EPS)
+    return p, m, v

@@ -26,7 +26,9 @@ if not torch.cuda.is_available():
 import paper_2212_01473_gb300 as mce  # noqa: E402
 from paper_2212_01473_gb300 import learn  # noqa: E402
 
-GRAPHS = [gen.complete(9), gen.moon_moser(5), gen.worked_example(), gen.gnp(300, 0.08, 2),
+from test_oracle import hub_graph  # noqa: E402
+
+GRAPHS = [hub_graph(), gen.complete(9), gen.moon_moser(5), gen.worked_example(), gen.gnp(300, 0.08, 2),
           gen.chung_lu(3000, 12.0, 2.1, 300.0, 3, 10, 20, 4), gen.random_forest(200, 3),
           gen.chung_lu(6000, 20.0, 2.1, 1500.0, 3, 10, 20, 6)]  # hubs with |X0| > 256
 
@@ -40,6 +42,36 @@ def test_features_match_definition(g):
     want = ofeat.root_features(g.row_ptr, g.col)
     assert np.array_equal(raw.astype(np.int64), want)
     assert np.allclose(flt, np.log2(1.0 + want.astype(np.float64)), rtol=1e-6, atol=1e-6)
+
+
+def test_adam_step_matches_reference():
+    # Two mce_model_train_step calls against the FP64 Adam of oracle/mlp.py,
+    # each fed the gradient the engine computes at the same parameters
+    # (mce_model_gradient), so that the check isolates the update itself.
+    # Tolerance: the FP32 update differs from FP64 by a few ulps of its size
+    # (<= lr), plus the rounding of the stored FP32 parameter; entries whose
+    # gradient is within 1e-6 of zero can flip direction between two FP32
+    # gradient evaluations (atomic summation order), so they are only checked
+    # to move by at most lr.
+    p, x, t = _params(3)
+    lr = 1e-3
+    m = mce.Model(p)
+    xf, tf = torch.from_numpy(x).cuda(), torch.from_numpy(t).cuda()
+    m1 = v1 = np.zeros(omlp.OMEAN)
+    cur = p.astype(np.float32)
+    for step in (1, 2):
+        g, _ = m.gradient(xf, tf)
+        m.train_step(xf, tf, lr)
+        got = m.params().astype(np.float64)
+        want, m1, v1 = omlp.adam_step(cur.astype(np.float64), g.astype(np.float64), m1, v1, step, lr)
+        d = np.abs(got - want)
+        tight = np.abs(g.astype(np.float64)) > 1e-6
+        tol = 1e-5 * lr + 2.0 ** -22 * np.abs(want)
+        assert np.all(d[:omlp.OMEAN][tight[:omlp.OMEAN]] <= tol[:omlp.OMEAN][tight[:omlp.OMEAN]]), step
+        assert np.all(np.abs(got - cur)[:omlp.OMEAN] <= lr * (1 + 1e-5) + 2.0 ** -22 * np.abs(cur[:omlp.OMEAN]))
+        assert np.array_equal(got[omlp.OMEAN:], p[omlp.OMEAN:].astype(np.float64))
+        cur = got.astype(np.float32)
+    m.close()
 
 
 def _params(seed):

@@ -490,6 +490,79 @@ def test_features_star_and_path():
         assert f[leaf].tolist()[:4] == [1, 1, 1, 0] and f[leaf, 8] == 5 and f[leaf, 15] == 0
 
 
+def hub_graph():
+    """Hub 0 with a K_5 on 1..5 and 300 leaves 6..305. Leaves 6 (-> 1),
+    7 (-> 1, 2), 304 (-> 4) and 305 (-> 1, 2, 3) also touch the clique. The
+    peel removes the plain leaves (k = 1), 6 and 304 (k = 2), 7 (k = 3), 305
+    (k = 4), then 0..5 together (k = 5, ascending id): the hub's P0 is the
+    K_5 and its X0 all 300 leaves, of which X0' holds ids 6..261."""
+    edges = [(0, c) for c in range(1, 6)] + [(a, b) for a in range(1, 6) for b in range(a + 1, 6)]
+    edges += [(0, x) for x in range(6, 306)]
+    edges += [(6, 1), (7, 1), (7, 2), (304, 4), (305, 1), (305, 2), (305, 3)]
+    return gen.from_edges(306, edges)
+
+
+def test_features_hub_with_more_than_256_excluded():
+    # features 4, 6 and 14 look at X0' = the 256 smallest ids of X0 only: of
+    # the leaves touching P0, 6 and 7 are in X0', 304 and 305 are not
+    from oracle.features import root_features
+    g = hub_graph()
+    f = root_features(g.row_ptr, g.col)
+    want = [305, 5, 5, 300,
+            10 + 3,      # e(P0) + e(P0, X0'): 6 -> {1}, 7 -> {1, 2}
+            10, 3,
+            65536,       # e(P0) / C(5, 2) = 1
+            296 * 1 + 2 + 3 + 2 + 4 + (8 + 7 + 6 + 6 + 5),  # degrees of the leaves, then of 1..5
+            4, 4, 5, 5, 25,
+            2,           # leaf 7; leaf 305 (3) is outside X0'
+            0]
+    assert f[0].tolist() == want
+    # a leaf: P0 = {0} (the hub is later), X0 empty
+    assert f[100].tolist() == [1, 1, 1, 0, 0, 0, 0, 0, 305, 0, 0, 1, 5, 5, 0, 0]
+
+
+def test_features_joined_cliques_with_pendant():
+    # K4 on 0..3 and K5 on 4..8 joined by 0-4; vertex 9 adjacent to 3, 8 and
+    # 10. Peel: 10 (k = 1), 9 (k = 2), then 1, 2, 3 and 0 (k = 3), then 4..8
+    # (k = 4): cores 1 / 2 / 3 / 4, so P0 sets span different cores.
+    from oracle.features import root_features
+    edges = [(a, b) for a in range(4) for b in range(a + 1, 4)] + [(a, b) for a in range(4, 9) for b in range(a + 1, 9)]
+    edges += [(0, 4), (3, 9), (8, 9), (9, 10)]
+    g = gen.from_edges(11, edges)
+    f = root_features(g.row_ptr, g.col)
+    # root 9: P0 = {3 (core 3), 8 (core 4)}, not adjacent; X0 = {10}
+    assert f[9].tolist() == [3, 2, 2, 1, 0, 0, 0, 0, 4 + 5 + 1, 0, 0, 0, 4, 7, 0, 1]
+    # root 0: P0 = {4}, X0 = {1, 2, 3}
+    assert f[0].tolist() == [4, 3, 1, 3, 0, 0, 0, 0, 3 + 3 + 4 + 5, 0, 0, 1, 4, 4, 0, 0]
+    # root 3: 9 is earlier (rank 1), so P0 = {0} and X0 = {1, 2, 9}; 1 and 2
+    # are adjacent to 0, 9 is not
+    assert f[3].tolist() == [4, 3, 1, 3, 0 + 2, 0, 2, 0, 4 + 3 + 3 + 3, 0, 0, 1, 3, 3, 1, 0]
+
+
+def test_adam_reference_closed_forms():
+    from oracle import mlp
+    rs = np.random.default_rng(5)
+    p0 = rs.normal(0, 0.5, mlp.NPARAMS)
+    g = rs.normal(0, 1e-2, mlp.NPARAMS)
+    g[:5] = [0.0, 1e-3, -2.0, 1e-9, -1e-9]
+    lr = 1e-3
+    z = np.zeros(mlp.OMEAN)
+    step = -lr * g[:mlp.OMEAN] / (np.abs(g[:mlp.OMEAN]) + mlp.ADAM_EPS)
+    # the same gradient every step: m_hat = g and v_hat = g^2 at every t
+    p, m, v = p0, z, z
+    for t in range(1, 6):
+        p, m, v = mlp.adam_step(p, g, m, v, t, lr)
+        assert np.allclose(p[:mlp.OMEAN] - p0[:mlp.OMEAN], t * step, rtol=1e-12, atol=1e-15)
+    assert np.array_equal(p[mlp.OMEAN:], p0[mlp.OMEAN:])  # mean and std are not trained
+    # g then -g: m_hat_2 = -(1 - b1) / (1 + b1) g and v_hat_2 = g^2
+    p1, m1, v1 = mlp.adam_step(p0, g, z, z, 1, lr)
+    p2, _, _ = mlp.adam_step(p1, -g, m1, v1, 2, lr)
+    b1 = mlp.ADAM_B1
+    want = -lr * (-(1 - b1) / (1 + b1) * g[:mlp.OMEAN]) / (np.abs(g[:mlp.OMEAN]) + mlp.ADAM_EPS)
+    assert np.allclose(p2[:mlp.OMEAN] - p1[:mlp.OMEAN], want, rtol=1e-12, atol=1e-15)
+    assert p2[0] == p0[0]  # a zero gradient never moves its entry
+
+
 def test_mlp_reference_gradient_matches_finite_differences():
     from oracle import mlp
     rs = np.random.default_rng(0)
