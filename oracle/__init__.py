@@ -37,6 +37,9 @@ def _load():
         lib.oracle_clique_hash.argtypes = [i32p, ctypes.c_int32]
         lib.oracle_clique_hash.restype = ctypes.c_uint64
         lib.oracle_default_threads.restype = ctypes.c_int32
+        dp = ctypes.POINTER(ctypes.c_double)
+        lib.oracle_tree_estimate.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
+                                             i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, dp, dp]
         _lib = lib
     return _lib
 
@@ -143,6 +146,24 @@ def work(row_ptr, col, mode: int = PIVOT_IP, threads: int = 0, roots=None):
     if rc != 0:
         raise RuntimeError("oracle_mce_work failed: %d" % rc)
     return rn[:n], rw[:n]
+
+
+def tree_estimate(row_ptr, col, roots, probes: int = 64, seed: int = 1, mode: int = PIVOT_IP, threads: int = 0):
+    """Knuth's estimate of each root's first-level subtree size (tree nodes):
+    (mean, variance of one path's estimate), float64 per listed root."""
+    rp, rpp = _i32(row_ptr)
+    c, cp = _i32(col if len(col) else np.zeros(1, np.int32))
+    ro, rop = _i32(roots)
+    mean = np.zeros(max(len(ro), 1), np.float64)
+    var = np.zeros(max(len(ro), 1), np.float64)
+    D = ctypes.POINTER(ctypes.c_double)
+    rc = _load().oracle_tree_estimate(len(rp) - 1, rpp, cp, mode, threads, rop, len(ro), int(probes),
+                                      ctypes.c_uint64(seed), mean.ctypes.data_as(D), var.ctypes.data_as(D))
+    if rc == 1:
+        raise ValueError("oracle: invalid graph or arguments")
+    if rc != 0:
+        raise MemoryError("oracle_tree_estimate failed")
+    return mean[:len(ro)], var[:len(ro)]
 
 
 def multipartite(first: int, parts: int, part_size: int):

@@ -517,3 +517,171 @@ int oracle_multipartite(int32_t first, int32_t parts, int32_t part_size, uint64_
     *hash = h;
     return 0;
 }
+
+/* ------------------------------------------ subtree size estimate */
+
+/*
+ * Knuth's estimator of the size of a backtrack tree (D. E. Knuth, "Estimating
+ * the efficiency of backtrack programs", Math. Comp. 29 (1975) 121-136): walk
+ * one random path down from the root, at each node taking one of its d
+ * children with probability 1/d; the sum over the path's nodes of the product
+ * of the degrees above each node is an unbiased estimate of the number of
+ * nodes. The tree here is a first-level subtree of Algorithm 2 with the
+ * oracle's pivot rule: the same pivot, branch set and branch order as bk, so
+ * its node count is oracle_mce's per-root node count. The child for branch j
+ * starts from P minus the branches before j and X plus them (Algorithm 2's
+ * P = P - {v}, X = X u {v} after each branch), both intersected with N(v).
+ * Random numbers: SplitMix64 (Steele, Lea, Flood 2014) seeded per root.
+ */
+typedef struct {
+    const graph_t *g;
+    const int32_t *roots; /* ranks */
+    int64_t n_roots;
+    int32_t probes, max_deg;
+    uint64_t seed;
+    double *mean, *var;   /* by index into roots */
+    atomic_llong next;
+    atomic_int failed;
+} est_job_t;
+
+static uint64_t sm64_next(uint64_t *s) {
+    *s += 0x9E3779B97F4A7C15ull;
+    return mix64(*s);
+}
+
+/* one path of the subtree of rank r; buffers hold max_deg + 1 ints each */
+static double knuth_path(const graph_t *g, int32_t r, uint64_t *rng, int32_t *P, int32_t *XP, int32_t *XX,
+                         int32_t *B, int32_t *T, int32_t *U) {
+    const int32_t *row = g->adj + g->ap[r];
+    int32_t deg = g->ap[r + 1] - g->ap[r], split = 0;
+    while (split < deg && row[split] < r) split++;
+    int32_t np = deg - split, nxp = 0, nxx = split;
+    memcpy(P, row + split, (size_t)np * sizeof(int32_t));
+    memcpy(XX, row, (size_t)split * sizeof(int32_t));
+    double est = 0.0, weight = 1.0;
+    for (;;) {
+        est += weight;
+        if (np == 0) break;
+        /* pivot: largest |P n N(u)| over P u XP (u XX under the full rule), ties to the smallest rank */
+        int32_t best = -1, best_u = -1;
+        const int32_t *lists[3] = {P, XP, XX};
+        int32_t lens[3] = {np, nxp, g->mode == ORACLE_PIVOT_FULL ? nxx : 0};
+        for (int32_t q = 0; q < 3; q++)
+            for (int32_t i = 0; i < lens[q]; i++) {
+                int32_t u = lists[q][i], score = 0;
+                for (int32_t j = 0; j < np; j++) score += adjacent(g, u, P[j]);
+                if (score > best || (score == best && u < best_u)) { best = score; best_u = u; }
+            }
+        int32_t nb = 0;
+        for (int32_t j = 0; j < np; j++)
+            if (!adjacent(g, best_u, P[j])) B[nb++] = P[j];
+        if (nb == 0) break;
+        const int32_t pick = (int32_t)(((sm64_next(rng) >> 32) * (uint64_t)nb) >> 32);
+        weight *= (double)nb;
+        const int32_t v = B[pick];
+        /* P' = (P - B[0..pick)) n N(v), B[0..pick) being the smallest branches */
+        int32_t nt = 0, bi = 0;
+        for (int32_t j = 0; j < np; j++) {
+            while (bi < pick && B[bi] < P[j]) bi++;
+            if (bi < pick && B[bi] == P[j]) continue;
+            T[nt++] = P[j];
+        }
+        np = intersect_nbrs(g, T, nt, v, P);
+        /* XP' = (XP u B[0..pick)) n N(v), merged in ascending rank */
+        int32_t i = 0, k = 0, nu = 0;
+        while (i < nxp || k < pick) {
+            if (k >= pick || (i < nxp && XP[i] < B[k])) U[nu++] = XP[i++];
+            else U[nu++] = B[k++];
+        }
+        nxp = intersect_nbrs(g, U, nu, v, XP);
+        /* XX' = XX n N(v) */
+        nt = intersect_nbrs(g, XX, nxx, v, T);
+        memcpy(XX, T, (size_t)nt * sizeof(int32_t));
+        nxx = nt;
+    }
+    return est;
+}
+
+static void *est_worker(void *arg) {
+    est_job_t *job = (est_job_t *)arg;
+    const size_t sz = ((size_t)job->max_deg + 2) * sizeof(int32_t);
+    int32_t *buf = (int32_t *)malloc(6 * sz);
+    if (!buf) { atomic_store(&job->failed, 1); return NULL; }
+    int32_t *P = buf, *XP = P + job->max_deg + 2, *XX = XP + job->max_deg + 2, *B = XX + job->max_deg + 2,
+            *T = B + job->max_deg + 2, *U = T + job->max_deg + 2;
+    for (;;) {
+        long long i = atomic_fetch_add(&job->next, 1);
+        if (i >= job->n_roots) break;
+        const int32_t r = job->roots[i];
+        uint64_t rng = job->seed ^ mix64((uint64_t)(int64_t)job->g->order[r] + 1ull);
+        double s = 0.0, s2 = 0.0;
+        for (int32_t p = 0; p < job->probes; p++) {
+            const double e = knuth_path(job->g, r, &rng, P, XP, XX, B, T, U);
+            s += e;
+            s2 += e * e;
+        }
+        const double m = s / job->probes;
+        job->mean[i] = m;
+        job->var[i] = job->probes > 1 ? (s2 - job->probes * m * m) / (job->probes - 1) : 0.0;
+    }
+    free(buf);
+    return NULL;
+}
+
+int oracle_tree_estimate(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode, int32_t nthreads,
+                         const int32_t *roots_in, int64_t n_roots, int32_t probes, uint64_t seed, double *mean,
+                         double *var) {
+    if (oracle_validate(n, row_ptr, col) || !roots_in || n_roots < 0 || probes < 1) return 1;
+    if (mode != ORACLE_PIVOT_IP && mode != ORACLE_PIVOT_FULL) return 1;
+    int32_t *rank = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *order = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *ap = (int32_t *)malloc(((size_t)n + 1) * sizeof(int32_t));
+    int32_t *adj = (int32_t *)malloc(((size_t)row_ptr[n] + 1) * sizeof(int32_t));
+    int32_t *roots = (int32_t *)malloc(((size_t)n_roots + 1) * sizeof(int32_t));
+    int rc = 0;
+    if (!rank || !order || !ap || !adj || !roots) { rc = 2; goto done; }
+    if (oracle_peel(n, row_ptr, col, NULL, rank, order) < 0) { rc = 2; goto done; }
+    int32_t max_deg = 0;
+    ap[0] = 0;
+    for (int32_t r = 0; r < n; r++) {
+        int32_t v = order[r], d = row_ptr[v + 1] - row_ptr[v];
+        if (d > max_deg) max_deg = d;
+        ap[r + 1] = ap[r] + d;
+        int32_t *out = adj + ap[r];
+        for (int32_t j = 0; j < d; j++) out[j] = rank[col[row_ptr[v] + j]];
+        qsort(out, (size_t)d, sizeof(int32_t), cmp_int32);
+    }
+    for (int64_t i = 0; i < n_roots; i++) {
+        if (roots_in[i] < 0 || roots_in[i] >= n) { rc = 1; goto done; }
+        roots[i] = rank[roots_in[i]];
+    }
+    {
+        graph_t g = {ap, adj, order, mode, 0};
+        est_job_t job;
+        memset(&job, 0, sizeof(job));
+        job.g = &g;
+        job.roots = roots;
+        job.n_roots = n_roots;
+        job.probes = probes;
+        job.max_deg = max_deg;
+        job.seed = seed;
+        job.mean = mean;
+        job.var = var;
+        atomic_init(&job.next, 0);
+        atomic_init(&job.failed, 0);
+        int32_t nt = nthreads > 0 ? nthreads : oracle_default_threads();
+        if (nt > 1024) nt = 1024;
+        pthread_t th[1024];
+        int32_t started = 0;
+        for (int32_t t = 0; t < nt; t++) {
+            if (pthread_create(&th[t], NULL, est_worker, &job) != 0) break;
+            started++;
+        }
+        if (started == 0) est_worker(&job);
+        for (int32_t t = 0; t < started; t++) pthread_join(th[t], NULL);
+        if (atomic_load(&job.failed)) rc = 2;
+    }
+done:
+    free(rank); free(order); free(ap); free(adj); free(roots);
+    return rc;
+}

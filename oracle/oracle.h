@@ -98,6 +98,17 @@ int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32
  * graphs have part_size 3): the transversals, enumerated directly. */
 int oracle_multipartite(int32_t first, int32_t parts, int32_t part_size, uint64_t *count, uint64_t *hash);
 
+/*
+ * Knuth's unbiased estimate of each listed root's first-level subtree size
+ * (Bron-Kerbosch calls, as oracle_mce_work's root_nodes) under pivot rule
+ * `mode` (ORACLE_PIVOT_IP or ORACLE_PIVOT_FULL): mean[i] and sample variance
+ * var[i] of `probes` random root-to-leaf paths of roots[i] (input ids), each
+ * root's paths seeded from `seed` and its id. Returns 0, 1 (bad input) or 2.
+ */
+int oracle_tree_estimate(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode, int32_t nthreads,
+                         const int32_t *roots, int64_t n_roots, int32_t probes, uint64_t seed, double *mean,
+                         double *var);
+
 /* h(C) for a clique given by input ids (any order) */
 uint64_t oracle_clique_hash(const int32_t *ids, int32_t k);
 

@@ -563,6 +563,52 @@ def test_adam_reference_closed_forms():
     assert p2[0] == p0[0]  # a zero gradient never moves its entry
 
 
+def test_tree_estimate_exact_on_regular_trees():
+    # Moon-Moser and complete graphs: every node at a given depth of a root's
+    # subtree has the same number of children, so every random path gives the
+    # exact node count (zero variance), which the branching recurrence fixes:
+    # the first root of K_{3xk} has T(k) = 1 + 3 T(k - 1), T(0) = 1 nodes,
+    # and the first root of K_n is a chain of n nodes.
+    for k in (3, 5, 7):
+        g = gen.moon_moser(k)
+        mean, var = oracle.tree_estimate(g.row_ptr, g.col, np.arange(g.n, dtype=np.int32), probes=5, seed=3)
+        rn, _ = oracle.work(g.row_ptr, g.col, mode=oracle.PIVOT_IP)
+        assert np.array_equal(mean, rn.astype(np.float64)) and np.all(var == 0)
+        t = 1
+        for _ in range(k - 1):
+            t = 1 + 3 * t
+        assert mean[0] == t
+    # K_n: under the partial rule (pivot from P u X_P) root r walks a chain of
+    # n - r nodes; under full Tomita an earlier vertex covers P, so every root
+    # after the first has one node
+    g = gen.complete(10)
+    ids = np.arange(10, dtype=np.int32)
+    mean, var = oracle.tree_estimate(g.row_ptr, g.col, ids, probes=3, mode=oracle.PIVOT_IP)
+    assert mean.tolist() == [10 - r for r in range(10)] and np.all(var == 0)
+    mean, var = oracle.tree_estimate(g.row_ptr, g.col, ids, probes=3, mode=oracle.PIVOT_FULL)
+    assert mean[0] == 10 and np.all(mean[1:] == 1) and np.all(var == 0)
+
+
+@pytest.mark.parametrize("mode", [oracle.PIVOT_IP, oracle.PIVOT_FULL])
+def test_tree_estimate_is_unbiased_on_irregular_graphs(mode):
+    # Knuth's estimate is unbiased: the mean of many random paths sits within a
+    # few standard errors of the exact node count, root by root and in total
+    g = gen.chung_lu(3000, 12.0, 2.1, 300.0, 3, 10, 20, 4)
+    roots = np.arange(g.n, dtype=np.int32)
+    probes = 2000
+    mean, var = oracle.tree_estimate(g.row_ptr, g.col, roots, probes=probes, seed=7, mode=mode)
+    exact, _ = oracle.work(g.row_ptr, g.col, mode=mode)
+    exact = exact.astype(np.float64)
+    se = np.sqrt(var / probes)
+    assert np.all(mean[var == 0] == exact[var == 0])
+    z = np.abs(mean - exact)[var > 0] / se[var > 0]
+    assert z.max() < 6.0
+    assert abs(mean.sum() - exact.sum()) < 5.0 * np.sqrt((var / probes).sum())
+    # and the path choice matters: a different seed changes some estimates
+    mean2, _ = oracle.tree_estimate(g.row_ptr, g.col, roots, probes=probes, seed=8, mode=mode)
+    assert np.any(mean2[var > 0] != mean[var > 0])
+
+
 def test_mlp_reference_gradient_matches_finite_differences():
     from oracle import mlp
     rs = np.random.default_rng(0)
