@@ -119,8 +119,9 @@ typedef struct {
                             (2, Algorithm 4: R = {v_i, v_j}, no pivot step at the vertex level);
                             results are the same, tree nodes differ; opts.roots then selects
                             the edges of those vertices */
-    int64_t run_budget_ms; /* 0 = none; else the traversal stops once this much time has passed
-                              since its first launch and the run fails with MCE_EBUDGET */
+    int64_t run_budget_ms; /* the traversal stops once this much time has passed since its first
+                              launch and the run fails with MCE_EBUDGET (default 600000, a safety
+                              net that no run of the bundled workloads comes near); 0 = none */
 } mce_opts;
 
 typedef struct {
@@ -136,7 +137,7 @@ typedef struct {
 
 /* Fill *opts with defaults (IP/IPX auto, plain order, worker list on,
  * donate_min_p 0 = automatic, donate_policy MCE_DONATE_EITHER, timeout 60 s,
- * no run budget). */
+ * run budget 10 min). */
 void mce_default_opts(mce_opts *opts);
 
 /*

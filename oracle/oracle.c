@@ -565,12 +565,12 @@ static double knuth_path(const graph_t *g, int32_t r, uint64_t *rng, int32_t *P,
         /* pivot: largest |P n N(u)| over P u XP (u XX under the full rule), ties to the smallest rank */
         int32_t best = -1, best_u = -1;
         const int32_t *lists[3] = {P, XP, XX};
-        int32_t lens[3] = {np, nxp, g->mode == ORACLE_PIVOT_FULL ? nxx : 0};
+        int32_t lens[3] = {np, nxp, (g->mode == ORACLE_PIVOT_FULL) ? nxx : 0};
         for (int32_t q = 0; q < 3; q++)
             for (int32_t i = 0; i < lens[q]; i++) {
                 int32_t u = lists[q][i], score = 0;
                 for (int32_t j = 0; j < np; j++) score += adjacent(g, u, P[j]);
-                if (score > best || (score == best && u < best_u)) { best = score; best_u = u; }
+                if (score > best || (score == best && best_u > u)) { best = score; best_u = u; }
             }
         int32_t nb = 0;
         for (int32_t j = 0; j < np; j++)

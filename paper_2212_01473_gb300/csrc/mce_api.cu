@@ -256,6 +256,7 @@ extern "C" void mce_default_opts(mce_opts *o) {
     o->donate_min_p = 0;
     o->donate_policy = MCE_DONATE_EITHER;
     o->timeout_ms = 60000;
+    o->run_budget_ms = 600000;
 }
 
 extern "C" const char *mce_last_error(void) { return g_err.c_str(); }

@@ -282,6 +282,21 @@ __device__ __forceinline__ int grp_bits_to_list(const Grp<GW> &g, int *red, uint
     return tot;
 }
 
+// Position of the t-th (from 0) set bit of m; t < popc(m).
+__device__ __forceinline__ int nth_set_bit(uint32_t m, int t) {
+    int pos = 0;
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+        const int c = __popc(m & ((1u << sh) - 1u));
+        if (c <= t) {
+            t -= c;
+            m >>= sh;
+            pos += sh;
+        }
+    }
+    return pos;
+}
+
 // Copies the rows listed in rows[0..nrows) of a WP-word bit matrix.
 template <int WP, int GW>
 __device__ __forceinline__ void grp_copy_rows(const Grp<GW> &g, const int32_t *rows, int nrows, const uint32_t *src,
@@ -513,7 +528,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             // [3] kind. Kind 0 (wide): [4..4+WP) R' (path below the root), then
             // P', then X_P'. Kind 1 (compact, one-warp groups): [4..36) the rows
             // over the index space, [36..68) its local indices, [68] P, [69] X_P,
-            // [70..72) the hash sum of R; its X_X rows are in the arena's xcomp.
+            // [70..72) the hash sum of R; its X_X rows are in the arena's xcomp
+            // (by position), their ranks in xscr.
             const uint32_t *mb = C.mail + (size_t)gg * C.mail_words;
             const bool edge = L2 && !have_mail;  // a task of one edge {r, P0[ej]}
             const int l0 = have_mail ? (int)mb[1] : (edge ? 1 : 0);
@@ -524,7 +540,98 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             if (!reuse)
                 for (int i = g.gl; i < n0; i += GT) p0[i] = prow[i];
             int nx = 0;
-            if (reuse) {
+            // A root with |P0| <= 32 in a one-warp group (not an edge task, not
+            // received): its whole subtree runs in compact mode over L = P0, so
+            // its rows are built straight into registers: A in shared memory
+            // (cand[0, n0)), the X_X rows as one word each, packed by position
+            // into lane registers (rows 32 and on, and their ranks, in the arena's
+            // xcomp and xscr). No A or X_X rows go to the global arena.
+            const bool fast = GW == 1 && !have_mail && !L2 && n0 <= 32;
+            uint32_t f_row = 0u, f_xr = 0u, f_xk = 0u;
+            if (fast) {
+                constexpr unsigned FULL = 0xffffffffu;
+                uint32_t *frow = reinterpret_cast<uint32_t *>(cand);
+                if (g.lane < n0) frow[g.lane] = 0u;
+                __syncwarp();
+                int rb = 0, re = 0;
+                if (g.lane < n0) {
+                    const int32_t u = p0[g.lane];
+                    rb = G.out_ptr[u];
+                    re = G.out_ptr[u + 1];
+                }
+                const int npairs = n0 * (n0 - 1) / 2;
+                for (int q0 = 0; q0 < npairs; q0 += 32) {
+                    const int q = q0 + g.lane;
+                    // row i of pair q: the largest i with i (2 n0 - i - 1) / 2 <= q
+                    int i = 0;
+                    if (q < npairs) {
+                        int lo = 0, hi = n0 - 2;
+                        while (lo < hi) {
+                            const int mid = (lo + hi + 1) >> 1;
+                            if (mid * (2 * n0 - mid - 1) / 2 <= q) lo = mid;
+                            else hi = mid - 1;
+                        }
+                        i = lo;
+                    }
+                    const int lo0 = __shfl_sync(FULL, rb, i), hi0 = __shfl_sync(FULL, re, i);
+                    if (q < npairs) {
+                        const int k = i + 1 + (q - i * (2 * n0 - i - 1) / 2);
+                        const int32_t w = p0[k];
+                        int lo = lo0, hi = hi0;
+                        while (lo < hi) {
+                            const int mid = (lo + hi) >> 1;
+                            if (G.out_col[mid] < w) lo = mid + 1;
+                            else hi = mid;
+                        }
+                        if (lo < hi0 && G.out_col[lo] == w) {
+                            atomicOr(&frow[i], 1u << k);
+                            atomicOr(&frow[k], 1u << i);
+                        }
+                    }
+                }
+                __syncwarp();
+                f_row = g.lane < n0 ? frow[g.lane] : 0u;
+                for (int it = 0; it < x0; it += 32) {
+                    const int idx = it + g.lane;
+                    uint32_t w = 0u;
+                    int32_t x = 0;
+                    if (idx < x0) {
+                        x = xrow[idx];
+                        const int32_t *nr = G.out_col + G.out_ptr[x];
+                        const int len = G.out_ptr[x + 1] - G.out_ptr[x];
+                        int lo = 0;
+                        for (int j = find_in(nr, 0, len, r + 1); j < len && lo < n0; j++) {
+                            const int k = find_in(p0, lo, n0, nr[j]);
+                            if (k < n0 && p0[k] == nr[j]) {
+                                w |= 1u << k;
+                                lo = k + 1;
+                            } else {
+                                lo = k;
+                            }
+                        }
+                    }
+                    const unsigned hm = __ballot_sync(FULL, w != 0u);
+                    const int tot = __popc(hm);
+                    // lane j takes the (j - nx)-th row found in this chunk
+                    const int t = g.lane - nx;
+                    const int src = (t >= 0 && t < tot) ? nth_set_bit(hm, t) : 0;
+                    const uint32_t wv = __shfl_sync(FULL, w, src);
+                    const uint32_t xv = (uint32_t)__shfl_sync(FULL, x, src);
+                    if (t >= 0 && t < tot) {
+                        f_xr = wv;
+                        f_xk = xv;
+                    }
+                    if (w != 0u) {
+                        const int k = nx + __popc(hm & ((1u << g.lane) - 1u));
+                        if (k >= 32) {
+                            xcomp[k] = w;
+                            xscr[k] = (uint32_t)x;
+                        }
+                    }
+                    nx += tot;
+                }
+                __syncwarp();
+            } else if (reuse) {
                 nx = cached_nx;
             } else if (have_mail) {
                 // the donor wrote the A rows of P' u X_P' into the arena's A region
@@ -802,18 +909,21 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             // L = P u X_P of that node, in ascending local index so ties still go
             // to the smaller rank. Lane i holds L[i]'s adjacency row over L (kRow),
             // its local index (kL) and clique-hash id (kmj), and the saved state
-            // of compact depth i (ks*); X_X rows are re-encoded over L once
-            // (xcomp). Entered from a wide descent, at a root with |P0| <= 32, or
+            // of compact depth i (ks*); X_X rows are re-encoded over L once. Entered from a wide descent, at a root with |P0| <= 32, or
             // from a donated compact subtree; when the subtree is done the wide
             // loop backtracks as from any child.
-            bool kstart = GW == 1 && !have_mail && !L2 && n0 <= 32;  // the root itself
+            bool kstart = false;
             bool kmode = false, kcentr = false, kpend = false;
             // In compact mode the node's P, X_P, branch set, X_X end and hash sum
             // reuse the wide registers: the wide node is on the stack meanwhile.
             uint32_t &kP = p, &kX = xp, &kB = b;
-            int &kclx = lpx;
             uint64_t &kS = S;
             uint32_t kRow = 0u;
+            // X_X rows at compact entry (lane i keeps row i, and its rank, in kxr
+            // and kxk; rows 32 and on in xcomp[i], ranks in xscr[i]); kRc = the
+            // compact part of R as bits over L
+            int kclx = 0;
+            uint32_t kxr = 0u, kxk = 0u, kRc = 0u;
             int kL = 0, kd = 0, kbase = 0;
             if (edge) {
                 // Algorithm 4: R = {r, v_j}; P = the common neighbours after v_j,
@@ -839,12 +949,35 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     kstart = true;
                 }
             }
+            if (fast) {
+                // the root itself, in compact mode over L = P0 (local index = lane)
+                kRow = f_row;
+                kL = g.lane < n0 ? g.lane : 0;
+                kP = n0 == 32 ? 0xffffffffu : (1u << n0) - 1u;
+                kX = 0u;
+                kclx = nx;
+                kxr = f_xr;
+                kxk = C.pivot_ipx ? f_xk : 0u;
+                kRc = 0u;
+                kbase = 1;
+                kd = 0;
+                kcentr = true;
+                kpend = false;
+                kmode = true;
+                t_nodes++;  // the root node
+                enter = false;
+            }
             if (cmail) {
                 kRow = mb[4 + g.lane];
                 kL = (int)mb[36 + g.lane];
                 kP = mb[68];
                 kX = mb[69];
                 kS = (uint64_t)mb[70] | ((uint64_t)mb[71] << 32);
+                // the donor wrote the surviving X_X rows to xcomp, their ranks to xscr
+                kclx = (int)mb[2];
+                kxr = g.lane < kclx ? xcomp[g.lane] : 0u;
+                kxk = (C.pivot_ipx && g.lane < kclx) ? xscr[g.lane] : 0u;
+                kRc = 0u;
                 kbase = l0 + 1;
                 kd = 0;
                 kcentr = true;
@@ -892,9 +1025,13 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         }
                         if (!inl) kRow = 0u;
                     }
-                    for (int i0 = 0; i0 < lpx; i0 += 32) {
+                    // the X_X rows over L, by position: lane i keeps row i (and
+                    // its rank) in registers, rows 32 and on go to xcomp[i] and
+                    // their ranks to xscr[i]
+                    kclx = lpx;
+                    for (int i0 = 0; i0 < kclx; i0 += 32) {
                         const int i = i0 + g.lane;
-                        const uint32_t e = i < lpx ? xidx[i] : 0u;
+                        const uint32_t e = i < kclx ? xidx[i] : 0u;
                         const uint32_t *xr = xrows + (size_t)e * WP;
                         uint32_t w = 0u;
                         if (ident) {
@@ -906,9 +1043,17 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                 w |= ((xr[lj >> 5] >> (lj & 31)) & 1u) << j;
                             }
                         }
-                        if (i < lpx) xcomp[e] = w;
+                        const uint32_t rk = (C.pivot_ipx && i < kclx) ? xrank[e] : 0u;
+                        if (i0 == 0) {
+                            kxr = i < kclx ? w : 0u;
+                            kxk = rk;
+                        } else if (i < kclx) {
+                            xcomp[i] = w;
+                            xscr[i] = rk;
+                        }
                     }
                     __syncwarp();
+                    kRc = 0u;
                     kbase = l + 1;
                     kd = 0;
                     kcentr = true;
@@ -924,8 +1069,25 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     // copy of P0[0]'s), and the saved state of compact depth i
                     const uint64_t kmj = G.mixid[p0[kL]];
                     const int32_t kid = listing ? G.order[p0[kL]] : 0;  // input id of L[i]
-                    uint32_t ksP = 0u, ksX = 0u, ksB = 0u, ksL = 0u;
+                    uint32_t ksP = 0u, ksX = 0u, ksB = 0u, ksR = 0u;
                     uint64_t ksS = 0ull;
+                    // The X_X of a compact node is the entry rows that hold all of
+                    // R's compact part Rc (each branch keeps the rows adjacent to
+                    // its vertex), so no list is partitioned on the way down.
+                    // row_at: X_X row i (and its rank) of the lane's entry in the
+                    // chunk starting at i0
+                    auto row_at = [&](int i0, int i) -> uint32_t { return i0 == 0 ? kxr : (i < kclx ? xcomp[i] : 0u); };
+                    auto rank_at = [&](int i0, int i) -> uint32_t { return i0 == 0 ? kxk : (i < kclx ? xscr[i] : 0u); };
+                    // any X_X row holding all of `need` (Rc plus the branch) with f(row)
+                    auto xx_any = [&](uint32_t need, auto f) -> bool {
+                        bool found = false;
+                        for (int i0 = 0; i0 < kclx && !found; i0 += 32) {
+                            const int i = i0 + g.lane;
+                            const uint32_t xc = row_at(i0, i);
+                            found = __any_sync(FULL, i < kclx && (xc & need) == need && f(xc)) != 0;
+                        }
+                        return found;
+                    };
                     for (;;) {
                         if ((++iters & 1023u) == 0 && __any_sync(FULL, g.lane == 0 && tick())) {
                             over_budget = true;
@@ -942,38 +1104,27 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             const int bsc = (int)(best >> 8) - 1;
                             uint32_t prow = __shfl_sync(FULL, kRow, 31 - (int)(best & 255u));
                             if (ipx && kclx > 0) {
-                                unsigned long long bx = 0ull;
+                                // the best X_X row: largest score, then smallest rank
+                                int xs = 0;
+                                uint32_t xk = 0u, xrow = 0u;
                                 for (int i0 = 0; i0 < kclx; i0 += 32) {
                                     const int i = i0 + g.lane;
-                                    unsigned long long k2 = 0ull;
-                                    if (i < kclx) {
-                                        const uint32_t e = xidx[i];
-                                        k2 = ((unsigned long long)(__popc(xcomp[e] & kP) + 1) << 32) |
-                                             (unsigned long long)(0xffffffffu - xrank[e]);
-                                    }
-                                    for (int o = 16; o; o >>= 1) {
-                                        const unsigned long long y = __shfl_xor_sync(FULL, k2, o);
-                                        k2 = y > k2 ? y : k2;
-                                    }
-                                    bx = k2 > bx ? k2 : bx;
-                                }
-                                if ((int)(bx >> 32) - 1 >= bsc) {
-                                    const uint32_t want = 0xffffffffu - (uint32_t)(bx & 0xffffffffull);
-                                    for (int i0 = 0; i0 < kclx; i0 += 32) {
-                                        const int i = i0 + g.lane;
-                                        uint32_t e = 0u;
-                                        bool hit = false;
-                                        if (i < kclx) {
-                                            e = xidx[i];
-                                            hit = xrank[e] == want;
-                                        }
-                                        const unsigned hm = __ballot_sync(FULL, hit);
-                                        if (hm) {
-                                            prow = xcomp[__shfl_sync(FULL, e, __ffs(hm) - 1)];
-                                            break;
-                                        }
+                                    const uint32_t xc = row_at(i0, i);
+                                    const bool cur = i < kclx && (xc & kRc) == kRc;
+                                    const int s = cur ? __popc(xc & kP) + 1 : 0;
+                                    const int sm = (int)__reduce_max_sync(FULL, (unsigned)s);
+                                    if (sm == 0 || sm < xs) continue;
+                                    const uint32_t rk = rank_at(i0, i);
+                                    const uint32_t inv = s == sm ? 0xffffffffu - rk : 0u;
+                                    const uint32_t bi = __reduce_max_sync(FULL, inv);
+                                    if (sm > xs || 0xffffffffu - bi < xk) {
+                                        const unsigned hm = __ballot_sync(FULL, s == sm && inv == bi);
+                                        xrow = __shfl_sync(FULL, xc, __ffs(hm) - 1);
+                                        xk = 0xffffffffu - bi;
+                                        xs = sm;
                                     }
                                 }
+                                if (xs - 1 >= bsc && xs > 0) prow = xrow;
                             }
                             kB = kP & ~prow;
                             pc.stop(PH_PIVOT);
@@ -985,7 +1136,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             kP = __shfl_sync(FULL, ksP, kd);
                             kX = __shfl_sync(FULL, ksX, kd);
                             kB = __shfl_sync(FULL, ksB, kd);
-                            kclx = (int)__shfl_sync(FULL, ksL, kd);
+                            kRc = __shfl_sync(FULL, ksR, kd);
                             kS = __shfl_sync(FULL, ksS, kd);
                             pc.stop(PH_POP);
                             pc.count(PH_POP, 1);
@@ -1002,20 +1153,13 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         const uint64_t mu = __shfl_sync(FULL, kmj, u);
                         const int32_t idu = __shfl_sync(FULL, kid, u);
                         const int szc = kbase + kd + 1;  // |R u {u}|
+                        const uint32_t need = kRc | ubit;  // the child's Rc
                         pc.stop(PH_BRANCH);
                         if (qn <= 2) {
                             t_nodes++;
-                            // the child's X_X rows are this node's rows holding u
-                            auto xx_any = [&](auto f) -> bool {
-                                bool found = false;
-                                for (int i0 = 0; i0 < kclx && !found; i0 += 32) {
-                                    const int i = i0 + g.lane;
-                                    found = __any_sync(FULL, i < kclx && f(xcomp[xidx[i]])) != 0;
-                                }
-                                return found;
-                            };
+                            // the child's X_X rows are the rows holding `need`
                             if (qn == 0) {
-                                if (qx == 0u && !xx_any([&](uint32_t xc) { return ((xc >> u) & 1u) != 0u; }))
+                                if (qx == 0u && !xx_any(need, [](uint32_t) { return true; }))
                                     record(szc, kS + mu, 1, idu, 0, 0);
                             } else if (qn == 1) {
                                 // as for a one-vertex P' in the wide walk
@@ -1023,7 +1167,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                 const uint32_t rw = __shfl_sync(FULL, kRow, w);
                                 if ((qx & rw) == 0u) {
                                     const uint32_t both = ubit | (1u << w);
-                                    const bool found = xx_any([&](uint32_t xc) { return (xc & both) == both; });
+                                    const bool found = xx_any(need, [&](uint32_t xc) { return (xc & both) == both; });
                                     if (!found || !ipx) t_nodes++;
                                     const int32_t idw = __shfl_sync(FULL, kid, w);
                                     if (!found) record(szc + 1, kS + mu + __shfl_sync(FULL, kmj, w), 2, idu, idw, 0);
@@ -1043,14 +1187,11 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                     const int i = i0 + g.lane;
                                     bool h1 = false, h2 = false;
                                     unsigned k1 = 0u;
-                                    if (i < kclx) {
-                                        const uint32_t e = xidx[i];
-                                        const uint32_t xc = xcomp[e];
-                                        if ((xc >> u) & 1u) {
-                                            h1 = ((xc >> w1) & 1u) != 0u;
-                                            h2 = ((xc >> w2) & 1u) != 0u;
-                                            if (ipx && h1 != h2) k1 = ((0x7fffffffu - xrank[e]) << 1) | (h1 ? 1u : 0u);
-                                        }
+                                    const uint32_t xc = row_at(i0, i);
+                                    if (i < kclx && (xc & need) == need) {
+                                        h1 = ((xc >> w1) & 1u) != 0u;
+                                        h2 = ((xc >> w2) & 1u) != 0u;
+                                        if (ipx && h1 != h2) k1 = ((0x7fffffffu - rank_at(i0, i)) << 1) | (h1 ? 1u : 0u);
                                     }
                                     s2x |= __any_sync(FULL, h1 && h2) != 0;
                                     x1 |= __any_sync(FULL, h1) != 0;
@@ -1098,15 +1239,13 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                                     int out = 0;
                                     for (int i0 = 0; i0 < kclx; i0 += 32) {
                                         const int i = i0 + g.lane;
-                                        const uint32_t e = i < kclx ? xidx[i] : 0u;
-                                        const uint32_t xc = i < kclx ? xcomp[e] : 0u;
-                                        const bool surv = i < kclx && ((xc >> u) & 1u) != 0u;
+                                        const uint32_t xc = row_at(i0, i);
+                                        const bool surv = i < kclx && (xc & need) == need;
                                         const unsigned bm = __ballot_sync(FULL, surv);
                                         if (surv) {
                                             const int k = out + __popc(bm & ((1u << g.lane) - 1u));
                                             ra.xcomp[k] = xc;
-                                            ra.xrank[k] = xrank[e];
-                                            ra.xidx[k] = (uint32_t)k;
+                                            ra.xscr[k] = rank_at(i0, i);
                                         }
                                         out += __popc(bm);
                                     }
@@ -1142,16 +1281,16 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             }
                             pc.stop(PH_DONATE);
                         }
-                        // descend
+                        // descend: this node's state goes to lane kd
                         if (g.lane == kd) {
                             ksP = kP;
                             ksX = kX;
                             ksB = kB;
-                            ksL = (uint32_t)kclx;
+                            ksR = kRc;
                             ksS = kS;
                         }
-                        if (kclx > 0) kclx = partition(kclx, [&](uint32_t e) { return ((xcomp[e] >> u) & 1u) != 0u; });
                         if (listing && g.lane == 0) rid[kbase + kd] = (uint32_t)idu;
+                        kRc = need;
                         kP = q;
                         kX = qx;
                         kS += mu;

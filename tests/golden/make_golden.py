@@ -7,6 +7,7 @@ same graph on another machine.
 
     python tests/golden/make_golden.py er_2000 chunglu_1m ...
     python tests/golden/make_golden.py work batch_4096   # adds per-width work to a batch file
+    python tests/golden/make_golden.py roots rmat_22     # per-root results of a banded root sample
 
 Batched workloads (batch_*) store per-graph count, hash, largest size and
 histogram instead (see make_batch). Per single-graph workload, <name>.json holds: fingerprint (n, m, sha256 of row_ptr and
@@ -127,6 +128,54 @@ def make_batch(name, threads=0):
     print(name, total_c, out["hash"], "%.1fs" % out["oracle_seconds"], flush=True)
 
 
+RMAT_BANDS = [(1, 1), (2, 2), (3, 4), (5, 8), (9, 12), (13, 16), (17, 20), (21, 24), (25, 28), (29, 31)]
+
+
+def make_root_sample(name, per_band=40, cost_cap=2e9, threads=0, seed=17):
+    """Per-root oracle results for a seeded sample of roots in every row-width
+    band W = ceil(|P0| / 32) of a graph too large to enumerate whole. Within a
+    band, roots are drawn at random among those whose oracle cost, estimated
+    as |P0|^2 (the root's own pivot scan) plus (Knuth's subtree-size
+    estimate, 16 paths) x |P0|, is at most cost_cap, so that the oracle
+    finishes; each drawn root's count, hash and tree nodes (pivot from P u
+    X_P) are stored."""
+    g = gen.workload(name)
+    core, rank, order, rounds = oracle.peel(g.row_ptr, g.col)
+    outd = later_degree(g, rank)
+    W = (outd + 31) // 32
+    rs = np.random.default_rng(seed)
+    t0 = time.time()
+    chosen, bands = [], {}
+    for lo, hi in RMAT_BANDS:
+        ids = np.nonzero((W >= lo) & (W <= hi))[0].astype(np.int32)
+        if len(ids) == 0:
+            continue
+        cand = np.sort(rs.choice(ids, size=min(len(ids), 8 * per_band), replace=False)).astype(np.int32)
+        est, _ = oracle.tree_estimate(g.row_ptr, g.col, cand, probes=16, seed=seed, threads=threads)
+        p0 = outd[cand].astype(np.float64)
+        ok = cand[p0 * p0 + est * p0 <= cost_cap]
+        pick = np.sort(rs.choice(ok, size=min(len(ok), per_band), replace=False)).astype(np.int32)
+        chosen.append(pick)
+        bands["%d-%d" % (lo, hi)] = {"roots_in_band": int(len(ids)), "drawn": int(len(cand)),
+                                    "within_cap": int(len(ok)), "stored": int(len(pick))}
+        print(name, lo, hi, bands["%d-%d" % (lo, hi)], "%.0fs" % (time.time() - t0), flush=True)
+    roots = np.concatenate(chosen)
+    r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=threads, roots=roots, per_root=True)
+    out = {"workload": name,
+           "source": "CPU oracle (oracle/oracle.c), pivot from P u X_P, per root, on a seeded sample of "
+                     "gen.workload(%r) roots in every row-width band (tests/golden/make_golden.py)" % name,
+           "fingerprint": fingerprint(g), "selection": {"per_band": per_band, "cost_cap": cost_cap,
+                                                        "seed": seed, "bands": bands},
+           "roots": roots.tolist(), "W": W[roots].tolist(),
+           "root_count": r.root_count[roots].astype(np.uint64).tolist(),
+           "root_hash": ["0x%016x" % int(x) for x in r.root_hash[roots]],
+           "root_nodes": r.root_nodes[roots].astype(np.uint64).tolist(),
+           "count": r.count, "hash": "0x%016x" % r.hash, "oracle_seconds": round(time.time() - t0, 1)}
+    with open(os.path.join(HERE, name + "_roots.json"), "w") as f:
+        json.dump(out, f)
+    print(name, "sample of", len(roots), "roots:", r.count, "cliques", "%.0fs" % out["oracle_seconds"])
+
+
 def add_batch_work(name, threads=0):
     """Add the oracle's tree nodes and bitset word-ops per row width W to a
     stored batch file (pivot from P u X_P): the G(n,p) parts by one oracle
@@ -180,6 +229,10 @@ if __name__ == "__main__":
     if args and args[0] == "work":
         for name in args[1:]:
             add_batch_work(name)
+        sys.exit(0)
+    if args and args[0] == "roots":
+        for name in args[1:]:
+            make_root_sample(name)
         sys.exit(0)
     for name in args:
         if name.startswith("batch_"):

@@ -41,6 +41,7 @@ def test_default_opts_without_gpu():
     import paper_2212_01473_gb300 as mce
     o = mce.mce_default_opts()
     assert o.donate_min_p == 0 and o.donate_policy == 1 and o.worker_list == 1 and o.timeout_ms == 60000
+    assert o.run_budget_ms == 600000
     assert o.struct_size == ctypes_sizeof_opts()
 
 

@@ -5,8 +5,10 @@
   oracle), after checking that the generator rebuilt the same graph.
 * rmat_22 (R-MAT scale 22): too heavy for the oracle as a whole, so the peel
   (core numbers and ranks, unique by definition) is compared in full, and the
-  first-level subtrees of seeded samples of roots of several widths are
-  compared one by one (count, hash, tree nodes per root).
+  first-level subtrees of seeded samples of roots are compared one by one
+  (count, hash, tree nodes per root): roots of up to 4 words per row drawn
+  here, and 40 stored roots in every row-width band up to the widest (31
+  words; tests/golden/rmat_22_roots.json, written by the oracle).
 """
 import hashlib
 import json
@@ -96,3 +98,21 @@ def test_rmat_22_sampled_roots(rmat):
     assert np.array_equal(rh[roots], o.root_hash[roots])
     assert np.array_equal(rn[roots], o.root_nodes[roots])
     assert not rc[np.setdiff1d(np.arange(g.n), roots)].any()
+
+
+def test_rmat_22_every_width_band(rmat):
+    # the stored per-root oracle results of 40 seeded roots per band W = 1 ..
+    # 31 (roots whose estimated oracle cost fits a budget), through the launch
+    # configuration of a whole run (all width classes, worker list on)
+    g, core_o, rank_o = rmat
+    with open(os.path.join(GOLDEN, "rmat_22_roots.json")) as f:
+        gold = json.load(f)
+    assert fingerprint(g) == gold["fingerprint"], "generator produced a different graph"
+    roots = np.asarray(gold["roots"], np.int32)
+    assert len(set(gold["W"])) >= 20 and max(gold["W"]) == 31
+    r, (rc, rh, rn) = mce.enumerate_maximal_cliques(g.row_ptr, g.col, per_root=True, roots=roots,
+                                                     pivot=mce.MCE_PIVOT_IP)
+    assert r.count == gold["count"] and "0x%016x" % r.hash == gold["hash"]
+    assert rc[roots].tolist() == gold["root_count"]
+    assert ["0x%016x" % int(x) for x in rh[roots]] == gold["root_hash"]
+    assert rn[roots].tolist() == gold["root_nodes"]

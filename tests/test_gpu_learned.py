@@ -52,7 +52,7 @@ def test_adam_step_matches_reference():
     # (<= lr), plus the rounding of the stored FP32 parameter; entries whose
     # gradient is within 1e-6 of zero can flip direction between two FP32
     # gradient evaluations (atomic summation order), so they are only checked
-    # to move by at most lr.
+    # against Adam's bound on one step.
     p, x, t = _params(3)
     lr = 1e-3
     m = mce.Model(p)
@@ -68,7 +68,10 @@ def test_adam_step_matches_reference():
         tight = np.abs(g.astype(np.float64)) > 1e-6
         tol = 1e-5 * lr + 2.0 ** -22 * np.abs(want)
         assert np.all(d[:omlp.OMEAN][tight[:omlp.OMEAN]] <= tol[:omlp.OMEAN][tight[:omlp.OMEAN]]), step
-        assert np.all(np.abs(got - cur)[:omlp.OMEAN] <= lr * (1 + 1e-5) + 2.0 ** -22 * np.abs(cur[:omlp.OMEAN]))
+        # Adam moves an entry by at most lr (1 - b1) / sqrt(1 - b2) (about 3.2 lr)
+        mv = np.abs(got - cur)[:omlp.OMEAN]
+        bad = np.nonzero(mv > 3.2 * lr + 2.0 ** -22 * np.abs(cur[:omlp.OMEAN]))[0]
+        assert len(bad) == 0, (step, bad[:8], mv[bad[:8]], g[bad[:8]], (want - cur)[bad[:8]])
         assert np.array_equal(got[omlp.OMEAN:], p[omlp.OMEAN:].astype(np.float64))
         cur = got.astype(np.float32)
     m.close()
