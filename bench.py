@@ -52,6 +52,22 @@ def parse():
     return ap.parse_args()
 
 
+def split_workload(name):
+    """'rmat_22_w8' -> ('rmat_22', 8): the first-level subtrees of the roots
+    with at most 8 words per row (|P0| <= 256) of rmat_22; plain names -> (name, None)."""
+    base, _, tail = name.rpartition("_w")
+    if base and tail.isdigit():
+        return base, int(tail)
+    return name, None
+
+
+def subset_roots(outd, max_w):
+    """Input ids of the roots with at most max_w words per row (roots without
+    later neighbours included), int32."""
+    import numpy as np
+    return np.nonzero((outd.astype(np.int64) + 31) // 32 <= max_w)[0].astype(np.int32)
+
+
 def dist_env():
     return int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1")), \
         int(os.environ.get("LOCAL_RANK", "0"))
@@ -154,9 +170,10 @@ def launch_word_ops(word_ops_by_W, wp_lo, wp_hi):
     return sum(v for w, v in word_ops_by_W.items() if int(w) > 0 and wp_lo <= wp_of_words(int(w)) <= wp_hi)
 
 
-def launch_bytes(g, outd, wp_lo, wp_hi):
-    """Algorithmic bytes (BYTES_TEXT) of the roots whose row width falls in
-    width classes wp_lo..wp_hi (roots with |P0| = 0 run in no launch)."""
+def launch_bytes(g, outd, wp_lo, wp_hi, roots=None):
+    """Algorithmic bytes (BYTES_TEXT) of the roots (all, or those listed) whose
+    row width falls in width classes wp_lo..wp_hi (roots with |P0| = 0 run in
+    no launch)."""
     import numpy as np
     deg = np.diff(g.row_ptr).astype(np.int64)
     src = np.repeat(np.arange(g.n, dtype=np.int64), deg)
@@ -165,6 +182,10 @@ def launch_bytes(g, outd, wp_lo, wp_hi):
     cls = np.array([wp_of_words(int(w)) or 0 for w in range(int(W.max()) + 1)])
     wp = cls[W]
     sel = (outd > 0) & (wp >= wp_lo) & (wp <= wp_hi)
+    if roots is not None:
+        keep = np.zeros(g.n, bool)
+        keep[roots] = True
+        sel &= keep
     return 4 * int(per_root[sel].sum())
 
 
@@ -223,15 +244,24 @@ def dominant_launch_ms(mce, h, opts, steps, flush_buf):
     return dom, statistics.mean(same), r
 
 
-def cpu_baseline(g, frac, seed=12345, reps=3, single_frac=None):
-    """The CPU oracle as it stands, on a seeded uniform sample of roots: the
-    median of `reps` runs on every host core, and one single-threaded run on a
-    smaller sample (single_frac, default frac / 10)."""
+def later_degrees(g, rank):
+    """|P0| of every root from a degeneracy rank (numpy)."""
+    import numpy as np
+    src = np.repeat(np.arange(g.n, dtype=np.int64), np.diff(g.row_ptr))
+    return np.bincount(src[rank[g.col] > rank[src]], minlength=g.n)
+
+
+def cpu_baseline(g, frac, seed=12345, reps=3, single_frac=None, pool=None):
+    """The CPU oracle as it stands, on a seeded uniform sample of roots (of
+    `pool`, the workload's root subset, when given): the median of `reps`
+    runs on every host core, and one single-threaded run on a smaller sample
+    (single_frac, default frac / 10)."""
     import numpy as np
     import oracle
     rs = np.random.default_rng(seed)
-    k = max(1, int(round(frac * g.n)))
-    roots = np.sort(rs.choice(g.n, size=k, replace=False)).astype(np.int32)
+    ids = np.arange(g.n, dtype=np.int32) if pool is None else np.asarray(pool, np.int32)
+    k = max(1, int(round(frac * len(ids))))
+    roots = np.sort(rs.choice(ids, size=k, replace=False)).astype(np.int32)
     threads = oracle.default_threads()
     secs, r = [], None
     for _ in range(max(1, reps)):
@@ -241,17 +271,17 @@ def cpu_baseline(g, frac, seed=12345, reps=3, single_frac=None):
     dt = statistics.median(secs)
     out = {"value": r.count / dt, "unit": "cliques/s", "cores": threads, "kind": "oracle", "seconds": dt,
            "sample": "%d of %d roots (%.1f%%, seed %d), %d cliques; median of %d runs of %.2f s each incl. "
-                     "validation, peel and relabelling" % (k, g.n, 100.0 * frac, seed, r.count, len(secs), dt)}
+                     "validation, peel and relabelling" % (k, len(ids), 100.0 * frac, seed, r.count, len(secs), dt)}
     sf = frac / 10 if single_frac is None else single_frac
     if sf > 0:
-        k1 = max(1, int(round(sf * g.n)))
-        roots1 = np.sort(np.random.default_rng(seed + 1).choice(g.n, size=k1, replace=False)).astype(np.int32)
+        k1 = max(1, int(round(sf * len(ids))))
+        roots1 = np.sort(np.random.default_rng(seed + 1).choice(ids, size=k1, replace=False)).astype(np.int32)
         t0 = time.perf_counter()
         r1 = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=1, roots=roots1)
         d1 = time.perf_counter() - t0
         out["single_thread"] = {"value": r1.count / d1, "unit": "cliques/s", "cores": 1, "seconds": d1,
                                 "sample": "%d of %d roots (%.2f%%, seed %d), %d cliques" % (
-                                    k1, g.n, 100.0 * sf, seed + 1, r1.count)}
+                                    k1, len(ids), 100.0 * sf, seed + 1, r1.count)}
     return out
 
 
@@ -260,12 +290,18 @@ def run_reference(args):
     if rank != 0:
         return 0
     import gen
-    g = gen.workload(args.workload)
+    base, max_w = split_workload(args.workload)
+    g = gen.workload(base)
     frac = args.cpu_sample
+    pool = None
+    if max_w is not None:
+        import oracle
+        _, rank, _, _ = oracle.peel(g.row_ptr, g.col)
+        pool = subset_roots(later_degrees(g, rank), max_w)
     vals, secs = [], []
     info = None
     for it in range(args.warmup + args.steps):
-        b = cpu_baseline(g, frac, reps=1, single_frac=0)
+        b = cpu_baseline(g, frac, reps=1, single_frac=0, pool=pool)
         if it >= args.warmup:
             vals.append(b["value"])
             secs.append(b["seconds"])
@@ -427,17 +463,32 @@ def run_ours(args):
         if dist is not None:
             dist.barrier()
 
-    g = gen.workload(args.workload)
+    base, max_w = split_workload(args.workload)
+    g = gen.workload(base)
     rp_d = torch.from_numpy(g.row_ptr).cuda()
     col_d = torch.from_numpy(g.col).cuda()
     flush_buf = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     stream = torch.cuda.current_stream()
 
     pivot = {"auto": mce.MCE_PIVOT_AUTO, "ip": mce.MCE_PIVOT_IP, "ipx": mce.MCE_PIVOT_IPX}[args.pivot]
+    roots_np, roots_d = None, None
+    if max_w is not None:
+        # a root subset: the roots with at most max_w words per row, found once
+        h = mce.mce_create(rp_d, col_d)
+        roots_np = subset_roots(mce.mce_get_order(h)[2], max_w)
+        mce.mce_destroy(h)
+        roots_d = torch.from_numpy(roots_np).cuda()
+
+    def opts(**kw):
+        o = mce.mce_default_opts(**kw)
+        if roots_d is not None:
+            o.roots = roots_d.data_ptr()
+            o.n_roots = len(roots_np)
+        return o
 
     def step():
         h = mce.mce_create(rp_d, col_d)
-        r = mce.mce_run(h, mce.mce_default_opts(pivot=pivot))
+        r = mce.mce_run(h, opts(pivot=pivot))
         st = mce.mce_get_stats(h)
         mce.mce_destroy(h)
         return r, st
@@ -481,7 +532,7 @@ def run_ours(args):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         h = mce.mce_create(rp_h, col_h)
-        r = mce.mce_run(h, mce.mce_default_opts(pivot=pivot), hist_len=hl)
+        r = mce.mce_run(h, opts(pivot=pivot), hist_len=hl)
         t1 = time.perf_counter()
         mce.mce_destroy(h)
         assert r.count == count
@@ -499,15 +550,14 @@ def run_ours(args):
     peaks = measure_peaks()
     h = mce.mce_create(rp_d, col_d)
     _, _, outd = mce.mce_get_order(h)
-    dom, kms, r_ip = dominant_launch_ms(mce, h, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP), args.steps,
-                                        flush_buf)
+    dom, kms, r_ip = dominant_launch_ms(mce, h, opts(pivot=mce.MCE_PIVOT_IP), args.steps, flush_buf)
     mce.mce_destroy(h)
     golden = load_golden(args.workload)
     lo = dom.get("wp_min") or dom["wp"]
     words = None
     if golden and golden.get("count") == count and r_ip.tree_nodes == golden.get("tree_nodes"):
         words = launch_word_ops(golden["word_ops_by_W"], lo, dom["wp"])
-    nbytes = launch_bytes(g, outd, lo, dom["wp"])
+    nbytes = launch_bytes(g, outd, lo, dom["wp"], roots_np)
     bound, legs = roofline_legs(words, nbytes, kms, peaks)
     top = legs[bound]
     roofline = {"bound": bound, "achieved": top["achieved"], "peak": top["peak"], "unit": top["unit"],
@@ -550,10 +600,13 @@ def run_ours(args):
             "clocks": clk, "e2e": e2e, "roofline": roofline}
     if golden:
         line["config"]["oracle_match"] = golden.get("count") == count and golden.get("hash") == "0x%016x" % results[-1].hash
-    if rank == 0 and world == 1 and not args.no_forms:
+    if max_w is not None:
+        line["config"]["roots"] = "the %d roots with at most %d words per row (|P0| <= %d) of %s, isolated " \
+            "vertices included; each step enumerates their first-level subtrees" % (len(roots_np), max_w, 32 * max_w, base)
+    if rank == 0 and world == 1 and not args.no_forms and max_w is None:
         line["forms"] = measure_forms(args, rp_d, col_d, count, value, flush_buf, g, peaks)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(g, args.cpu_sample)
+        line["cpu_baseline"] = cpu_baseline(g, args.cpu_sample, pool=roots_np)
     if rank == 0:
         print(json.dumps(line), flush=True)
     if dist is not None:

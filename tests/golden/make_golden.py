@@ -8,6 +8,7 @@ same graph on another machine.
     python tests/golden/make_golden.py er_2000 chunglu_1m ...
     python tests/golden/make_golden.py work batch_4096   # adds per-width work to a batch file
     python tests/golden/make_golden.py roots rmat_22     # per-root results of a banded root sample
+    python tests/golden/make_golden.py subset rmat_22 8  # every root with at most 8 words per row
 
 Batched workloads (batch_*) store per-graph count, hash, largest size and
 histogram instead (see make_batch). Per single-graph workload, <name>.json holds: fingerprint (n, m, sha256 of row_ptr and
@@ -176,6 +177,42 @@ def make_root_sample(name, per_band=40, cost_cap=2e9, threads=0, seed=17):
     print(name, "sample of", len(roots), "roots:", r.count, "cliques", "%.0fs" % out["oracle_seconds"])
 
 
+def make_subset(name, max_w, threads=0):
+    """Oracle results of every first-level subtree whose root has at most
+    max_w words per row (|P0| <= 32 max_w; roots without later neighbours
+    included): count, hash, histogram, tree nodes and per-width work (pivot
+    from P u X_P), written to <name>_w<max_w>.json."""
+    g = gen.workload(name)
+    core, rank, order, rounds = oracle.peel(g.row_ptr, g.col)
+    outd = later_degree(g, rank)
+    W = (outd + 31) // 32
+    roots = np.nonzero(W <= max_w)[0].astype(np.int32)
+    t0 = time.time()
+    hl = int(outd.max()) + 2
+    r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=threads, roots=roots, hist_len=hl)
+    t_mce = time.time() - t0
+    rn, rw = oracle.work(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=threads, roots=roots)
+    by_w_nodes, by_w_work = {}, {}
+    for w in np.unique(W[roots]):
+        sel = np.zeros(g.n, bool)
+        sel[roots] = True
+        sel &= W == w
+        by_w_nodes[int(w)] = int(rn[sel].astype(np.uint64).sum())
+        by_w_work[int(w)] = int(rw[sel].astype(np.uint64).sum())
+    out = {"workload": "%s_w%d" % (name, max_w),
+           "source": "CPU oracle (oracle/oracle.c), pivot from P u X_P, on the roots of gen.workload(%r) with at "
+                     "most %d words per row" % (name, max_w),
+           "fingerprint": fingerprint(g), "max_w": max_w, "roots": int(len(roots)),
+           "count": r.count, "hash": "0x%016x" % r.hash, "max_size": r.max_size,
+           "hist": [int(x) for x in r.hist], "degeneracy": int(core.max()),
+           "tree_nodes": int(sum(by_w_nodes.values())), "word_ops": int(sum(by_w_work.values())),
+           "nodes_by_W": by_w_nodes, "word_ops_by_W": by_w_work,
+           "oracle_seconds": round(t_mce, 2), "oracle_threads": threads if threads > 0 else oracle.default_threads()}
+    with open(os.path.join(HERE, "%s_w%d.json" % (name, max_w)), "w") as f:
+        json.dump(out, f, indent=1)
+    print(out["workload"], out["count"], out["hash"], "%.1fs" % t_mce, flush=True)
+
+
 def add_batch_work(name, threads=0):
     """Add the oracle's tree nodes and bitset word-ops per row width W to a
     stored batch file (pivot from P u X_P): the G(n,p) parts by one oracle
@@ -229,6 +266,9 @@ if __name__ == "__main__":
     if args and args[0] == "work":
         for name in args[1:]:
             add_batch_work(name)
+        sys.exit(0)
+    if args and args[0] == "subset":
+        make_subset(args[1], int(args[2]))
         sys.exit(0)
     if args and args[0] == "roots":
         for name in args[1:]:
