@@ -403,10 +403,21 @@ def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf, g=None, peak
     ms_b, tot = timed(batched_step, 2)
     hb = mce.mce_batch_create(gp, rp, col)
     tune = mce.mce_autotune(hb, budget_ms=8000.0)
+    # one run with the tuned settings, launched directly: its kernel launches,
+    # and the host time around it beyond its device time
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, rd = mce.mce_run_batch(hb, mce.mce_default_opts(tuned=1))
+    wall_d = (time.perf_counter() - t0) * 1e3
+    launches_direct = mce.mce_get_stats(hb)["kernel_launches"]
     mce.mce_prepare(hb, mce.mce_default_opts(tuned=1))
     mce.mce_run_prepared(hb)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    _, _, rp_ = mce.mce_run_prepared(hb)
+    wall_r = (time.perf_counter() - t0) * 1e3
     ms_r, rr = timed(lambda: mce.mce_run_prepared(hb)[2], 2)
-    assert rr.count == tot.count and rr.hash == tot.hash
+    assert rr.count == tot.count and rr.hash == tot.hash and rd.count == tot.count
     b_roof = None
     if peaks is not None:
         b_roof = form_roofline(mce, hb, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP), b, load_golden("batch_4096"),
@@ -438,6 +449,10 @@ def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf, g=None, peak
                         "replay_value": v_r, "replay_ms": sum(ms_r) / len(ms_r),
                         "replay": "autotuned launch settings, run captured once and replayed as one CUDA graph",
                         "tuning": tune,
+                        "direct": {"kernel_launches": launches_direct, "wall_ms": wall_d,
+                                   "device_ms": rd.ms_traverse, "host_ms": wall_d - rd.ms_traverse},
+                        "replayed": {"graph_launches": 1, "wall_ms": wall_r, "device_ms": rp_.ms_traverse,
+                                     "host_ms": wall_r - rp_.ms_traverse},
                         "one_by_one_value": v_1, "one_by_one_ms": ms_1[0],
                         "vs_one_by_one": v_b / v_1}
     if b_roof is not None:

@@ -122,6 +122,10 @@ typedef struct {
     int64_t run_budget_ms; /* the traversal stops once this much time has passed since its first
                               launch and the run fails with MCE_EBUDGET (default 600000, a safety
                               net that no run of the bundled workloads comes near); 0 = none */
+    int32_t merge_wp;      /* one-warp width classes with rows of at most this many words share one
+                              launch at the widest of them: 12 (default when 0), 4 or 1 (none) */
+    int32_t block_warps;   /* warps per block of every traversal launch: 16 (default when 0), 8 or 4
+                              (never fewer than a group's warps) */
 } mce_opts;
 
 typedef struct {
@@ -206,16 +210,23 @@ int mce_run_batch(mce_graph *g, const mce_opts *opts, mce_result *per_graph, uin
                   int32_t hist_len, mce_result *total);
 
 /*
- * Autotuner: for every width class, times the whole class with a few launch
- * settings (donation threshold max(10, |P0|max/10), max(10, |P0|max/20) and
- * max(10, |P0|max/5); donation rule EITHER, PAPER, ANY; full or
- * one-block-per-SM grid) within about budget_ms of device
- * time, and keeps the fastest per class in the handle. Runs with
- * opts.tuned = 1 then use them. Results are never affected.
+ * Autotuner, within about budget_ms of device time; results never change.
+ * (1) Bitset width of the one-warp width classes (rows of at most 12 words):
+ * their roots run in one launch at the widest row width present, or rows of
+ * 1-4 words share one 4-word launch and 12-word rows run alone, or every
+ * class runs alone at its own width; the fastest over all those roots is
+ * kept. (2) Then launch by launch, a coordinate search from the defaults over
+ * the donation threshold (max(10, |P0|max/10), max(10, |P0|max/20),
+ * max(10, |P0|max/5)), the donation rule (EITHER, PAPER, ANY), the block size
+ * (16, 8 or 4 warps) and the grid (all blocks that fit, or one per SM),
+ * keeping each change that is faster. Runs with opts.tuned = 1 use the result.
  */
 int mce_autotune(mce_graph *g, const mce_opts *base, double budget_ms);
-/* The chosen settings, HOST arrays of 9 width classes (0 / -1 = default). */
-int mce_get_tuning(const mce_graph *g, int32_t *donate_min_p, int32_t *donate_policy, int32_t *blocks);
+/* The chosen settings: HOST arrays of 9 width classes (0 / -1 = default;
+ * warps = warps per block) and *merge_wp = the widest row width (1, 4 or 12)
+ * whose one-warp classes share a launch. Any pointer may be NULL. */
+int mce_get_tuning(const mce_graph *g, int32_t *donate_min_p, int32_t *donate_policy, int32_t *blocks,
+                   int32_t *warps, int32_t *merge_wp);
 
 /*
  * Capture one complete run (every memset and kernel of mce_run / mce_run_batch

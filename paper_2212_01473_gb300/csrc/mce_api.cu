@@ -13,7 +13,7 @@
 
 namespace mce {
 #define MCE_EXTERN_WP(WP)                                                                             \
-    extern template cudaError_t plan_wp<WP>(int, int, int, int, bool, ClassLaunch *);                       \
+    extern template cudaError_t plan_wp<WP>(int, int, int, int, int, bool, ClassLaunch *);                  \
     extern template cudaError_t launch_wp<WP>(const ClassLaunch &, const DevGraph &, const DevOut &,  \
                                               const ClassArgs &, int, cudaStream_t);
 MCE_EXTERN_WP(1)
@@ -26,17 +26,17 @@ MCE_EXTERN_WP(36)
 MCE_EXTERN_WP(68)
 MCE_EXTERN_WP(132)
 
-static cudaError_t plan_class_wp(int wp, int rows, int sms, int smem, int req, bool bh, ClassLaunch *L) {
+static cudaError_t plan_class_wp(int wp, int rows, int sms, int smem, int req, int warps, bool bh, ClassLaunch *L) {
     switch (wp) {
-        case 1: return plan_wp<1>(rows, sms, smem, req, bh, L);
-        case 2: return plan_wp<2>(rows, sms, smem, req, bh, L);
-        case 4: return plan_wp<4>(rows, sms, smem, req, bh, L);
-        case 12: return plan_wp<12>(rows, sms, smem, req, bh, L);
-        case 20: return plan_wp<20>(rows, sms, smem, req, bh, L);
-        case 28: return plan_wp<28>(rows, sms, smem, req, bh, L);
-        case 36: return plan_wp<36>(rows, sms, smem, req, bh, L);
-        case 68: return plan_wp<68>(rows, sms, smem, req, bh, L);
-        case 132: return plan_wp<132>(rows, sms, smem, req, bh, L);
+        case 1: return plan_wp<1>(rows, sms, smem, req, warps, bh, L);
+        case 2: return plan_wp<2>(rows, sms, smem, req, warps, bh, L);
+        case 4: return plan_wp<4>(rows, sms, smem, req, warps, bh, L);
+        case 12: return plan_wp<12>(rows, sms, smem, req, warps, bh, L);
+        case 20: return plan_wp<20>(rows, sms, smem, req, warps, bh, L);
+        case 28: return plan_wp<28>(rows, sms, smem, req, warps, bh, L);
+        case 36: return plan_wp<36>(rows, sms, smem, req, warps, bh, L);
+        case 68: return plan_wp<68>(rows, sms, smem, req, warps, bh, L);
+        case 132: return plan_wp<132>(rows, sms, smem, req, warps, bh, L);
     }
     return cudaErrorInvalidValue;
 }
@@ -174,7 +174,13 @@ struct Tuned {
     int dmp = 0;
     int policy = -1;
     int blocks = 0;
+    int warps = 0;  // warps per block (0 = 16)
 };
+
+// One-warp width classes whose row width is at most this share one launch
+// (default 12: all of them; 4: rows of 1-4 words share one, 12-word rows run
+// alone; 1: every class alone).
+constexpr int kMergeDefault = 12;
 
 struct RunPlan;
 static void free_plan(mce_graph *g, RunPlan *P);
@@ -203,6 +209,7 @@ struct mce_graph {
     uint64_t create_launches = 0;  // kernels launched by create
     mce_stats last{};              // facts of the last run
     Tuned tuned[kNumClasses];      // per width class, from mce_autotune
+    int tuned_merge = kMergeDefault;  // merged one-warp launch width, from mce_autotune
     bool tuned_valid = false;
     struct RunPlan *prepared = nullptr;  // mce_prepare
     cudaGraphExec_t prepared_exec = nullptr;
@@ -537,7 +544,7 @@ static void free_plan(mce_graph *g, RunPlan *P) {
 
 // class_mask: bit c set = launch width class c (bit kNumClasses: roots with |P0| = 0)
 static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, const Tuned *tune_override,
-                    RunPlan **out) {
+                    RunPlan **out, int merge_override = 0) {
     *out = nullptr;
     if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
     RunPlan *P = new RunPlan();
@@ -557,6 +564,10 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     else if (opts.tuned && !g->tuned_valid) rc = fail(MCE_EINVAL, "opts.tuned set but mce_autotune has not run on this handle");
     else if (opts.subtree_level < 0 || opts.subtree_level > 2) rc = fail(MCE_EINVAL, "bad opts.subtree_level");
     else if (opts.run_budget_ms < 0) rc = fail(MCE_EINVAL, "opts.run_budget_ms < 0");
+    else if (opts.merge_wp != 0 && opts.merge_wp != 1 && opts.merge_wp != 4 && opts.merge_wp != 12)
+        rc = fail(MCE_EINVAL, "opts.merge_wp must be 0, 1, 4 or 12");
+    else if (opts.block_warps != 0 && opts.block_warps != 4 && opts.block_warps != 8 && opts.block_warps != 16)
+        rc = fail(MCE_EINVAL, "opts.block_warps must be 0, 4, 8 or 16");
     if (rc != MCE_OK) { delete P; return rc; }
     if (opts.timeout_ms <= 0) opts.timeout_ms = 60000;
     P->level2 = opts.subtree_level == 2;
@@ -648,10 +659,13 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     // widest of them, its roots first: the narrow classes' roots fill the
     // groups that would otherwise idle at the end of each separate launch.
     {
+        const int merge_wp = merge_override > 0 ? merge_override
+                             : opts.merge_wp > 0 ? opts.merge_wp
+                             : (opts.tuned ? g->tuned_merge : kMergeDefault);
         int top = -1, nmerge = 0;
         int64_t total = 0;
         for (int c = kNumClasses - 1; c >= 0; c--) {
-            if (P->counts[c] == 0 || class_wp(c) > 12) continue;
+            if (P->counts[c] == 0 || class_wp(c) > std::min(12, merge_wp)) continue;
             if (top < 0) top = c;
             nmerge++;
             total += P->counts[c];
@@ -664,7 +678,7 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
             if (!lst) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
             int64_t at = 0;
             for (int c = top; c >= 0; c--) {
-                if (P->counts[c] == 0 || class_wp(c) > 12) continue;
+                if (P->counts[c] == 0 || class_wp(c) > std::min(12, merge_wp)) continue;
                 CK(cudaMemcpyAsync(lst + at, P->lists[c], (size_t)P->counts[c] * 4, cudaMemcpyDeviceToDevice, g->stream));
                 at += P->counts[c];
                 if (c != top) P->counts[c] = 0;
@@ -684,7 +698,8 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         k.x_cap = c == P->merged_top ? P->merged_xcap : g->class_x[c];
         k.wp_min = c == P->merged_top ? P->merged_wp_min : class_wp(c);
         const int blocks = (t && t->blocks > 0) ? t->blocks : opts.blocks;
-        CK(plan_class_wp(class_wp(c), k.rows, g->sm_count, g->smem_optin, blocks, g->gid == nullptr, &k.L));
+        const int warps = (t && t->warps > 0) ? t->warps : opts.block_warps;
+        CK(plan_class_wp(class_wp(c), k.rows, g->sm_count, g->smem_optin, blocks, warps, g->gid == nullptr, &k.L));
         k.groups = k.L.blocks * (k.L.warps_per_block / k.L.gw);
         const size_t aw = arena_words(k.L.wp, k.rows, k.x_cap, k.L.a_global, stack_in_smem(k.L.wp));
         const size_t idle_words = ((size_t)k.groups + 31) / 32;
@@ -959,60 +974,137 @@ extern "C" int mce_run_prepared(mce_graph *g, mce_result *per_graph, uint64_t *h
     return collect_run(g, g->prepared, per_graph, hist, hist_len, total);
 }
 
-// Try launch settings per width class on the whole class and keep the
-// fastest: donation threshold, donation rule, block count.
+// Time one run of the classes in `mask` with these settings (device time of
+// the traversal launches); a failed run returns a negative time.
+static double time_setting(mce_graph *g, const mce_opts *base, unsigned mask, const Tuned *over, int merge_wp,
+                           int *rc_out) {
+    RunPlan *P = nullptr;
+    int rc = plan_run(g, base, mask, over, &P, merge_wp);
+    double ms = -1.0;
+    if (rc == MCE_OK) {
+        rc = enqueue_run(g, P);
+        if (rc == MCE_OK) {
+            mce_result tot{};
+            rc = collect_run(g, P, nullptr, nullptr, 0, &tot);
+            if (rc == MCE_OK) ms = tot.ms_traverse;
+        }
+        free_plan(g, P);
+    }
+    *rc_out = rc;
+    return ms;
+}
+
+// The autotuner (config of the batched form: bitset width and block size are
+// tuned). (1) Bitset width of the one-warp classes: their roots run in one
+// launch at the widest of their row widths, or rows of 1-4 words share a
+// 4-word launch and 12-word rows run alone, or each class runs alone at its
+// own width; the fastest over all one-warp roots is kept. (2) Then, launch by
+// launch, a coordinate search from the defaults over the donation threshold
+// (|P0|max / 10, / 20, / 5, never below 10), the donation rule (EITHER,
+// PAPER, ANY), the warps per block (16, 8, 4) and the grid (all blocks that
+// fit, or one per SM), keeping each change that is faster. Results never
+// depend on any of these.
 extern "C" int mce_autotune(mce_graph *g, const mce_opts *base, double budget_ms) {
     if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
+    int rc = MCE_OK;
+    double spent = 0;
+    const double budget = budget_ms > 0 ? budget_ms : 1e300;
     Tuned over[kNumClasses];
-    for (int c = 0; c < kNumClasses; c++) {
-        g->tuned[c] = Tuned{};
+    for (int c = 0; c < kNumClasses; c++) g->tuned[c] = Tuned{};
+    g->tuned_merge = kMergeDefault;
+    unsigned one_warp = 0;
+    int n_one = 0;
+    for (int c = 0; c < kNumClasses; c++)
+        if (g->class_count[c] > 0 && class_wp(c) <= 12) {
+            one_warp |= 1u << c;
+            n_one++;
+        }
+    // (1) bitset width of the one-warp launch
+    if (n_one > 1) {
+        double best = 1e300;
+        for (int mw : {12, 4, 1}) {
+            const double ms = time_setting(g, base, one_warp, nullptr, mw, &rc);
+            if (rc != MCE_OK) return rc;
+            spent += ms;
+            if (ms < best) {
+                best = ms;
+                g->tuned_merge = mw;
+            }
+        }
+    }
+    // (2) launch by launch: the leading class of each launch and the classes it carries
+    for (int c = kNumClasses - 1; c >= 0; c--) {
         if (g->class_count[c] == 0) continue;
+        unsigned mask = 1u << c;
+        if (class_wp(c) <= 12) {
+            const int mw = std::min(12, g->tuned_merge);
+            if (class_wp(c) <= mw) {
+                // the widest merged class leads the launch; the others ride along
+                bool leads = true;
+                for (int q = c + 1; q < kNumClasses; q++)
+                    if (g->class_count[q] > 0 && class_wp(q) <= mw) leads = false;
+                if (!leads) continue;
+                for (int q = 0; q < c; q++)
+                    if (g->class_count[q] > 0) mask |= 1u << q;
+            }
+        }
         const int rows = g->class_rows[c];
         const int A = std::max(10, rows / 10);
-        const Tuned cands[] = {{A, MCE_DONATE_EITHER, 0},
-                               {std::max(10, rows / 20), MCE_DONATE_EITHER, 0},
-                               {std::max(10, rows / 5), MCE_DONATE_EITHER, 0},
-                               {A, MCE_DONATE_PAPER, 0},
-                               {A, MCE_DONATE_ANY, 0},
-                               {A, MCE_DONATE_EITHER, g->sm_count}};
-        double best_ms = 1e300, spent = 0;
-        const double share = budget_ms > 0 ? budget_ms / kNumClasses : 1e300;
-        for (const Tuned &t : cands) {
-            for (int q = 0; q < kNumClasses; q++) over[q] = Tuned{};
+        Tuned best_t{A, MCE_DONATE_EITHER, 0, 0};
+        for (int q = 0; q < kNumClasses; q++) over[q] = Tuned{};
+        over[c] = best_t;
+        double best = time_setting(g, base, mask, over, g->tuned_merge, &rc);
+        if (rc != MCE_OK) return rc;
+        spent += best;
+        auto attempt = [&](Tuned t) -> int {
+            if (spent > budget) return MCE_OK;
             over[c] = t;
-            RunPlan *P = nullptr;
-            int rc = plan_run(g, base, 1u << c, over, &P);
+            const double ms = time_setting(g, base, mask, over, g->tuned_merge, &rc);
             if (rc != MCE_OK) return rc;
-            rc = enqueue_run(g, P);
-            if (rc == MCE_OK) {
-                mce_result tot{};
-                rc = collect_run(g, P, nullptr, nullptr, 0, &tot);
-                if (rc == MCE_OK) {
-                    const double ms = tot.ms_traverse;
-                    spent += ms;
-                    if (ms < best_ms) {
-                        best_ms = ms;
-                        g->tuned[c] = t;
-                    }
-                }
+            spent += ms;
+            if (ms < best) {
+                best = ms;
+                best_t = t;
             }
-            free_plan(g, P);
-            if (rc != MCE_OK) return rc;
-            if (spent > share) break;
+            return MCE_OK;
+        };
+        for (int d : {std::max(10, rows / 20), std::max(10, rows / 5)}) {
+            Tuned t = best_t;
+            t.dmp = d;
+            if ((rc = attempt(t)) != MCE_OK) return rc;
         }
+        for (int pol : {MCE_DONATE_PAPER, MCE_DONATE_ANY}) {
+            Tuned t = best_t;
+            t.policy = pol;
+            if ((rc = attempt(t)) != MCE_OK) return rc;
+        }
+        for (int w : {8, 4}) {
+            Tuned t = best_t;
+            t.warps = w;
+            if (w >= group_warps(class_wp(c)) && (rc = attempt(t)) != MCE_OK) return rc;
+        }
+        {
+            Tuned t = best_t;
+            t.blocks = g->sm_count;
+            if ((rc = attempt(t)) != MCE_OK) return rc;
+        }
+        g->tuned[c] = best_t;
     }
     g->tuned_valid = true;
     return MCE_OK;
 }
 
-extern "C" int mce_get_tuning(const mce_graph *g, int32_t *donate_min_p, int32_t *donate_policy, int32_t *blocks) {
+extern "C" int mce_get_tuning(const mce_graph *g, int32_t *donate_min_p, int32_t *donate_policy, int32_t *blocks,
+                              int32_t *warps, int32_t *merge_wp) {
     if (!g) return fail(MCE_EINVAL, "graph handle is NULL");
     if (!g->tuned_valid) return fail(MCE_EINVAL, "mce_autotune has not run on this handle");
     for (int c = 0; c < kNumClasses; c++) {
         if (donate_min_p) donate_min_p[c] = g->tuned[c].dmp;
         if (donate_policy) donate_policy[c] = g->tuned[c].policy;
         if (blocks) blocks[c] = g->tuned[c].blocks;
+        if (warps) warps[c] = g->tuned[c].warps;
     }
+    if (merge_wp) *merge_wp = g->tuned_merge;
     return MCE_OK;
 }
 

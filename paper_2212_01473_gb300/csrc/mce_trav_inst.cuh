@@ -14,12 +14,13 @@ __host__ __device__ constexpr bool a_in_global(int wp) { return wp == 12 || wp >
 __host__ __device__ constexpr bool stack_in_smem(int wp) { return wp <= 4; }
 
 template <int WP>
-cudaError_t plan_wp(int rows, int sm_count, int max_smem_optin, int requested_blocks, bool block_hist,
-                    ClassLaunch *L) {
+cudaError_t plan_wp(int rows, int sm_count, int max_smem_optin, int requested_blocks, int requested_warps,
+                    bool block_hist, ClassLaunch *L) {
     constexpr int GW = group_warps(WP);
     constexpr bool AG = a_in_global(WP);
     const GrpSmem lay = grp_smem_layout(WP, GW, rows, AG, stack_in_smem(WP), block_hist);
-    int gpb = 16 / GW;
+    // groups per block: 16 warps by default, or the requested warps (a multiple of the group width)
+    int gpb = (requested_warps >= GW && requested_warps <= 16 ? requested_warps : 16) / GW;
     while (gpb > 1 && smem_bytes(lay, gpb) > (size_t)max_smem_optin) gpb--;
     if (smem_bytes(lay, gpb) > (size_t)max_smem_optin) return cudaErrorInvalidConfiguration;
     L->wp = WP;
@@ -59,7 +60,7 @@ cudaError_t launch_wp(const ClassLaunch &L, const DevGraph &g, const DevOut &o, 
 }
 
 #define MCE_INSTANTIATE_WP(WP)                                                                        \
-    template cudaError_t plan_wp<WP>(int, int, int, int, bool, ClassLaunch *);                              \
+    template cudaError_t plan_wp<WP>(int, int, int, int, int, bool, ClassLaunch *);                         \
     template cudaError_t launch_wp<WP>(const ClassLaunch &, const DevGraph &, const DevOut &,         \
                                        const ClassArgs &, int, cudaStream_t);
 

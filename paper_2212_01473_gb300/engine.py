@@ -49,7 +49,7 @@ class mce_opts(ctypes.Structure):
                 ("root_hash", ctypes.c_void_p), ("root_nodes", ctypes.c_void_p),
                 ("root_priority", ctypes.c_void_p), ("roots", ctypes.c_void_p),
                 ("n_roots", ctypes.c_int64), ("tuned", ctypes.c_int32), ("subtree_level", ctypes.c_int32),
-                ("run_budget_ms", ctypes.c_int64)]
+                ("run_budget_ms", ctypes.c_int64), ("merge_wp", ctypes.c_int32), ("block_warps", ctypes.c_int32)]
 
 
 class mce_result(ctypes.Structure):
@@ -97,7 +97,7 @@ def library():
         lib.mce_get_order.argtypes = [vp, i32p, i32p, i32p]
         lib.mce_get_stats.argtypes = [vp, ctypes.POINTER(mce_stats)]
         lib.mce_autotune.argtypes = [vp, ctypes.POINTER(mce_opts), ctypes.c_double]
-        lib.mce_get_tuning.argtypes = [vp, i32p, i32p, i32p]
+        lib.mce_get_tuning.argtypes = [vp, i32p, i32p, i32p, i32p, i32p]
         lib.mce_prepare.argtypes = [vp, ctypes.POINTER(mce_opts)]
         lib.mce_run_prepared.argtypes = [vp, ctypes.POINTER(mce_result), u64p, i32, ctypes.POINTER(mce_result)]
         lib.mce_peel_noalloc.argtypes = [vp, vp, i32, i64, vp, vp, vp, vp]
@@ -289,9 +289,11 @@ def mce_run_batch(h: Handle, opts: Optional[mce_opts] = None, hist_len: Optional
 def mce_autotune(h: Handle, opts: Optional[mce_opts] = None, budget_ms: float = 5000.0) -> dict:
     """Pick launch settings per width class (see include/mce.h); returns them."""
     _check(library().mce_autotune(h.ptr, ctypes.byref(opts) if opts is not None else None, budget_ms))
-    d, p, b = (ctypes.c_int32 * 9)(), (ctypes.c_int32 * 9)(), (ctypes.c_int32 * 9)()
-    _check(library().mce_get_tuning(h.ptr, d, p, b))
-    return {"donate_min_p": list(d), "donate_policy": list(p), "blocks": list(b)}
+    d, p, b, w = ((ctypes.c_int32 * 9)() for _ in range(4))
+    mw = ctypes.c_int32()
+    _check(library().mce_get_tuning(h.ptr, d, p, b, w, ctypes.byref(mw)))
+    return {"donate_min_p": list(d), "donate_policy": list(p), "blocks": list(b), "warps": list(w),
+            "merge_wp": mw.value}
 
 
 def mce_prepare(h: Handle, opts: Optional[mce_opts] = None):

@@ -66,11 +66,15 @@ def test_autotune_changes_schedule_only():
     h = mce.mce_create(g.row_ptr, g.col)
     plain = mce.mce_run(h)
     t = mce.mce_autotune(h, budget_ms=2000.0)
-    assert len(t["donate_min_p"]) == 9
+    assert len(t["donate_min_p"]) == 9 and len(t["warps"]) == 9 and t["merge_wp"] in (1, 4, 12)
     tuned = mce.mce_run(h, mce.mce_default_opts(tuned=1))
+    # every bitset width of the one-warp launch and every block size the tuner may pick
+    others = [mce.mce_run(h, mce.mce_default_opts(merge_wp=mw, block_warps=bw))
+              for mw in (1, 4, 12) for bw in (4, 8, 16)]
     mce.mce_destroy(h)
-    assert (tuned.count, tuned.hash, tuned.tree_nodes) == (plain.count, plain.hash, plain.tree_nodes)
-    assert np.array_equal(tuned.hist, plain.hist)
+    for r in [tuned] + others:
+        assert (r.count, r.hash, r.tree_nodes) == (plain.count, plain.hash, plain.tree_nodes)
+        assert np.array_equal(r.hist, plain.hist)
 
 
 @pytest.mark.skipif(not os.path.exists(os.path.join(GOLDEN, "batch_4096.json")), reason="no stored results")
