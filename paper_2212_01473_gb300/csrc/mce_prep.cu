@@ -159,15 +159,22 @@ __device__ void block_bitonic(int *a, int len) {
 // Segments longer than kSmallSort are put in id order here through a bitmap;
 // shorter ones, and all final ranks, are done by k_peel_rank afterwards.
 //
-// Once the live graph is small (live degree sum, live vertices and the
-// level's S within kCoreDegrees, kCoreLive and kCoreS), every block returns at
-// a level start and k_peel_core finishes the peel in one block: the dense
-// core's many short sub-rounds are barrier-bound, and a block barrier and
-// shared-memory degree counters cost far less than a grid barrier and global
-// atomics. Removal order and core numbers are the same either way.
-constexpr long long kCoreDegrees = 1ll << 22;
-constexpr int kCoreLive = 32768;
-constexpr int kCoreS = 1024;
+// As the remaining graph shrinks, fewer blocks go on. A level start may narrow
+// the grid when the live degree sum, the live vertices and the level's S are
+// all small: at most kNarrowDegrees, kNarrowLive and kNarrowS. Blocks
+// kNarrowBlocks and up then return, and the rest meet at cheaper barriers (the
+// dense core's many short sub-rounds are barrier-bound). Within kSoloDegrees,
+// kSoloLive and kSoloS, block 0 finishes alone with block barriers. A warp
+// removes one vertex at a time, so the stage must not start while S sets of
+// thousands of vertices can still come: the live vertices bound every later
+// S. Removal order and core numbers are the same either way.
+constexpr long long kNarrowDegrees = 1ll << 22;
+constexpr int kNarrowBlocks = 16;
+constexpr int kNarrowLive = 2 * kNarrowBlocks * kPeelThreads;
+constexpr int kNarrowS = 2 * kNarrowBlocks * (kPeelThreads / 32);
+constexpr long long kSoloDegrees = 32768;
+constexpr int kSoloLive = 2 * kPeelThreads;
+constexpr int kSoloS = 2 * (kPeelThreads / 32);
 // adjacency lists longer than this are removed by a whole block
 constexpr int kHeavyDeg = 64;
 
@@ -178,14 +185,21 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                                                        PeelCtl *ctl, int *status, uint64_t timeout_ns) {
     __shared__ int sh[64];
     __shared__ long long shl[32];
-    const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int64_t nth = (int64_t)gridDim.x * blockDim.x;
+    int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    const int64_t gwarp = tid >> 5, nwarps = nth >> 5;
-    const int nblocks = gridDim.x, bid = blockIdx.x;
-    const unsigned nbar = gridDim.x;  // blocks meeting at grid barriers
+    int64_t gwarp = tid >> 5, nwarps = nth >> 5;
+    int nblocks = gridDim.x, bid = blockIdx.x;
+    bool solo = false;
+    unsigned nbar = gridDim.x;  // blocks meeting at grid barriers
     GridBar *gbar = &ctl->bar;
-    auto barrier = [&]() -> bool { return grid_barrier(gbar, status, timeout_ns, nbar); };
+    auto barrier = [&]() -> bool {
+        if (solo) {
+            __syncthreads();
+            return true;
+        }
+        return grid_barrier(gbar, status, timeout_ns, nbar);
+    };
 
     for (int64_t v = tid; v < n; v += nth) {
         deg[v] = rp[v + 1] - rp[v];
@@ -271,23 +285,29 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         }
         k = guess;
         guess = k + 1;
-        // every block reads the same sum after the barrier and decides alike:
-        // once the live graph is small, the rest of the peel runs in one block
-        // (k_peel_core), whose barriers are block barriers and whose degrees
-        // live in shared memory
+        // every block reads the same sum after the barrier and decides alike
         const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[ls];
         const int nlive = nrem + ns;
-        if (live <= kCoreDegrees && nlive <= kCoreLive && ns <= kCoreS) {
-            if (bid == 0 && threadIdx.x == 0) {
-                ctl->h_k = k;
-                ctl->h_next = next;
-                ctl->h_nrem = nrem;
-                ctl->h_remsel = remsel ? 1 : 0;
-                ctl->h_t = t;
-                ctl->h_ns = ns;
-                ctl->h_on = 1;
-            }
-            return;
+        const bool to_solo = !solo && live <= kSoloDegrees && nlive <= kSoloLive && ns <= kSoloS;
+        if (!solo && !to_solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && nlive <= kNarrowLive &&
+            ns <= kNarrowS) {
+            if (blockIdx.x >= kNarrowBlocks) return;
+            nbar = kNarrowBlocks;
+            nblocks = kNarrowBlocks;
+            tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+            nth = (int64_t)kNarrowBlocks * blockDim.x;
+            gwarp = tid >> 5;
+            nwarps = nth >> 5;
+        }
+        if (to_solo) {
+            if (blockIdx.x != 0) return;
+            solo = true;
+            tid = threadIdx.x;
+            nth = blockDim.x;
+            gwarp = tid >> 5;
+            nwarps = nth >> 5;
+            nblocks = 1;
+            bid = 0;
         }
 
         // sub-rounds at level k
@@ -393,161 +413,6 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         }
     }
     if (bid == 0 && threadIdx.x == 0) {
-        ctl->next = next;
-        ctl->rounds = t;
-        ctl->k = k;
-    }
-}
-
-// The peel's dense core in one block (see kCoreDegrees). It continues from
-// the hand-off state in ctl: the level start at core h_k has put its S into
-// order[h_next, h_next + h_ns), and the remaining live vertices are the
-// h_nrem entries of remA (h_remsel = 0) or remB. Each live vertex gets a local
-// id: its degree moves to shared memory (ldeg) and rank[v] = -(id + 2) marks it
-// live there (removed vertices have rank 0, as in k_peel, until k_peel_rank
-// writes the final ranks). Sub-rounds and level starts follow k_peel: a
-// vertex joins the next sub-round when its degree falls from k + 1 to k, and a
-// level start takes k = the smallest live degree and S = the live vertices of
-// that degree. Segments longer than kSmallSort are put in id order here
-// through the bitmap; shorter ones by k_peel_rank.
-__global__ void __launch_bounds__(kPeelThreads) k_peel_core(int n, const int32_t *rp, const int32_t *col,
-                                                            const int32_t *deg, int32_t *rank, int32_t *core,
-                                                            int32_t *order, const int32_t *remA,
-                                                            const int32_t *remB, int32_t *lvid, int32_t *segstart,
-                                                            unsigned *bitmap, PeelCtl *ctl) {
-    extern __shared__ int ldeg[];                 // [kCoreLive] degrees by local id
-    __shared__ unsigned gone[kCoreLive / 32];     // removed local ids
-    __shared__ int sh[64];
-    __shared__ int s_cnt;
-    if (vload(&ctl->h_on) == 0) return;  // k_peel finished the whole peel
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    constexpr int NW = kPeelThreads / 32;
-    int k = ctl->h_k, next = ctl->h_next, t = ctl->h_t, ns = ctl->h_ns;
-    const int nrem = ctl->h_nrem;
-    const int32_t *rem = ctl->h_remsel ? remB : remA;
-    const int nl = nrem + ns;  // local ids: [0, nrem) the remaining list, then this level's S
-    for (int i = tid; i < kCoreLive / 32; i += kPeelThreads) gone[i] = 0u;
-    __syncthreads();
-    for (int i = tid; i < nl; i += kPeelThreads) {
-        const int v = i < nrem ? rem[i] : order[next + i - nrem];
-        lvid[i] = v;
-        ldeg[i] = deg[v];
-        if (i < nrem) rank[v] = -(i + 2);
-        else atomicOr(&gone[i >> 5], 1u << (i & 31));
-    }
-    if (tid == 0) s_cnt = 0;
-    __syncthreads();
-    // one removed edge endpoint u: its degree falls by one, and it joins the
-    // next sub-round when that takes it from k + 1 to k
-    auto dec = [&](bool valid, int u, int32_t *S2) {
-        bool push = false;
-        int lid = 0;
-        if (valid) {
-            const int rk = rank[u];
-            if (rk < -1) {
-                lid = -rk - 2;
-                push = atomicSub(&ldeg[lid], 1) == k + 1;
-            }
-        }
-        const unsigned b = __ballot_sync(0xffffffffu, push);
-        int base = 0;
-        if (lane == 0 && b) base = atomicAdd(&s_cnt, __popc(b));
-        base = __shfl_sync(0xffffffffu, base, 0);
-        if (push) {
-            const int p = base + __popc(b & ((1u << lane) - 1u));
-            rank[u] = 0;
-            core[u] = k;
-            S2[p] = u;
-            atomicOr(&gone[lid >> 5], 1u << (lid & 31));
-        }
-    };
-    for (;;) {
-        // sub-rounds at level k
-        while (ns > 0) {
-            if (tid == 0) segstart[t] = next;
-            int32_t *S = order + next;
-            if (ns > kSmallSort) {
-                // ascending id: mark the bitmap, then each thread takes a chunk of its words
-                for (int i = tid; i < ns; i += kPeelThreads) atomicOr(&bitmap[S[i] >> 5], 1u << (S[i] & 31));
-                __syncthreads();
-                const int nw = (n + 31) >> 5;
-                const int chunk = (nw + kPeelThreads - 1) / kPeelThreads;
-                const int w_lo = min(nw, tid * chunk), w_hi = min(nw, w_lo + chunk);
-                int c = 0;
-                for (int w = w_lo; w < w_hi; w++) c += __popc(bitmap[w]);
-                int tot;
-                int pos = block_scan_excl<kPeelThreads>(c, sh, &tot);
-                __syncthreads();  // every S[i] was read before any is overwritten
-                for (int w = w_lo; w < w_hi; w++) {
-                    unsigned bits = bitmap[w];
-                    while (bits) {
-                        const int bb = __ffs(bits) - 1;
-                        bits &= bits - 1;
-                        S[pos++] = w * 32 + bb;
-                    }
-                    bitmap[w] = 0u;
-                }
-                __syncthreads();
-            }
-            int32_t *S2 = S + ns;
-            // a vertex of degree <= kHeavyDeg is one warp's work; longer lists are strided over the block
-            for (int i = warp; i < ns; i += NW) {
-                const int v = S[i];
-                const int b = rp[v], e = rp[v + 1];
-                if (e - b > kHeavyDeg) continue;
-                for (int j0 = b; j0 < e; j0 += 32) {
-                    const int j = j0 + lane;
-                    dec(j < e, j < e ? col[j] : 0, S2);
-                }
-            }
-            for (int i = 0; i < ns; i++) {
-                const int v = S[i];
-                const int b = rp[v], e = rp[v + 1];
-                if (e - b <= kHeavyDeg) continue;
-                for (int j0 = b; j0 < e; j0 += kPeelThreads) {
-                    const int j = j0 + tid;
-                    dec(j < e, j < e ? col[j] : 0, S2);
-                }
-            }
-            __syncthreads();
-            next += ns;
-            t++;
-            ns = s_cnt;
-            __syncthreads();
-            if (tid == 0) s_cnt = 0;
-        }
-        if (next >= n) break;
-        // level start: k = the smallest live degree, S = the live vertices of that degree
-        int lmin = INT_MAX;
-        for (int i = tid; i < nl; i += kPeelThreads)
-            if (!((gone[i >> 5] >> (i & 31)) & 1u)) lmin = min(lmin, ldeg[i]);
-        lmin = block_reduce_min<kPeelThreads>(lmin, sh);
-        if (lmin == INT_MAX) break;  // cannot happen while next < n
-        k = max(k, lmin);
-        int32_t *S = order + next;
-        for (int i0 = 0; i0 < nl; i0 += kPeelThreads) {
-            const int i = i0 + tid;
-            bool in = false;
-            if (i < nl && !((gone[i >> 5] >> (i & 31)) & 1u) && ldeg[i] <= k) in = true;
-            const unsigned bm = __ballot_sync(0xffffffffu, in);
-            int base = 0;
-            if (lane == 0 && bm) base = atomicAdd(&s_cnt, __popc(bm));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (in) {
-                const int v = lvid[i];
-                S[base + __popc(bm & ((1u << lane) - 1u))] = v;
-                rank[v] = 0;
-                core[v] = k;
-                atomicOr(&gone[i >> 5], 1u << (i & 31));
-            }
-        }
-        __syncthreads();
-        ns = s_cnt;
-        __syncthreads();
-        if (tid == 0) s_cnt = 0;
-        __syncthreads();
-    }
-    if (tid == 0) {
         ctl->next = next;
         ctl->rounds = t;
         ctl->k = k;
@@ -904,13 +769,6 @@ cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &
     count_launch();
     e = cudaLaunchCooperativeKernel((void *)k_peel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
     if (e != cudaSuccess) return e;
-    // the dense core, when k_peel handed it off (otherwise the kernel returns at once)
-    const size_t core_smem = (size_t)kCoreLive * sizeof(int);
-    e = cudaFuncSetAttribute(k_peel_core, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)core_smem);
-    if (e != cudaSuccess) return e;
-    k_peel_core<<<1, kPeelThreads, core_smem, s>>>(n, rp, col, b.deg, b.rank, b.core, b.order, b.remA, b.remB, b.SB,
-                                                   segstart, b.bitmap, b.ctl);
-    count_launch();
     k_peel_rank<<<2 * sm_count, kRankThreads, 0, s>>>(n, segstart, b.ctl, b.order, b.rank);
     count_launch();
     return cudaGetLastError();
@@ -928,7 +786,6 @@ __global__ void k_peel_init(PeelCtl *ctl, int n) {
     }
     ctl->bar.count = 0;
     ctl->bar.gen = 0;
-    ctl->h_on = 0;
 }
 
 cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s) {

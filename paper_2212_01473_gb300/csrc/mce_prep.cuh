@@ -11,15 +11,12 @@ struct PeelCtl {
     int minval[3];        // smallest live degree at a level start, by level % 3
     unsigned long long sumdeg[3];  // live degree sum at a level start, by level % 3
     GridBar bar;
-    // hand-off to k_peel_core (h_on = 1): the state at a level start whose
-    // S = order[h_next, h_next + h_ns) has just been removed at core h_k
-    int h_on, h_k, h_next, h_nrem, h_remsel, h_t, h_ns;
 };
 
 struct PeelBufs {
     int32_t *deg, *rank, *core, *order, *remA, *remB;
     int32_t *SA;  // n ints: start of each removal sub-round in order
-    int32_t *SB;  // n ints: the vertex of each local id of the dense core (k_peel_core)
+    int32_t *SB;  // unused
     unsigned *bitmap;  // ceil(n/32) words, zero on entry and on exit
     int *blocksums;    // max_blocks
     PeelCtl *ctl;

@@ -161,10 +161,20 @@ def evaluate(model, families=FAMILIES, seeds=EVAL_SEEDS, repeats=3, log=print):
             full = model.predict(E.mce_root_features(h))  # every root, for the accuracy figures
             pred = priority(model, h)                     # what the ordering uses
             torch.cuda.synchronize()
+            # the priority pass itself (features + network for the scored roots)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            priority(model, h)
+            e1.record()
+            e1.synchronize()
+            ms_priority = e0.elapsed_time(e1)
+            _, rank, _ = E.mce_get_order(h)
             t, p = truth.cpu().numpy(), full.cpu().numpy()
             heavy = t > 1.0
             row = {"family": fam, "seed": s, "mse": float(np.mean((p - t) ** 2)),
-                   "spearman": spearman(p, t), "spearman_nontrivial": spearman(p[heavy], t[heavy]) if heavy.sum() > 2 else None}
+                   "spearman": spearman(p, t), "spearman_nontrivial": spearman(p[heavy], t[heavy]) if heavy.sum() > 2 else None,
+                   "spearman_rank_nontrivial": spearman(rank[heavy], t[heavy]) if heavy.sum() > 2 else None,
+                   "ms_priority": ms_priority}
             for name, pr in (("plain", None), ("learned", pred), ("true", truth)):
                 ms = []
                 for _ in range(repeats):
@@ -184,7 +194,7 @@ def evaluate(model, families=FAMILIES, seeds=EVAL_SEEDS, repeats=3, log=print):
 
 def main(argv=None):
     ap = argparse.ArgumentParser()
-    ap.add_argument("cmd", choices=["train", "eval"])
+    ap.add_argument("cmd", choices=["train", "eval", "reeval"])
     ap.add_argument("--out", default=DEFAULT_MODEL)
     ap.add_argument("--model", default=DEFAULT_MODEL)
     ap.add_argument("--epochs", type=int, default=4)
@@ -203,6 +213,12 @@ def main(argv=None):
                 "collect_s": round(t1 - t0, 1), "train_s": round(t2 - t1, 2), "eval": rows}
         save(model, args.out, meta)
         print(json.dumps({"saved": args.out, "samples": int(len(label)), "train_s": round(t2 - t1, 2)}))
+    elif args.cmd == "reeval":
+        # the held-out evaluation again, with the current engine, stored in the model file
+        model, meta = load(args.model)
+        meta["eval"] = evaluate(model)
+        meta["eval_note"] = "held-out seeds re-evaluated with the current traversal kernel"
+        save(model, args.model, meta)
     else:
         model, meta = load(args.model)
         evaluate(model)

@@ -651,45 +651,44 @@ def test_multipartite_enumeration(k, size, first):
 
 
 def peel_stage_passes(g):
-    """The GPU peel's stage at every level of g, from the oracle.
+    """The GPU peel's stage at every level-start pass of g, from the oracle.
 
-    The peel runs on the full grid until a level start whose live degree sum
-    is at most 2^22, live vertices at most 32,768 and S at most 1,024
-    vertices; from that level on one block finishes it. On the full grid a
-    level start guesses k + 1; when no live vertex has that degree, one more
-    pass runs first. At level k the live vertices are those of core number
-    >= k, and S holds those with at most k live neighbours. Returns (stage of
-    each level, stage of each level whose k jumped past k + 1); 0 = full grid,
-    1 = one block.
+    A level start of the GPU peel narrows the grid to 16 blocks when the live
+    degree sum is at most 2^22, the live vertices at most 32,768 and its S at
+    most 1,024 vertices; it goes to one block (checked first) at most 32,768,
+    2,048 and 64. It guesses k + 1; when no live vertex has that degree, one
+    more pass runs first, in the stage of the level before. At level k the
+    live vertices are those of core number >= k, and S holds those with at
+    most k live neighbours. Returns (stage of each level, stage of each extra
+    pass); 0, 1, 2 = full grid, 16 blocks, one block.
     """
     core = oracle.peel(g.row_ptr, g.col)[0]
     src = np.repeat(np.arange(g.n), g.degrees())
-    stage, levels, jumps, prev = 0, [], [], -1
+    stage, levels, extra, prev = 0, [], [], -1
     for k in np.unique(core):
         live_v = core >= k
         both = live_v[src] & live_v[g.col]
         ldeg = np.bincount(src[both], minlength=g.n)
         live_sum, nlive = int(both.sum()), int(live_v.sum())
         s_size = int((live_v & (ldeg <= k)).sum())
-        jumped = k > prev + 1
-        if stage == 0 and jumped:
-            jumps.append(0)  # the guess missed: one more pass on the full grid
-        if stage == 0 and live_sum <= (1 << 22) and nlive <= 32768 and s_size <= 1024:
+        if k > prev + 1:
+            extra.append(stage)
+        if stage < 2 and live_sum <= 32768 and nlive <= 2048 and s_size <= 64:
+            stage = 2
+        elif stage == 0 and live_sum <= (1 << 22) and nlive <= 32768 and s_size <= 1024:
             stage = 1
-        elif stage == 1 and jumped:
-            jumps.append(1)
         levels.append(stage)
         prev = int(k)
-    return levels, jumps
+    return levels, extra
 
 
 def test_peel_stages_graph_spans_every_stage():
-    # gen.peel_stages() must run levels in both stages of the GPU peel, with
-    # k jumping past k + 1 in each
+    # gen.peel_stages() must run levels in all three stages of the GPU peel
+    # and make the extra level-start pass in each
     g = gen.peel_stages()
-    levels, jumps = peel_stage_passes(g)
-    assert set(levels) == {0, 1}
-    assert set(jumps) == {0, 1}
+    levels, extra = peel_stage_passes(g)
+    assert set(levels) == {0, 1, 2}
+    assert set(extra) == {0, 1, 2}
     assert int(g.degrees().min()) > 0
 
 
