@@ -218,7 +218,7 @@ def main(argv=None):
         model, meta = load(args.model)
         meta["eval"] = evaluate(model)
         meta["eval_note"] = "held-out seeds re-evaluated with the current traversal kernel"
-        save(model, args.model, meta)
+        save(model, args.out, meta)
     else:
         model, meta = load(args.model)
         evaluate(model)
