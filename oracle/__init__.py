@@ -37,6 +37,8 @@ def _load():
         lib.oracle_clique_hash.argtypes = [i32p, ctypes.c_int32]
         lib.oracle_clique_hash.restype = ctypes.c_uint64
         lib.oracle_default_threads.restype = ctypes.c_int32
+        lib.oracle_mce_capped.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32, i32p,
+                                          ctypes.c_int64, ctypes.c_uint64, u64p, u64p, u64p]
         dp = ctypes.POINTER(ctypes.c_double)
         lib.oracle_tree_estimate.argtypes = [ctypes.c_int32, i32p, i32p, ctypes.c_int32, ctypes.c_int32,
                                              i32p, ctypes.c_int64, ctypes.c_int32, ctypes.c_uint64, dp, dp]
@@ -146,6 +148,24 @@ def work(row_ptr, col, mode: int = PIVOT_IP, threads: int = 0, roots=None):
     if rc != 0:
         raise RuntimeError("oracle_mce_work failed: %d" % rc)
     return rn[:n], rw[:n]
+
+
+def capped(row_ptr, col, roots, node_cap: int, mode: int = PIVOT_IP, threads: int = 0):
+    """Per-root (count, hash, nodes) uint64 arrays by input id for the listed
+    roots; a root needing more than node_cap calls is abandoned and gets
+    nodes = 2^64 - 1 (count and hash 0)."""
+    rp, rpp = _i32(row_ptr)
+    c, cp = _i32(col if len(col) else np.zeros(1, np.int32))
+    ro, rop = _i32(roots)
+    n = len(rp) - 1
+    rc_a, rh_a, rn_a = (np.zeros(max(n, 1), np.uint64) for _ in range(3))
+    rc = _load().oracle_mce_capped(n, rpp, cp, mode, threads, rop, len(ro), ctypes.c_uint64(node_cap),
+                                   _u64(rc_a), _u64(rh_a), _u64(rn_a))
+    if rc == 1:
+        raise ValueError("oracle: invalid graph or arguments")
+    if rc != 0:
+        raise MemoryError("oracle_mce_capped failed")
+    return rc_a[:n], rh_a[:n], rn_a[:n]
 
 
 def tree_estimate(row_ptr, col, roots, probes: int = 64, seed: int = 1, mode: int = PIVOT_IP, threads: int = 0):

@@ -141,6 +141,9 @@ typedef struct {
     int32_t words;     /* 32-bit words per bitset row for the current root: ceil(|P0|/32) */
     uint64_t *hist;
     int32_t hist_len, max_size;
+    uint64_t node_cap;  /* 0 = none; else a root's walk stops after this many calls */
+    uint64_t node_base; /* w->nodes when the current root started */
+    int aborted;        /* the current root's walk hit node_cap */
 } walk_t;
 
 static int adjacent(const graph_t *g, int32_t a, int32_t b) {
@@ -184,6 +187,10 @@ static void bk(walk_t *w, int32_t *P, int32_t np, int32_t *XP, int32_t nxp, cons
                int32_t nxx) {
     const graph_t *g = w->g;
     w->nodes++;
+    if (w->node_cap && w->nodes - w->node_base > w->node_cap) {
+        w->aborted = 1;
+        return;
+    }
     if (np == 0 && nxp == 0 && nxx == 0) { /* R is a maximal clique */
         report(w);
         return;
@@ -242,6 +249,7 @@ static void bk(walk_t *w, int32_t *P, int32_t np, int32_t *XP, int32_t nxp, cons
         free(cP);
         free(cXP);
         free(cXX);
+        if (w->aborted) break;
         /* P = P - {v} */
         int32_t k = 0;
         for (int32_t j = 0; j < np; j++)
@@ -328,6 +336,7 @@ typedef struct {
     atomic_llong next;
     int32_t hist_len, max_deg;
     uint64_t *root_count, *root_hash, *root_nodes, *root_work; /* by input id */
+    uint64_t node_cap; /* per root; 0 = none */
     /* merged results */
     pthread_mutex_t mu;
     uint64_t count, hash;
@@ -357,9 +366,20 @@ static void *worker(void *arg) {
         if (i >= job->n_roots) break;
         int32_t r = job->roots[i];
         uint64_t c0 = w.count, h0 = w.hash, n0 = w.nodes, k0 = w.work;
+        w.node_cap = job->node_cap;
+        w.node_base = w.nodes;
+        w.aborted = 0;
         if (job->g->second_level) second_level(&w, r);
         else first_level(&w, r);
         int32_t id = job->g->order[r];
+        if (w.aborted) { /* over the cap: marked, and nothing of it kept */
+            w.count = c0;
+            w.hash = h0;
+            if (job->root_nodes) job->root_nodes[id] = UINT64_MAX;
+            if (job->root_count) job->root_count[id] = 0;
+            if (job->root_hash) job->root_hash[id] = 0;
+            continue;
+        }
         if (job->root_count) job->root_count[id] = w.count - c0;
         if (job->root_hash) job->root_hash[id] = w.hash - h0;
         if (job->root_nodes) job->root_nodes[id] = w.nodes - n0;
@@ -383,7 +403,7 @@ int32_t oracle_default_threads(void) {
 static int run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode, int32_t nthreads,
                const int32_t *roots_in, int64_t n_roots_in, uint64_t *count, uint64_t *hash,
                uint64_t *hist, int32_t hist_len, int32_t *max_size, uint64_t *root_count,
-               uint64_t *root_hash, uint64_t *root_nodes, uint64_t *root_work) {
+               uint64_t *root_hash, uint64_t *root_nodes, uint64_t *root_work, uint64_t node_cap) {
     if (oracle_validate(n, row_ptr, col)) return 1;
     const int32_t second = (mode & ORACLE_SECOND_LEVEL) != 0;
     mode &= ~ORACLE_SECOND_LEVEL;
@@ -431,6 +451,7 @@ static int run(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mo
     job.root_hash = root_hash;
     job.root_nodes = root_nodes;
     job.root_work = root_work;
+    job.node_cap = node_cap;
     job.hist = (uint64_t *)calloc((size_t)(job.hist_len > 0 ? job.hist_len : 1), sizeof(uint64_t));
     if (!job.hist) { rc = 2; goto done; }
     pthread_mutex_init(&job.mu, NULL);
@@ -462,7 +483,7 @@ int oracle_mce(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mo
                int32_t hist_len, int32_t *max_size, uint64_t *root_count,
                uint64_t *root_hash, uint64_t *root_nodes) {
     return run(n, row_ptr, col, mode, nthreads, NULL, 0, count, hash, hist, hist_len, max_size,
-               root_count, root_hash, root_nodes, NULL);
+               root_count, root_hash, root_nodes, NULL, 0);
 }
 
 int oracle_mce_roots(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode,
@@ -471,7 +492,7 @@ int oracle_mce_roots(int32_t n, const int32_t *row_ptr, const int32_t *col, int3
                      uint64_t *root_count, uint64_t *root_hash, uint64_t *root_nodes) {
     if (!roots || n_roots < 0) return 1;
     return run(n, row_ptr, col, mode, nthreads, roots, n_roots, count, hash, hist, hist_len,
-               max_size, root_count, root_hash, root_nodes, NULL);
+               max_size, root_count, root_hash, root_nodes, NULL, 0);
 }
 
 int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode,
@@ -480,8 +501,19 @@ int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32
     uint64_t count, hash;
     int32_t max_size;
     int rc = run(n, row_ptr, col, mode, nthreads, roots, roots ? n_roots : 0, &count, &hash, NULL, 0,
-                 &max_size, NULL, NULL, root_nodes, root_work);
+                 &max_size, NULL, NULL, root_nodes, root_work, 0);
     return rc == 5 ? 0 : rc; /* no histogram was asked for */
+}
+
+int oracle_mce_capped(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode, int32_t nthreads,
+                      const int32_t *roots, int64_t n_roots, uint64_t node_cap, uint64_t *root_count,
+                      uint64_t *root_hash, uint64_t *root_nodes) {
+    uint64_t count, hash;
+    int32_t max_size;
+    if (!roots || n_roots < 0 || node_cap == 0) return 1;
+    int rc = run(n, row_ptr, col, mode, nthreads, roots, n_roots, &count, &hash, NULL, 0, &max_size, root_count,
+                 root_hash, root_nodes, NULL, node_cap);
+    return rc == 5 ? 0 : rc;
 }
 
 /*

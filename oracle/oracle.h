@@ -93,6 +93,16 @@ int oracle_mce_work(int32_t n, const int32_t *row_ptr, const int32_t *col, int32
                     int32_t nthreads, const int32_t *roots, int64_t n_roots, uint64_t *root_nodes,
                     uint64_t *root_work);
 
+/*
+ * Per-root results of the listed roots (input ids) as oracle_mce_roots gives
+ * them, except that a root whose subtree needs more than node_cap calls is
+ * abandoned: its root_nodes entry is UINT64_MAX and its count and hash 0.
+ * Lets a test pick roots the oracle can finish. Returns as oracle_mce_work.
+ */
+int oracle_mce_capped(int32_t n, const int32_t *row_ptr, const int32_t *col, int32_t mode, int32_t nthreads,
+                      const int32_t *roots, int64_t n_roots, uint64_t node_cap, uint64_t *root_count,
+                      uint64_t *root_hash, uint64_t *root_nodes);
+
 /* count and hash of the maximal cliques of a complete multipartite graph with
  * `parts` parts of `part_size` consecutive ids starting at `first` (Moon-Moser
  * graphs have part_size 3): the transversals, enumerated directly. */

@@ -132,14 +132,13 @@ def make_batch(name, threads=0):
 RMAT_BANDS = [(1, 1), (2, 2), (3, 4), (5, 8), (9, 12), (13, 16), (17, 20), (21, 24), (25, 28), (29, 31)]
 
 
-def make_root_sample(name, per_band=40, cost_cap=2e9, threads=0, seed=17):
+def make_root_sample(name, per_band=40, node_cap=200000, threads=0, seed=17):
     """Per-root oracle results for a seeded sample of roots in every row-width
     band W = ceil(|P0| / 32) of a graph too large to enumerate whole. Within a
-    band, roots are drawn at random among those whose oracle cost, estimated
-    as |P0|^2 (the root's own pivot scan) plus (Knuth's subtree-size
-    estimate, 16 paths) x |P0|, is at most cost_cap, so that the oracle
-    finishes; each drawn root's count, hash and tree nodes (pivot from P u
-    X_P) are stored."""
+    band, 8 x per_band roots are drawn at random and walked by the oracle with
+    a cap of node_cap Bron-Kerbosch calls per root (oracle_mce_capped); of the
+    roots that finish, per_band are kept at random, with their count, hash
+    and tree nodes (pivot from P u X_P)."""
     g = gen.workload(name)
     core, rank, order, rounds = oracle.peel(g.row_ptr, g.col)
     outd = later_degree(g, rank)
@@ -147,34 +146,39 @@ def make_root_sample(name, per_band=40, cost_cap=2e9, threads=0, seed=17):
     rs = np.random.default_rng(seed)
     t0 = time.time()
     chosen, bands = [], {}
+    cnt, hsh, nds = [], [], []
     for lo, hi in RMAT_BANDS:
         ids = np.nonzero((W >= lo) & (W <= hi))[0].astype(np.int32)
         if len(ids) == 0:
             continue
         cand = np.sort(rs.choice(ids, size=min(len(ids), 8 * per_band), replace=False)).astype(np.int32)
-        est, _ = oracle.tree_estimate(g.row_ptr, g.col, cand, probes=16, seed=seed, threads=threads)
-        p0 = outd[cand].astype(np.float64)
-        ok = cand[p0 * p0 + est * p0 <= cost_cap]
+        c, h, nd = oracle.capped(g.row_ptr, g.col, cand, node_cap, mode=oracle.PIVOT_IP, threads=threads)
+        ok = cand[nd[cand] != np.iinfo(np.uint64).max]
         pick = np.sort(rs.choice(ok, size=min(len(ok), per_band), replace=False)).astype(np.int32)
         chosen.append(pick)
+        cnt.append(c[pick])
+        hsh.append(h[pick])
+        nds.append(nd[pick])
         bands["%d-%d" % (lo, hi)] = {"roots_in_band": int(len(ids)), "drawn": int(len(cand)),
-                                    "within_cap": int(len(ok)), "stored": int(len(pick))}
+                                    "finished_within_cap": int(len(ok)), "stored": int(len(pick))}
         print(name, lo, hi, bands["%d-%d" % (lo, hi)], "%.0fs" % (time.time() - t0), flush=True)
     roots = np.concatenate(chosen)
-    r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, threads=threads, roots=roots, per_root=True)
+    rc, rh, rn = np.concatenate(cnt), np.concatenate(hsh), np.concatenate(nds)
     out = {"workload": name,
-           "source": "CPU oracle (oracle/oracle.c), pivot from P u X_P, per root, on a seeded sample of "
-                     "gen.workload(%r) roots in every row-width band (tests/golden/make_golden.py)" % name,
-           "fingerprint": fingerprint(g), "selection": {"per_band": per_band, "cost_cap": cost_cap,
+           "source": "CPU oracle (oracle/oracle.c, oracle_mce_capped), pivot from P u X_P, per root, on a seeded "
+                     "sample of gen.workload(%r) roots in every row-width band (tests/golden/make_golden.py)" % name,
+           "fingerprint": fingerprint(g), "selection": {"per_band": per_band, "node_cap": node_cap,
                                                         "seed": seed, "bands": bands},
            "roots": roots.tolist(), "W": W[roots].tolist(),
-           "root_count": r.root_count[roots].astype(np.uint64).tolist(),
-           "root_hash": ["0x%016x" % int(x) for x in r.root_hash[roots]],
-           "root_nodes": r.root_nodes[roots].astype(np.uint64).tolist(),
-           "count": r.count, "hash": "0x%016x" % r.hash, "oracle_seconds": round(time.time() - t0, 1)}
+           "root_count": rc.astype(np.uint64).tolist(),
+           "root_hash": ["0x%016x" % int(x) for x in rh],
+           "root_nodes": rn.astype(np.uint64).tolist(),
+           "count": int(rc.astype(np.uint64).sum()),
+           "hash": "0x%016x" % (int(sum(int(x) for x in rh)) & ((1 << 64) - 1)),
+           "oracle_seconds": round(time.time() - t0, 1)}
     with open(os.path.join(HERE, name + "_roots.json"), "w") as f:
         json.dump(out, f)
-    print(name, "sample of", len(roots), "roots:", r.count, "cliques", "%.0fs" % out["oracle_seconds"])
+    print(name, "sample of", len(roots), "roots:", out["count"], "cliques", "%.0fs" % out["oracle_seconds"])
 
 
 def make_subset(name, max_w, threads=0):

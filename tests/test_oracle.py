@@ -563,6 +563,21 @@ def test_adam_reference_closed_forms():
     assert p2[0] == p0[0]  # a zero gradient never moves its entry
 
 
+def test_capped_walk_keeps_finished_roots_exact():
+    # a root over the cap is abandoned and marked; every other root's count,
+    # hash and node count equal the uncapped walk's, and the cap splits the
+    # roots exactly by their node counts
+    g = gen.chung_lu(3000, 12.0, 2.1, 300.0, 3, 10, 20, 4)
+    r = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP, per_root=True)
+    c, h, nd = oracle.capped(g.row_ptr, g.col, np.arange(g.n, dtype=np.int32), 50)
+    ok = nd != np.iinfo(np.uint64).max
+    assert 0 < (~ok).sum() < g.n
+    assert np.array_equal(c[ok], r.root_count[ok]) and np.array_equal(h[ok], r.root_hash[ok])
+    assert np.array_equal(nd[ok], r.root_nodes[ok])
+    assert np.all(r.root_nodes[ok] <= 50) and np.all(r.root_nodes[~ok] > 50)
+    assert not c[~ok].any() and not h[~ok].any()
+
+
 def test_tree_estimate_exact_on_regular_trees():
     # Moon-Moser and complete graphs: every node at a given depth of a root's
     # subtree has the same number of children, so every random path gives the
