@@ -132,13 +132,16 @@ def make_batch(name, threads=0):
 RMAT_BANDS = [(1, 1), (2, 2), (3, 4), (5, 8), (9, 12), (13, 16), (17, 20), (21, 24), (25, 28), (29, 31)]
 
 
-def make_root_sample(name, per_band=40, node_cap=200000, threads=0, seed=17):
+def make_root_sample(name, per_band=40, node_cap=200000, wide_from=9, wide_draw=48, wide_cap=4000000, threads=0,
+                     seed=17):
     """Per-root oracle results for a seeded sample of roots in every row-width
     band W = ceil(|P0| / 32) of a graph too large to enumerate whole. Within a
-    band, 8 x per_band roots are drawn at random and walked by the oracle with
-    a cap of node_cap Bron-Kerbosch calls per root (oracle_mce_capped); of the
-    roots that finish, per_band are kept at random, with their count, hash
-    and tree nodes (pivot from P u X_P)."""
+    band, 8 x per_band roots are drawn at random (wide_draw in the bands from
+    W = wide_from on, whose subtrees are far larger) and walked by the oracle
+    with a cap of node_cap (wide_cap) Bron-Kerbosch calls per root
+    (oracle_mce_capped); of the roots that finish, per_band are kept at
+    random, with their count, hash and tree nodes (pivot from P u X_P). A band
+    where no drawn root finishes is left out."""
     g = gen.workload(name)
     core, rank, order, rounds = oracle.peel(g.row_ptr, g.col)
     outd = later_degree(g, rank)
@@ -151,8 +154,11 @@ def make_root_sample(name, per_band=40, node_cap=200000, threads=0, seed=17):
         ids = np.nonzero((W >= lo) & (W <= hi))[0].astype(np.int32)
         if len(ids) == 0:
             continue
-        cand = np.sort(rs.choice(ids, size=min(len(ids), 8 * per_band), replace=False)).astype(np.int32)
-        c, h, nd = oracle.capped(g.row_ptr, g.col, cand, node_cap, mode=oracle.PIVOT_IP, threads=threads)
+        wide = lo >= wide_from
+        draw = wide_draw if wide else 8 * per_band
+        cand = np.sort(rs.choice(ids, size=min(len(ids), draw), replace=False)).astype(np.int32)
+        c, h, nd = oracle.capped(g.row_ptr, g.col, cand, wide_cap if wide else node_cap, mode=oracle.PIVOT_IP,
+                                 threads=threads)
         ok = cand[nd[cand] != np.iinfo(np.uint64).max]
         pick = np.sort(rs.choice(ok, size=min(len(ok), per_band), replace=False)).astype(np.int32)
         chosen.append(pick)
@@ -168,7 +174,8 @@ def make_root_sample(name, per_band=40, node_cap=200000, threads=0, seed=17):
            "source": "CPU oracle (oracle/oracle.c, oracle_mce_capped), pivot from P u X_P, per root, on a seeded "
                      "sample of gen.workload(%r) roots in every row-width band (tests/golden/make_golden.py)" % name,
            "fingerprint": fingerprint(g), "selection": {"per_band": per_band, "node_cap": node_cap,
-                                                        "seed": seed, "bands": bands},
+                                                        "wide_from": wide_from, "wide_draw": wide_draw,
+                                                        "wide_cap": wide_cap, "seed": seed, "bands": bands},
            "roots": roots.tolist(), "W": W[roots].tolist(),
            "root_count": rc.astype(np.uint64).tolist(),
            "root_hash": ["0x%016x" % int(x) for x in rh],

@@ -132,10 +132,15 @@ def test_training_reduces_loss_and_keeps_results():
 
 @pytest.mark.skipif(not os.path.exists(learn.DEFAULT_MODEL), reason="no trained model file")
 def test_trained_model_on_held_out_seed():
+    # a held-out Chung-Lu graph: the network ranks subtree sizes well, every
+    # order gives the same cliques (evaluate() checks count and hash), and the
+    # measured effect of the order is reported. On this family the effect is
+    # within box noise for the learned and even for the true sizes (the worker
+    # list rebalances), so the test bounds it instead of asserting a gain.
     model, meta = learn.load()
-    rows = learn.evaluate(model, families=("chunglu_1m",), seeds=(101,), repeats=2, log=lambda *a: None)
+    rows = learn.evaluate(model, families=("chunglu_1m",), seeds=(101,), repeats=3, log=print)
     model.close()
     r = rows[0]
-    assert r["spearman"] > 0.5
-    # the learned order must not lose to the plain order by more than noise
-    assert r["ms_learned"] <= 1.10 * r["ms_plain"]
+    assert r["spearman"] > 0.85 and r["spearman_nontrivial"] > 0.8
+    assert r["ms_learned"] <= 1.05 * r["ms_plain"] and r["ms_true"] <= 1.05 * r["ms_plain"]
+    assert r["ms_priority"] < 0.2 * r["ms_plain"]
