@@ -206,6 +206,8 @@ struct mce_graph {
     size_t scratch_bytes = 0;
     double ms_prep = 0;
     int64_t peel_rounds = 0;
+    double peel_stage_ms[3] = {0, 0, 0};
+    int32_t peel_stage_rounds[3] = {0, 0, 0};
     uint64_t create_launches = 0;  // kernels launched by create
     mce_stats last{};              // facts of the last run
     Tuned tuned[kNumClasses];      // per width class, from mce_autotune
@@ -393,6 +395,19 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
         if (h_status & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "degeneracy peel timed out"); goto cleanup; }
         if (hctl.next != n) { rc = fail(MCE_ECUDA, "peel ended early (%d of %d ranked)", hctl.next, n); goto cleanup; }
         g->peel_rounds = hctl.rounds;
+        {
+            // time and sub-rounds of each peel stage (full grid, 16 blocks, one block)
+            const unsigned long long te = hctl.t_end, tn = hctl.t_narrow ? hctl.t_narrow : te,
+                                     ts = hctl.t_solo ? hctl.t_solo : te;
+            const int rn = hctl.r_narrow >= 0 ? hctl.r_narrow : hctl.rounds,
+                      rs = hctl.r_solo >= 0 ? hctl.r_solo : hctl.rounds;
+            g->peel_stage_ms[0] = (double)(std::min(tn, ts) - hctl.t_start) / 1e6;
+            g->peel_stage_ms[1] = hctl.t_narrow ? (double)(ts - tn) / 1e6 : 0.0;
+            g->peel_stage_ms[2] = hctl.t_solo ? (double)(te - ts) / 1e6 : 0.0;
+            g->peel_stage_rounds[0] = std::min(rn, rs);
+            g->peel_stage_rounds[1] = hctl.r_narrow >= 0 ? rs - rn : 0;
+            g->peel_stage_rounds[2] = hctl.r_solo >= 0 ? hctl.rounds - rs : 0;
+        }
 
         // -------------------------------------------------------- orientation
         g->outdeg = dnew<int32_t>(g, nn, nullptr);
@@ -865,6 +880,10 @@ static int collect_run(mce_graph *g, RunPlan *P, mce_result *per_graph, uint64_t
     }
     st.kernel_launches = g->create_launches + (P->replay ? 0 : P->plan_launches) + P->run_launches;
     st.peel_rounds = g->peel_rounds;
+    for (int i = 0; i < 3; i++) {
+        st.peel_stage_ms[i] = g->peel_stage_ms[i];
+        st.peel_stage_rounds[i] = g->peel_stage_rounds[i];
+    }
     g->last = st;
     if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms with no progress", (long long)P->opts.timeout_ms); goto cleanup; }
     if (hflags[1] & ST_BUDGET) { rc = fail(MCE_EBUDGET, "the run exceeded its time budget of %lld ms", (long long)P->opts.run_budget_ms); goto cleanup; }

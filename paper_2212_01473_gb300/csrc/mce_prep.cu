@@ -201,6 +201,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         return grid_barrier(gbar, status, timeout_ns, nbar);
     };
 
+    if (tid == 0) ctl->t_start = globaltimer_ns();
     for (int64_t v = tid; v < n; v += nth) {
         deg[v] = rp[v + 1] - rp[v];
         rank[v] = -1;
@@ -292,6 +293,10 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         if (!solo && !to_solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && nlive <= kNarrowLive &&
             ns <= kNarrowS) {
             if (blockIdx.x >= kNarrowBlocks) return;
+            if (blockIdx.x == 0 && threadIdx.x == 0) {
+                ctl->t_narrow = globaltimer_ns();
+                ctl->r_narrow = t;
+            }
             nbar = kNarrowBlocks;
             nblocks = kNarrowBlocks;
             tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -301,6 +306,10 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         }
         if (to_solo) {
             if (blockIdx.x != 0) return;
+            if (threadIdx.x == 0) {
+                ctl->t_solo = globaltimer_ns();
+                ctl->r_solo = t;
+            }
             solo = true;
             tid = threadIdx.x;
             nth = blockDim.x;
@@ -416,6 +425,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         ctl->next = next;
         ctl->rounds = t;
         ctl->k = k;
+        ctl->t_end = globaltimer_ns();
     }
 }
 
@@ -786,6 +796,8 @@ __global__ void k_peel_init(PeelCtl *ctl, int n) {
     }
     ctl->bar.count = 0;
     ctl->bar.gen = 0;
+    ctl->t_start = ctl->t_narrow = ctl->t_solo = ctl->t_end = 0ull;
+    ctl->r_narrow = ctl->r_solo = -1;
 }
 
 cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s) {

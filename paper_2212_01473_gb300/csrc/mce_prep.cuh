@@ -11,6 +11,10 @@ struct PeelCtl {
     int minval[3];        // smallest live degree at a level start, by level % 3
     unsigned long long sumdeg[3];  // live degree sum at a level start, by level % 3
     GridBar bar;
+    // globaltimer (ns) at the start, at the narrow and one-block stages (0 if
+    // never reached) and at the end, by block 0; stage sub-rounds likewise
+    unsigned long long t_start, t_narrow, t_solo, t_end;
+    int r_narrow, r_solo;
 };
 
 struct PeelBufs {
