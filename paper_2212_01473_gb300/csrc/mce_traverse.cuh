@@ -356,7 +356,10 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
     g.warp = wib % GW;
     g.lane = threadIdx.x & 31;
     g.gl = g.warp * 32 + g.lane;
-    const bool block_hist = G.gid == nullptr;
+    // one clique-size histogram per block (single graph, multi-warp groups) or
+    // per group: one-warp groups record cliques too often to share one through
+    // shared-memory atomics, and batched runs flush per graph
+    const bool block_hist = G.gid == nullptr && GW > 1;
     const GrpSmem L = grp_smem_layout(WP, GW, rows_cap, AG, stack_smem != 0, block_hist);
     unsigned long long *bhist = (unsigned long long *)(smem_raw + L.block_hist);
     if (block_hist) {
