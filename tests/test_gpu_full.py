@@ -116,3 +116,23 @@ def test_rmat_22_every_width_band(rmat):
     assert rc[roots].tolist() == gold["root_count"]
     assert ["0x%016x" % int(x) for x in rh[roots]] == gold["root_hash"]
     assert rn[roots].tolist() == gold["root_nodes"]
+
+
+def test_rmat_22_w4_subset_matches_stored_oracle(rmat):
+    # the bench's rmat_22_w4 workload: every root with at most 4 words per
+    # row (|P0| <= 128), isolated vertices included, enumerated whole, in the
+    # launch configuration bench.py uses, against the stored oracle result
+    g, core_o, rank_o = rmat
+    with open(os.path.join(GOLDEN, "rmat_22_w4.json")) as f:
+        gold = json.load(f)
+    assert fingerprint(g) == gold["fingerprint"], "generator produced a different graph"
+    src = np.repeat(np.arange(g.n, dtype=np.int64), g.degrees())
+    later = np.bincount(src[rank_o[g.col] > rank_o[src]], minlength=g.n)
+    roots = np.nonzero((later + 31) // 32 <= 4)[0].astype(np.int32)
+    assert len(roots) == gold["roots"]
+    for pivot in (mce.MCE_PIVOT_IP, mce.MCE_PIVOT_AUTO):
+        r = mce.enumerate_maximal_cliques(g.row_ptr, g.col, roots=roots, pivot=pivot)
+        assert (r.count, "0x%016x" % r.hash, r.max_size) == (gold["count"], gold["hash"], gold["max_size"])
+        assert r.hist.tolist() == gold["hist"]
+        if pivot == mce.MCE_PIVOT_IP:
+            assert r.tree_nodes == gold["tree_nodes"]
