@@ -101,35 +101,41 @@ __device__ inline int idle_wait(int *flag, const int *active, int *status, const
 }
 
 // Grid-wide barrier for a cooperatively launched (all blocks co-resident)
-// kernel. Each wait is bounded: a block that has waited timeout_ns since it
-// arrived (globaltimer ns) sets ST_TIMEOUT in the status word, and the barrier
-// returns false in every block that sees it, so the kernel can return
-// instead of hanging. Work between barriers is never timed.
+// kernel. The arrival count only grows: every block keeps the same running
+// target (the count at which the barrier before this one completed) and the
+// same generation, so a barrier is one release-ordered atomic add per block,
+// and the block that brings the count to target + nblk publishes the next
+// generation; the others poll it. Each wait is bounded: a block that has
+// waited timeout_ns since it arrived (globaltimer ns) sets ST_TIMEOUT in the
+// status word, and the barrier returns false in every block that sees it, so
+// the kernel can return instead of hanging. Work between barriers is never
+// timed. GridBar must start at zero, with target = gen = 0 in every block.
 struct GridBar {
     unsigned count;
     unsigned gen;
 };
 
 // nblk: the number of blocks taking part (gridDim.x, or fewer once the others
-// have returned for good).
-__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t timeout_ns, unsigned nblk) {
+// have returned for good); target and gen are the block's running copies.
+__device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t timeout_ns, unsigned nblk,
+                                             unsigned &target, unsigned &gen) {
     __syncthreads();
     __shared__ int s_ok;
     if (threadIdx.x == 0) {
         int ok = 1;
-        unsigned g = ld_acquire_u(&bar->gen);
-        __threadfence();
-        unsigned arrived = atomicAdd(&bar->count, 1u);
-        if (arrived == nblk - 1) {
-            atomicExch(&bar->count, 0u);
-            __threadfence();
-            st_release_u(&bar->gen, g + 1);
+        unsigned old;
+        // acquire-release: this block's writes (ordered before it by the block
+        // barrier) are released with the arrival, and the last arrival acquires
+        // every earlier one before it releases the next generation
+        asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], 1;" : "=r"(old) : "l"(&bar->count) : "memory");
+        if (old == target + nblk - 1) {
+            st_release_u(&bar->gen, gen + 1);
         } else {
             // poll the generation word back to back; the status word and the
             // clock are read every 64 polls, and long waits back off
             const uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
-            while (ld_acquire_u(&bar->gen) == g) {
+            while (ld_acquire_u(&bar->gen) == gen) {
                 if ((++spins & 63u) == 0) {
                     if (ld_relaxed(status) & ST_TIMEOUT) { ok = 0; break; }
                     if (globaltimer_ns() - t0 > timeout_ns) {
@@ -141,10 +147,11 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
                 }
             }
         }
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
+    target += nblk;
+    gen += 1;
     return s_ok != 0;
 }
 

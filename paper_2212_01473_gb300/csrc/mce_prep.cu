@@ -193,12 +193,13 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     bool solo = false;
     unsigned nbar = gridDim.x;  // blocks meeting at grid barriers
     GridBar *gbar = &ctl->bar;
+    unsigned bar_target = 0, bar_gen = 0;  // running copies, the same in every block
     auto barrier = [&]() -> bool {
         if (solo) {
             __syncthreads();
             return true;
         }
-        return grid_barrier(gbar, status, timeout_ns, nbar);
+        return grid_barrier(gbar, status, timeout_ns, nbar, bar_target, bar_gen);
     };
 
     if (tid == 0) ctl->t_start = globaltimer_ns();

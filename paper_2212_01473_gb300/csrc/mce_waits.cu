@@ -47,7 +47,8 @@ __global__ void k_selftest_beat(int *words, uint64_t timeout_ns) {
 __global__ void k_selftest_barrier(int *words, uint64_t timeout_ns) {
     GridBar *bar = reinterpret_cast<GridBar *>(words);
     int *status = words + 64;
-    grid_barrier(bar, status, timeout_ns, gridDim.x + 1);
+    unsigned target = 0, gen = 0;
+    grid_barrier(bar, status, timeout_ns, gridDim.x + 1, target, gen);
 }
 
 }  // namespace mce
