@@ -175,7 +175,6 @@ struct DevGraph {
     const int32_t *out_col;   // ranks, ascending within a row
     const int32_t *in_ptr;    // [n+1] earlier neighbours
     const int32_t *in_col;    // ranks (any order)
-    const int32_t *in_pos;    // [m] in_pos[i]: where rank r sits in the later list of in_col[i], i in r's row
     const int32_t *order;     // rank -> input id
     const uint64_t *mixid;    // rank -> mix64(input id + 1)
     const int32_t *gid;       // rank -> graph index (NULL when G == 1)
