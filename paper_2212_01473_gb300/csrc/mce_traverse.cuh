@@ -518,6 +518,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             const int x0 = G.in_ptr[r + 1] - G.in_ptr[r];
             const int32_t *prow = G.out_col + G.out_ptr[r];
             const int32_t *xrow = G.in_col + G.in_ptr[r];
+            const int32_t *xpos = G.in_pos + G.in_ptr[r];  // where r sits in each x's later list
             if (n0 > rows_cap || x0 > C.x_cap || W > WP) {
                 if (g.gl == 0) atomicOr(O.status, ST_OVERFLOW);
                 break;
@@ -603,7 +604,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         const int32_t *nr = G.out_col + G.out_ptr[x];
                         const int len = G.out_ptr[x + 1] - G.out_ptr[x];
                         int lo = 0;
-                        for (int j = find_in(nr, 0, len, r + 1); j < len && lo < n0; j++) {
+                        const int js = x0 > kInPosMin ? xpos[idx] + 1 : find_in(nr, 0, len, r + 1);
+                        for (int j = js; j < len && lo < n0; j++) {
                             const int k = find_in(p0, lo, n0, nr[j]);
                             if (k < n0 && p0[k] == nr[j]) {
                                 w |= 1u << k;
@@ -723,7 +725,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         x = xrow[idx];
                         nr = G.out_col + G.out_ptr[x];
                         len = G.out_ptr[x + 1] - G.out_ptr[x];
-                        j0 = find_in(nr, 0, len, r + 1);  // only later vertices can be in P0
+                        // only vertices after r can be in P0
+                        j0 = x0 > kInPosMin ? xpos[idx] + 1 : find_in(nr, 0, len, r + 1);
                         int lo = 0;
                         for (int j = j0; j < len && lo < n0; j++) {
                             int32_t w = nr[j];
@@ -774,6 +777,9 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             // 32-bit word per thread (thread gl owns word gl < WP); the stack
             // holds the ancestors (pushed on descent, reloaded on backtrack).
             const bool own = g.gl < WP;
+            // the words of the root's rows that can hold bits (W <= WP): the
+            // stack keeps only these; the node's other words stay 0
+            const bool ownw = g.gl < W;
             uint32_t p = 0u, xp = 0u, b = 0u;
             int lpx = nx, npend = 0;
             uint64_t S = G.mixid[r];
@@ -1307,7 +1313,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     // branch set is empty, and words no thread owns are 0)
                     kmode = false;
                     if (over_budget) break;
-                    if (!own) {
+                    if (!ownw) {
                         p = 0u;
                         xp = 0u;
                     }
@@ -1406,7 +1412,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     if (l == l0) break;
                     l--;
                     const uint32_t *lv = stk + (size_t)l * LS;
-                    if (own) {
+                    if (ownw) {
                         p = lv[Lvl<WP>::P + g.gl];
                         xp = lv[Lvl<WP>::XP + g.gl];
                         b = lv[Lvl<WP>::B + g.gl];
@@ -1536,7 +1542,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 // ------------------------------ descend: push this level, partition X_X by v
                 {
                     uint32_t *lv = stk + (size_t)l * LS;
-                    if (own) {
+                    if (ownw) {
                         lv[Lvl<WP>::P + g.gl] = p;
                         lv[Lvl<WP>::XP + g.gl] = xp;
                         lv[Lvl<WP>::B + g.gl] = b;
