@@ -196,7 +196,6 @@ struct mce_graph {
     bool has_alloc = false;
     int sm_count = 0, smem_optin = 0;
     int32_t *out_ptr = nullptr, *out_col = nullptr, *in_ptr = nullptr, *in_col = nullptr;
-    int32_t *in_pos = nullptr;  // [m]: see DevGraph::in_pos
     int32_t *order = nullptr, *rank = nullptr, *core = nullptr, *outdeg = nullptr, *gid = nullptr;
     uint64_t *mixid = nullptr;
     int32_t *class_roots[kNumClasses + 1] = {};
@@ -247,7 +246,7 @@ static void release_prepared(mce_graph *g);
 
 static void release(mce_graph *g) {
     release_prepared(g);
-    void *ps[] = {g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->in_pos, g->order, g->rank,
+    void *ps[] = {g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->rank,
                   g->core,    g->outdeg,  g->gid,    g->mixid,  g->scratch};
     for (void *p : ps) dfree(g, p);
     for (int c = 0; c <= kNumClasses; c++) dfree(g, g->class_roots[c]);
@@ -417,17 +416,15 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
         g->in_ptr = dnew<int32_t>(g, nn, nullptr);
         g->out_col = dnew<int32_t>(g, (size_t)m + 1, nullptr);
         g->in_col = dnew<int32_t>(g, (size_t)m + 1, nullptr);
-        g->in_pos = dnew<int32_t>(g, (size_t)m + 1, nullptr);
         int32_t *scan_tmp = dnew<int32_t>(g, (size_t)scan_tmp_words(n + 1), &tmp);
         g->mixid = dnew<uint64_t>(g, nn, nullptr);
         if (G > 1) g->gid = dnew<int32_t>(g, nn, nullptr);
         int *small = dnew<int>(g, 64, &tmp);
         int *long_rows = dnew<int>(g, nn + 1, &tmp);
-        if (!g->outdeg || !indeg || !g->out_ptr || !g->in_ptr || !g->out_col || !g->in_col || !g->in_pos || !scan_tmp ||
+        if (!g->outdeg || !indeg || !g->out_ptr || !g->in_ptr || !g->out_col || !g->in_col || !scan_tmp ||
             !g->mixid || (G > 1 && !g->gid) || !small || !long_rows) { rc = fail(MCE_ENOMEM, "device allocation for orientation failed"); goto cleanup; }
         CK(launch_orient(n, d_rp, d_col, g->order, g->rank, g->outdeg, indeg, g->out_ptr, g->out_col,
                          g->in_ptr, g->in_col, scan_tmp, long_rows, g->stream));
-        CK(launch_in_pos(n, g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->in_pos, g->stream));
         CK(launch_mix_gid(n, g->order, g->mixid, g->gid, d_gptr, G, g->stream));
         CK(cudaMemsetAsync(small, 0, 64 * 4, g->stream));
         k_last_core<<<1, 1, 0, g->stream>>>(g->order, g->core, n, small);
@@ -606,7 +603,6 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     dg.out_col = g->out_col;
     dg.in_ptr = g->in_ptr;
     dg.in_col = g->in_col;
-    dg.in_pos = g->in_pos;
     dg.order = g->order;
     dg.mixid = g->mixid;
     dg.gid = g->gid;

@@ -167,9 +167,6 @@ inline void count_launch() { launch_counter()++; }
 
 // ----------------------------------------------------------------- handles
 
-// Ranks with more earlier neighbours than this get DevGraph::in_pos.
-constexpr int kInPosMin = 1024;
-
 // Everything the traversal needs about the oriented graph (device pointers).
 struct DevGraph {
     int32_t n;
@@ -178,8 +175,6 @@ struct DevGraph {
     const int32_t *out_col;   // ranks, ascending within a row
     const int32_t *in_ptr;    // [n+1] earlier neighbours
     const int32_t *in_col;    // ranks (any order)
-    const int32_t *in_pos;    // [m] in_pos[i]: where rank r sits in the later list of in_col[i], i in r's
-                              // row; written for rows longer than kInPosMin only
     const int32_t *order;     // rank -> input id
     const uint64_t *mixid;    // rank -> mix64(input id + 1)
     const int32_t *gid;       // rank -> graph index (NULL when G == 1)

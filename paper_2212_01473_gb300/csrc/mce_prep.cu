@@ -835,41 +835,6 @@ cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const in
     return cudaGetLastError();
 }
 
-// One warp per rank r with more than kInPosMin earlier neighbours: each
-// earlier neighbour x finds r in its sorted later list. Every search is
-// independent, so the pass is throughput-bound here instead of latency-bound
-// inside the one traversal group that sets such a root up (a hub root can
-// have 10^5 earlier neighbours); other rows are left unwritten.
-__global__ void k_in_pos(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
-                         const int32_t *in_col, int32_t *in_pos) {
-    const int lane = threadIdx.x & 31;
-    const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    for (int64_t r = w0; r < n; r += nw) {
-        const int b = in_ptr[r], e = in_ptr[r + 1];
-        if (e - b <= kInPosMin) continue;
-        for (int i = b + lane; i < e; i += 32) {
-            const int x = in_col[i];
-            const int xb = out_ptr[x];
-            int lo = xb, hi = out_ptr[x + 1];
-            while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (out_col[mid] < (int32_t)r) lo = mid + 1;
-                else hi = mid;
-            }
-            in_pos[i] = lo - xb;
-        }
-    }
-}
-
-cudaError_t launch_in_pos(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
-                          const int32_t *in_col, int32_t *in_pos, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    k_in_pos<<<grid_for((int64_t)n * 32, 256, 65536), 256, 0, s>>>(n, out_ptr, out_col, in_ptr, in_col, in_pos);
-    count_launch();
-    return cudaGetLastError();
-}
-
 __global__ void k_gather_outdeg(const int32_t *roots, int64_t k, const int32_t *outdeg, int32_t *out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
         out[i] = outdeg[roots[i]];

@@ -44,11 +44,6 @@ cudaError_t launch_orient(int n, const int32_t *rp, const int32_t *col, const in
                           const int32_t *rank, int32_t *outdeg, int32_t *indeg, int32_t *out_ptr,
                           int32_t *out_col, int32_t *in_ptr, int32_t *in_col, int32_t *scan_tmp,
                           int *long_rows /* n + 1 ints */, cudaStream_t s);
-// in_pos[i] = the index of rank r within out_col[out_ptr[x] ..) for each
-// earlier neighbour x = in_col[i] of r (out lists sorted), written only for
-// the rows of ranks with more than kInPosMin earlier neighbours
-cudaError_t launch_in_pos(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
-                          const int32_t *in_col, int32_t *in_pos, cudaStream_t s);
 cudaError_t launch_mix_gid(int n, const int32_t *order, uint64_t *mixid, int32_t *gid,
                            const int32_t *graph_ptr, int G, cudaStream_t s);
 cudaError_t launch_classify(int n, const int32_t *outdeg, const int32_t *indeg, int *cls_rows,

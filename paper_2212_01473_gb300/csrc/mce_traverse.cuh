@@ -518,7 +518,6 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
             const int x0 = G.in_ptr[r + 1] - G.in_ptr[r];
             const int32_t *prow = G.out_col + G.out_ptr[r];
             const int32_t *xrow = G.in_col + G.in_ptr[r];
-            const int32_t *xpos = G.in_pos + G.in_ptr[r];  // where r sits in each x's later list
             if (n0 > rows_cap || x0 > C.x_cap || W > WP) {
                 if (g.gl == 0) atomicOr(O.status, ST_OVERFLOW);
                 break;
@@ -604,8 +603,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         const int32_t *nr = G.out_col + G.out_ptr[x];
                         const int len = G.out_ptr[x + 1] - G.out_ptr[x];
                         int lo = 0;
-                        const int js = x0 > kInPosMin ? xpos[idx] + 1 : find_in(nr, 0, len, r + 1);
-                        for (int j = js; j < len && lo < n0; j++) {
+                        for (int j = find_in(nr, 0, len, r + 1); j < len && lo < n0; j++) {
                             const int k = find_in(p0, lo, n0, nr[j]);
                             if (k < n0 && p0[k] == nr[j]) {
                                 w |= 1u << k;
@@ -725,8 +723,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         x = xrow[idx];
                         nr = G.out_col + G.out_ptr[x];
                         len = G.out_ptr[x + 1] - G.out_ptr[x];
-                        // only vertices after r can be in P0
-                        j0 = x0 > kInPosMin ? xpos[idx] + 1 : find_in(nr, 0, len, r + 1);
+                        j0 = find_in(nr, 0, len, r + 1);  // only later vertices can be in P0
                         int lo = 0;
                         for (int j = j0; j < len && lo < n0; j++) {
                             int32_t w = nr[j];
