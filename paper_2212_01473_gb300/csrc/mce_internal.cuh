@@ -166,10 +166,10 @@ __device__ __forceinline__ int lower_bound_i32(const int32_t *a, int lo, int hi,
 }
 
 // Calls f(k), k ascending, for every k with p0[k] in nr[j0, len) (both sorted
-// ascending). A short list is walked: an entry below p0[k] is stepped over, an
-// entry above it moves k by a binary search in p0. A list far longer than p0
-// (an excluded hub's later neighbours) is probed once per p0 entry instead,
-// by a binary search that starts past the previous hit.
+// ascending). Each entry of a short list finds its place in p0 by a binary
+// search that starts past the previous one. A list far longer than p0 (an
+// excluded hub's later neighbours) is probed once per p0 entry instead, by a
+// binary search that starts past the previous hit.
 template <typename F>
 __device__ __forceinline__ void for_each_common(const int32_t *nr, int j0, int len, const int32_t *p0, int n0, F f) {
     if (len - j0 > 16 * n0 + 64) {
@@ -184,19 +184,17 @@ __device__ __forceinline__ void for_each_common(const int32_t *nr, int j0, int l
                 jl = j;
             }
         }
-    } else {
-        int j = j0, k = 0;
-        while (j < len && k < n0) {
-            const int32_t a = nr[j], b = p0[k];
-            if (a < b) {
-                j++;
-            } else if (a > b) {
-                k = lower_bound_i32(p0, k + 1, n0, a);
-            } else {
-                f(k);
-                j++;
-                k++;
-            }
+        return;
+    }
+    int lo = 0;
+    for (int j = j0; j < len && lo < n0; j++) {
+        const int32_t w = nr[j];
+        const int k = lower_bound_i32(p0, lo, n0, w);
+        if (k < n0 && p0[k] == w) {
+            f(k);
+            lo = k + 1;
+        } else {
+            lo = k;
         }
     }
 }

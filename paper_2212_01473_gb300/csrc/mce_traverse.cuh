@@ -689,7 +689,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         const int32_t u = p0[i];
                         const int32_t *nr = G.out_col + G.out_ptr[u];
                         const int len = G.out_ptr[u + 1] - G.out_ptr[u];
-                        if (len > 64 * (n0 - i) + 256) {
+                        if (len > 16 * (n0 - i) + 64) {
                             // a later list far longer than the rest of P0 (a hub in P0): the
                             // lanes probe it for P0[k], k > i, instead of walking it
                             for (int k = i + 1 + g.lane; k < n0; k += 32) {
