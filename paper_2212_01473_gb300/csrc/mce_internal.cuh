@@ -155,50 +155,6 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
     return s_ok != 0;
 }
 
-// first index in [lo, hi) of sorted a with a[idx] >= key (hi if none)
-__device__ __forceinline__ int lower_bound_i32(const int32_t *a, int lo, int hi, int32_t key) {
-    while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (a[mid] < key) lo = mid + 1;
-        else hi = mid;
-    }
-    return lo;
-}
-
-// Calls f(k), k ascending, for every k with p0[k] in nr[j0, len) (both sorted
-// ascending). Each entry of a short list finds its place in p0 by a binary
-// search that starts past the previous one. A list far longer than p0 (an
-// excluded hub's later neighbours) is probed once per p0 entry instead, by a
-// binary search that starts past the previous hit.
-template <typename F>
-__device__ __forceinline__ void for_each_common(const int32_t *nr, int j0, int len, const int32_t *p0, int n0, F f) {
-    if (len - j0 > 16 * n0 + 64) {
-        int jl = j0;
-        for (int k = 0; k < n0 && jl < len; k++) {
-            const int32_t w = p0[k];
-            const int j = lower_bound_i32(nr, jl, len, w);
-            if (j < len && nr[j] == w) {
-                f(k);
-                jl = j + 1;
-            } else {
-                jl = j;
-            }
-        }
-        return;
-    }
-    int lo = 0;
-    for (int j = j0; j < len && lo < n0; j++) {
-        const int32_t w = nr[j];
-        const int k = lower_bound_i32(p0, lo, n0, w);
-        if (k < n0 && p0[k] == w) {
-            f(k);
-            lo = k + 1;
-        } else {
-            lo = k;
-        }
-    }
-}
-
 // Record a message for mce_last_error() on this thread; returns code.
 int set_last_error(int code, const char *msg);
 

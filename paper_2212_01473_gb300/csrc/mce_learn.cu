@@ -63,12 +63,17 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
             const int32_t u = P0[i];
             const int32_t *nu = out_col + out_ptr[u];
             const int lu = out_ptr[u + 1] - out_ptr[u];
-            int c = 0;
-            // later neighbours of u that are in P0 after u: every P0 entry is later than r
-            for_each_common(nu, 0, lu, P0 + i + 1, n0 - i - 1, [&](int k) {
-                c++;
-                atomicAdd(&dg[i + 1 + k], 1);
-            });
+            int c = 0, lo = i + 1;
+            for (int j = 0; j < lu && lo < n0; j++) {
+                const int k = find_sorted(P0, lo, n0, nu[j]);
+                if (k < n0 && P0[k] == nu[j]) {
+                    c++;
+                    atomicAdd(&dg[k], 1);
+                    lo = k + 1;
+                } else {
+                    lo = k;
+                }
+            }
             atomicAdd(&dg[i], c);
             eP += c;
         }
@@ -97,8 +102,16 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
             if (i >= kXCap) continue;
             const int32_t *nx = out_col + out_ptr[x];
             const int lx = out_ptr[x + 1] - out_ptr[x];
-            int c = 0;
-            for_each_common(nx, find_sorted(nx, 0, lx, (int32_t)r + 1), lx, P0, n0, [&](int) { c++; });
+            int c = 0, lo = 0;
+            for (int j = find_sorted(nx, 0, lx, (int32_t)r + 1); j < lx && lo < n0; j++) {
+                const int k = find_sorted(P0, lo, n0, nx[j]);
+                if (k < n0 && P0[k] == nx[j]) {
+                    c++;
+                    lo = k + 1;
+                } else {
+                    lo = k;
+                }
+            }
             eX += c;
             xmax = max(xmax, c);
         }

@@ -602,7 +602,16 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         x = xrow[idx];
                         const int32_t *nr = G.out_col + G.out_ptr[x];
                         const int len = G.out_ptr[x + 1] - G.out_ptr[x];
-                        for_each_common(nr, find_in(nr, 0, len, r + 1), len, p0, n0, [&](int k) { w |= 1u << k; });
+                        int lo = 0;
+                        for (int j = find_in(nr, 0, len, r + 1); j < len && lo < n0; j++) {
+                            const int k = find_in(p0, lo, n0, nr[j]);
+                            if (k < n0 && p0[k] == nr[j]) {
+                                w |= 1u << k;
+                                lo = k + 1;
+                            } else {
+                                lo = k;
+                            }
+                        }
                     }
                     const unsigned hm = __ballot_sync(FULL, w != 0u);
                     const int tot = __popc(hm);
@@ -689,19 +698,6 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         const int32_t u = p0[i];
                         const int32_t *nr = G.out_col + G.out_ptr[u];
                         const int len = G.out_ptr[u + 1] - G.out_ptr[u];
-                        if (len > 16 * (n0 - i) + 64) {
-                            // a later list far longer than the rest of P0 (a hub in P0): the
-                            // lanes probe it for P0[k], k > i, instead of walking it
-                            for (int k = i + 1 + g.lane; k < n0; k += 32) {
-                                const int32_t w = p0[k];
-                                const int j = find_in(nr, 0, len, w);
-                                if (j < len && nr[j] == w) {
-                                    atomicOr(&Arow[(size_t)i * WP + (k >> 5)], 1u << (k & 31));
-                                    atomicOr(&Arow[(size_t)k * WP + (i >> 5)], 1u << (i & 31));
-                                }
-                            }
-                            continue;
-                        }
                         for (int j = g.lane; j < len; j += 32) {
                             int32_t w = nr[j];
                             int k = find_in(p0, i + 1, n0, w);
@@ -728,7 +724,13 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         nr = G.out_col + G.out_ptr[x];
                         len = G.out_ptr[x + 1] - G.out_ptr[x];
                         j0 = find_in(nr, 0, len, r + 1);  // only later vertices can be in P0
-                        for_each_common(nr, j0, len, p0, n0, [&](int) { hits++; });
+                        int lo = 0;
+                        for (int j = j0; j < len && lo < n0; j++) {
+                            int32_t w = nr[j];
+                            int k = find_in(p0, lo, n0, w);
+                            if (k < n0 && p0[k] == w) { hits++; lo = k + 1; }
+                            else lo = k;
+                        }
                     }
                     int tot;
                     int pos = grp_prefix(g, red, hits > 0, &tot);
@@ -737,11 +739,19 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                         uint32_t *row = xrows + (size_t)slot * WP;
                         int cw = 0;
                         uint32_t accw = 0;
-                        for_each_common(nr, j0, len, p0, n0, [&](int k) {
-                            const int wi = k >> 5;
-                            while (cw < wi) { row[cw++] = accw; accw = 0; }
-                            accw |= 1u << (k & 31);
-                        });
+                        int lo = 0;
+                        for (int j = j0; j < len && lo < n0; j++) {
+                            int32_t w = nr[j];
+                            int k = find_in(p0, lo, n0, w);
+                            if (k < n0 && p0[k] == w) {
+                                int wi = k >> 5;
+                                while (cw < wi) { row[cw++] = accw; accw = 0; }
+                                accw |= 1u << (k & 31);
+                                lo = k + 1;
+                            } else {
+                                lo = k;
+                            }
+                        }
                         while (cw < WP) { row[cw++] = accw; accw = 0; }
                         xidx[slot] = (uint32_t)slot;
                         xrank[slot] = (uint32_t)x;
