@@ -96,7 +96,8 @@ typedef struct {
                             max(10, largest |P0| of the width class / 10) */
     int32_t blocks;        /* persistent blocks per width class; 0 = all that fit on the GPU */
     int32_t donate_policy; /* which busy groups may donate a child (Sec. III-C): MCE_DONATE_* */
-    int32_t stats;         /* 1 = collect per-phase SM cycle counters (see mce_stats); slows the run */
+    int32_t stats;         /* 1 = collect per-phase SM cycle counters (see mce_stats); slows the run.
+                              Counting runs only: mce_run_list and subtree_level = 2 collect none */
     int64_t timeout_ms;    /* bound of every device-side wait (default 60000): an idle worker gives up
                               when no donation, no end of the launch and no heartbeat of a busy
                               worker has come for this long; work itself is never timed */

@@ -30,7 +30,8 @@ cudaError_t plan_wp(int rows, int sm_count, int max_smem_optin, int requested_bl
     L->a_global = AG;
     auto kern = k_traverse<WP, GW, AG, false, false>;
     for (auto variant : {k_traverse<WP, GW, AG, false, false>, k_traverse<WP, GW, AG, true, false>,
-                         k_traverse<WP, GW, AG, false, true>, k_traverse<WP, GW, AG, true, true>}) {
+                         k_traverse<WP, GW, AG, false, true>, k_traverse<WP, GW, AG, true, true>,
+                         k_traverse<WP, GW, AG, false, false, true>}) {
         cudaError_t e = cudaFuncSetAttribute(variant, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
         if (e != cudaSuccess) return e;
     }
@@ -55,6 +56,7 @@ cudaError_t launch_wp(const ClassLaunch &L, const DevGraph &g, const DevOut &o, 
     if (o.list && a.level2) k_traverse<WP, GW, AG, true, true><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     else if (o.list) k_traverse<WP, GW, AG, true, false><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     else if (a.level2) k_traverse<WP, GW, AG, false, true><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
+    else if (a.stats) k_traverse<WP, GW, AG, false, false, true><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     else k_traverse<WP, GW, AG, false, false><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     return cudaGetLastError();
 }

@@ -297,6 +297,68 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int t) {
     return pos;
 }
 
+// First index of a sorted a[0, n) with a[idx] >= key[u], for U keys at once.
+// The steps depend on n only (the range halves whatever the comparison), so
+// the U searches advance in lock step and their loads overlap.
+template <int U>
+__device__ __forceinline__ void lower_bounds(const int32_t *a, int n, const int32_t (&key)[U], int (&pos)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; u++) pos[u] = 0;
+    if (n == 0) return;
+    int len = n;
+    while (len > 1) {
+        const int half = len >> 1;
+#pragma unroll
+        for (int u = 0; u < U; u++) pos[u] = a[pos[u] + half] < key[u] ? pos[u] + half : pos[u];
+        len -= half;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) pos[u] += a[pos[u]] < key[u] ? 1 : 0;
+}
+
+// One warp walks 32 sorted lists of ranks at once, lane l's list being
+// col[jb_l, jb_l + cnt_l). The lists are laid end to end and dealt out at
+// stride 32, U entries per lane in flight, so a long list no longer holds up
+// the other lanes. Each entry is looked up in P0 (shared memory, n0 sorted
+// ranks) and hit(l, k) runs for an entry of lane l's list found at index k.
+template <int U, class F>
+__device__ __forceinline__ void warp_walk_lists(const int32_t *col, int jb, int cnt, int lane, const int32_t *p0,
+                                                int n0, F hit) {
+    constexpr unsigned FULL = 0xffffffffu;
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int tot = __shfl_sync(FULL, inc, 31);
+    const int exc = inc - cnt;  // where lane l's list starts in the joined range
+    for (int e0 = 0; e0 < tot; e0 += 32 * U) {
+        int ow[U], j[U];
+        int32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int e = min(e0 + u * 32 + lane, tot - 1);
+            // the list holding e: the last lane whose start is <= e
+            int l = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const int st = __shfl_sync(FULL, exc, l + s);
+                if (st <= e) l += s;
+            }
+            ow[u] = l;
+            j[u] = __shfl_sync(FULL, jb, l) + (e - __shfl_sync(FULL, exc, l));
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) w[u] = col[j[u]];
+        int k[U];
+        lower_bounds<U>(p0, n0, w, k);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (e0 + u * 32 + lane < tot && k[u] < n0 && p0[k[u]] == w[u]) hit(ow[u], k[u]);
+    }
+}
+
 // Copies the rows listed in rows[0..nrows) of a WP-word bit matrix.
 template <int WP, int GW>
 __device__ __forceinline__ void grp_copy_rows(const Grp<GW> &g, const int32_t *rows, int nrows, const uint32_t *src,
@@ -341,9 +403,10 @@ struct PhaseClock {
 };
 
 // LIST: the variant that also writes each clique's members (mce_run_list);
-// L2: the variant whose tasks are edges (Algorithm 4). The plain counting
-// variant carries none of that code.
-template <int WP, int GW, bool AG, bool LIST, bool L2>
+// L2: the variant whose tasks are edges (Algorithm 4); ST: the counting
+// variant that also keeps per-phase cycle counters (opts.stats). The plain
+// counting variant carries none of that code.
+template <int WP, int GW, bool AG, bool LIST, bool L2, bool ST = false>
 __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArgs C, int rows_cap, int stack_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int GT = 32 * GW;
@@ -407,7 +470,7 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
         return now > budget_end;
     };
     PhaseClock pc{};
-    pc.on = C.stats != 0 && g.gl == 0;
+    pc.on = ST && g.gl == 0;
 
     // per-group accumulators (meaningful in thread 0 of the group)
     unsigned long long acc_cnt = 0, acc_hash = 0, acc_nodes = 0, acc_don = 0;
@@ -693,6 +756,27 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                             }
                         }
                     }
+                } else if (GW == 1) {
+                    // 32 rows at a time: the part of each later neighbour's
+                    // out-list up to the last rank of P0 (all of it lies after that
+                    // neighbour), walked by the whole warp
+                    const int32_t maxp = p0[n0 - 1];
+                    for (int i0 = 0; i0 < n0; i0 += 32) {
+                        const int i = i0 + g.lane;
+                        int jb = 0, cnt = 0;
+                        if (i < n0) {
+                            const int32_t u = p0[i];
+                            jb = G.out_ptr[u];
+                            const int len = G.out_ptr[u + 1] - jb;
+                            cnt = (len == 0 || G.out_col[jb + len - 1] <= maxp) ? len
+                                                                                 : find_in(G.out_col + jb, 0, len, maxp + 1);
+                        }
+                        warp_walk_lists<4>(G.out_col, jb, cnt, g.lane, p0, n0, [&](int l, int k) {
+                            const int ii = i0 + l;
+                            atomicOr(&Arow[(size_t)ii * WP + (k >> 5)], 1u << (k & 31));
+                            atomicOr(&Arow[(size_t)k * WP + (ii >> 5)], 1u << (ii & 31));
+                        });
+                    }
                 } else {
                     for (int i = g.warp; i < n0; i += GW) {
                         const int32_t u = p0[i];
@@ -712,53 +796,96 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                 g.sync();
 
                 // ----------------------------------- X_X rows (Sec. III-E)
-                int base_slot = 0;
-                for (int it = 0; it < x0; it += GT) {
-                    int idx = it + g.gl;
-                    int hits = 0;
-                    const int32_t *nr = nullptr;
-                    int len = 0, j0 = 0;
-                    int32_t x = 0;
-                    if (idx < x0) {
-                        x = xrow[idx];
-                        nr = G.out_col + G.out_ptr[x];
-                        len = G.out_ptr[x + 1] - G.out_ptr[x];
-                        j0 = find_in(nr, 0, len, r + 1);  // only later vertices can be in P0
-                        int lo = 0;
-                        for (int j = j0; j < len && lo < n0; j++) {
-                            int32_t w = nr[j];
-                            int k = find_in(p0, lo, n0, w);
-                            if (k < n0 && p0[k] == w) { hits++; lo = k + 1; }
-                            else lo = k;
-                        }
+                if (GW == 1) {
+                    // The row of X0[i] goes to slot i. Clear the words a row can
+                    // use, walk the later lists of X0 between r and the last rank
+                    // of P0 with the whole warp, then list the slots whose row
+                    // holds a bit.
+                    constexpr unsigned FULL = 0xffffffffu;
+                    const int32_t maxp = n0 > 0 ? p0[n0 - 1] : -1;
+                    for (int i = g.lane; i < x0; i += 32) {
+                        xrank[i] = (uint32_t)xrow[i];
+                        for (int w = 0; w < W; w++) xrows[(size_t)i * WP + w] = 0u;
                     }
-                    int tot;
-                    int pos = grp_prefix(g, red, hits > 0, &tot);
-                    if (hits > 0) {
-                        int slot = base_slot + pos;
-                        uint32_t *row = xrows + (size_t)slot * WP;
-                        int cw = 0;
-                        uint32_t accw = 0;
-                        int lo = 0;
-                        for (int j = j0; j < len && lo < n0; j++) {
-                            int32_t w = nr[j];
-                            int k = find_in(p0, lo, n0, w);
-                            if (k < n0 && p0[k] == w) {
-                                int wi = k >> 5;
-                                while (cw < wi) { row[cw++] = accw; accw = 0; }
-                                accw |= 1u << (k & 31);
-                                lo = k + 1;
-                            } else {
-                                lo = k;
+                    __syncwarp();
+                    for (int i0 = 0; i0 < x0; i0 += 32) {
+                        const int i = i0 + g.lane;
+                        int jb = 0, cnt = 0;
+                        if (i < x0) {
+                            const int32_t x = xrow[i];
+                            const int b0 = G.out_ptr[x], len = G.out_ptr[x + 1] - b0;
+                            const int32_t *nr = G.out_col + b0;
+                            const int j0 = find_in(nr, 0, len, r + 1);  // only later vertices can be in P0
+                            const int j1 = (j0 == len || nr[len - 1] <= maxp) ? len : find_in(nr, j0, len, maxp + 1);
+                            jb = b0 + j0;
+                            cnt = j1 - j0;
+                        }
+                        warp_walk_lists<4>(G.out_col, jb, cnt, g.lane, p0, n0, [&](int l, int k) {
+                            atomicOr(&xrows[(size_t)(i0 + l) * WP + (k >> 5)], 1u << (k & 31));
+                        });
+                    }
+                    __threadfence_block();
+                    __syncwarp();
+                    int nl = 0;
+                    for (int i0 = 0; i0 < x0; i0 += 32) {
+                        const int i = i0 + g.lane;
+                        bool ne = false;
+                        if (i < x0)
+                            for (int w = 0; w < W; w++) ne |= __ldcg(&xrows[(size_t)i * WP + w]) != 0u;
+                        const unsigned bm = __ballot_sync(FULL, ne);
+                        if (ne) xidx[nl + __popc(bm & ((1u << g.lane) - 1u))] = (uint32_t)i;
+                        nl += __popc(bm);
+                    }
+                    nx = nl;
+                } else {
+                    int base_slot = 0;
+                    for (int it = 0; it < x0; it += GT) {
+                        int idx = it + g.gl;
+                        int hits = 0;
+                        const int32_t *nr = nullptr;
+                        int len = 0, j0 = 0;
+                        int32_t x = 0;
+                        if (idx < x0) {
+                            x = xrow[idx];
+                            nr = G.out_col + G.out_ptr[x];
+                            len = G.out_ptr[x + 1] - G.out_ptr[x];
+                            j0 = find_in(nr, 0, len, r + 1);  // only later vertices can be in P0
+                            int lo = 0;
+                            for (int j = j0; j < len && lo < n0; j++) {
+                                int32_t w = nr[j];
+                                int k = find_in(p0, lo, n0, w);
+                                if (k < n0 && p0[k] == w) { hits++; lo = k + 1; }
+                                else lo = k;
                             }
                         }
-                        while (cw < WP) { row[cw++] = accw; accw = 0; }
-                        xidx[slot] = (uint32_t)slot;
-                        xrank[slot] = (uint32_t)x;
+                        int tot;
+                        int pos = grp_prefix(g, red, hits > 0, &tot);
+                        if (hits > 0) {
+                            int slot = base_slot + pos;
+                            uint32_t *row = xrows + (size_t)slot * WP;
+                            int cw = 0;
+                            uint32_t accw = 0;
+                            int lo = 0;
+                            for (int j = j0; j < len && lo < n0; j++) {
+                                int32_t w = nr[j];
+                                int k = find_in(p0, lo, n0, w);
+                                if (k < n0 && p0[k] == w) {
+                                    int wi = k >> 5;
+                                    while (cw < wi) { row[cw++] = accw; accw = 0; }
+                                    accw |= 1u << (k & 31);
+                                    lo = k + 1;
+                                } else {
+                                    lo = k;
+                                }
+                            }
+                            while (cw < WP) { row[cw++] = accw; accw = 0; }
+                            xidx[slot] = (uint32_t)slot;
+                            xrank[slot] = (uint32_t)x;
+                        }
+                        base_slot += tot;
                     }
-                    base_slot += tot;
+                    nx = base_slot;
                 }
-                nx = base_slot;
             }
             if (edge) {
                 cached_r = r;

@@ -366,3 +366,27 @@ def test_run_budget_stops_the_run_and_context_survives():
     r = mce.mce_run(h)
     mce.mce_destroy(h)
     assert r.count == 3 ** 15
+
+
+def test_phase_counters_variant_gives_the_same_results():
+    # opts.stats = 1 launches the kernel variant that keeps per-phase cycle
+    # counters; the plain counting variant carries none of that code. Both must
+    # walk the same trees, and the counters must account for every task and node.
+    g = gen.disjoint_union([gen.chung_lu(3000, 12.0, 2.1, 400.0, 4, 12, 24, 5), gen.moon_moser(7)])
+    o = oracle.mce(g.row_ptr, g.col, mode=oracle.PIVOT_IP)
+    h = mce.mce_create(g.row_ptr, g.col)
+    try:
+        r0 = mce.mce_run(h, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP, stats=0))
+        st0 = mce.mce_get_stats(h)
+        r1 = mce.mce_run(h, mce.mce_default_opts(pivot=mce.MCE_PIVOT_IP, stats=1, blocks=2, donate_min_p=1))
+        st1 = mce.mce_get_stats(h)
+    finally:
+        mce.mce_destroy(h)
+    for r in (r0, r1):
+        assert (r.count, r.hash, r.max_size) == (o.count, o.hash, o.max_size)
+    assert r0.tree_nodes == r1.tree_nodes
+    assert sum(st0["phase_cycles"].values()) == 0
+    assert all(v > 0 for k, v in st1["phase_cycles"].items() if k in ("setup", "pivot", "branch"))
+    # one setup per task: every root with later neighbours, plus every received subtree
+    _, _, outd = mce.mce_get_order(mce.mce_create(g.row_ptr, g.col))
+    assert st1["phase_counts"]["setup"] == int((np.asarray(outd) > 0).sum()) + r1.donations
