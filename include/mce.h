@@ -125,8 +125,8 @@ typedef struct {
                               net that no run of the bundled workloads comes near); 0 = none */
     int32_t merge_wp;      /* one-warp width classes with rows of at most this many words share one
                               launch at the widest of them: 12 (default when 0), 4 or 1 (none) */
-    int32_t block_warps;   /* warps per block of every traversal launch: 16 (default when 0), 8 or 4
-                              (never fewer than a group's warps) */
+    int32_t block_warps;   /* warps per block of every traversal launch: 24 (default when 0), 16, 8
+                              or 4 (never fewer than a group's warps) */
 } mce_opts;
 
 typedef struct {
@@ -254,7 +254,7 @@ int mce_get_order(const mce_graph *g, int32_t *core, int32_t *rank, int32_t *out
 
 /* Launch facts and optional counters of the handle's last mce_run / mce_run_batch. */
 #define MCE_STATS_MAX_CLASSES 16
-#define MCE_STATS_PHASES 8
+#define MCE_STATS_PHASES 9
 typedef struct {
     int32_t struct_size;                         /* sizeof(mce_stats), set by the caller */
     int32_t n_classes;                           /* width classes launched (entries below) */
@@ -273,7 +273,8 @@ typedef struct {
      * maximality tests (excluded rows tested), 4 excluded-set partition
      * (rows moved), 5 worker-list donations (donations), 6 idle wait
      * (subtrees received), 7 reloading the parent level on backtrack
-     * (backtracks) */
+     * (backtracks), 8 entering a one-word (compact) subtree from a wider
+     * node (excluded rows re-encoded) */
     uint64_t phase_cycles[MCE_STATS_PHASES];
     uint64_t phase_counts[MCE_STATS_PHASES];
     /* narrowest row width whose roots the launch ran: one launch takes the

@@ -581,8 +581,9 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
     else if (opts.run_budget_ms < 0) rc = fail(MCE_EINVAL, "opts.run_budget_ms < 0");
     else if (opts.merge_wp != 0 && opts.merge_wp != 1 && opts.merge_wp != 4 && opts.merge_wp != 12)
         rc = fail(MCE_EINVAL, "opts.merge_wp must be 0, 1, 4 or 12");
-    else if (opts.block_warps != 0 && opts.block_warps != 4 && opts.block_warps != 8 && opts.block_warps != 16)
-        rc = fail(MCE_EINVAL, "opts.block_warps must be 0, 4, 8 or 16");
+    else if (opts.block_warps != 0 && opts.block_warps != 4 && opts.block_warps != 8 && opts.block_warps != 16 &&
+             opts.block_warps != 24)
+        rc = fail(MCE_EINVAL, "opts.block_warps must be 0, 4, 8, 16 or 24");
     if (rc != MCE_OK) { delete P; return rc; }
     if (opts.timeout_ms <= 0) opts.timeout_ms = 60000;
     P->level2 = opts.subtree_level == 2;
@@ -1020,7 +1021,7 @@ static double time_setting(mce_graph *g, const mce_opts *base, unsigned mask, co
 // own width; the fastest over all one-warp roots is kept. (2) Then, launch by
 // launch, a coordinate search from the defaults over the donation threshold
 // (|P0|max / 10, / 20, / 5, never below 10), the donation rule (EITHER,
-// PAPER, ANY), the warps per block (16, 8, 4) and the grid (all blocks that
+// PAPER, ANY), the warps per block (24, 16, 8, 4) and the grid (all blocks that
 // fit, or one per SM), keeping each change that is faster. Results never
 // depend on any of these.
 extern "C" int mce_autotune(mce_graph *g, const mce_opts *base, double budget_ms) {
@@ -1097,7 +1098,7 @@ extern "C" int mce_autotune(mce_graph *g, const mce_opts *base, double budget_ms
             t.policy = pol;
             if ((rc = attempt(t)) != MCE_OK) return rc;
         }
-        for (int w : {8, 4}) {
+        for (int w : {16, 8, 4}) {
             Tuned t = best_t;
             t.warps = w;
             if (w >= group_warps(class_wp(c)) && (rc = attempt(t)) != MCE_OK) return rc;

@@ -190,7 +190,8 @@ enum Phase : int {
     PH_DONATE = 5,     // worker-list checks and donations; count = donations
     PH_IDLE = 6,       // waiting in the worker list; count = subtrees received
     PH_POP = 7,        // reloading the parent level on backtrack; count = backtracks
-    kNumPhases = 8
+    PH_CENTRY = 8,     // entering a compact subtree from a wide node; count = X_X rows re-encoded
+    kNumPhases = 9
 };
 
 // Per-launch traversal outputs (device pointers).

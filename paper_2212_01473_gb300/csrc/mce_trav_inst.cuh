@@ -19,8 +19,8 @@ cudaError_t plan_wp(int rows, int sm_count, int max_smem_optin, int requested_bl
     constexpr int GW = group_warps(WP);
     constexpr bool AG = a_in_global(WP);
     const GrpSmem lay = grp_smem_layout(WP, GW, rows, AG, stack_in_smem(WP), block_hist && GW > 1);
-    // groups per block: 16 warps by default, or the requested warps (a multiple of the group width)
-    int gpb = (requested_warps >= GW && requested_warps <= 16 ? requested_warps : 16) / GW;
+    // groups per block: kTravMaxWarps warps by default, or the requested warps (a multiple of the group width)
+    int gpb = (requested_warps >= GW && requested_warps <= kTravMaxWarps ? requested_warps : kTravMaxWarps) / GW;
     while (gpb > 1 && smem_bytes(lay, gpb) > (size_t)max_smem_optin) gpb--;
     if (smem_bytes(lay, gpb) > (size_t)max_smem_optin) return cudaErrorInvalidConfiguration;
     L->wp = WP;

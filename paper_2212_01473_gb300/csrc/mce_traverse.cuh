@@ -153,6 +153,12 @@ __device__ __forceinline__ ArenaPtrs arena_at(uint32_t *base, int wp, int rows, 
 // Edge tasks (Algorithm 4) claimed per atomic.
 constexpr int kEdgeChunk = 16;
 
+// Warps per traversal block, at most and by default. The traversal is bound
+// by dependent latency (shuffle and reduction chains, L1/L2 round trips), so
+// resident warps are what hides it: 24 warps at 80 registers a thread beat 16
+// at 128 (chunglu_1m 54.5 -> 46.6 ms) despite a few spilled registers.
+constexpr int kTravMaxWarps = 24;
+
 __device__ __forceinline__ int find_in(const int32_t *a, int lo, int hi, int32_t key) {
     while (lo < hi) {
         int mid = (lo + hi) >> 1;
@@ -407,7 +413,7 @@ struct PhaseClock {
 // variant that also keeps per-phase cycle counters (opts.stats). The plain
 // counting variant carries none of that code.
 template <int WP, int GW, bool AG, bool LIST, bool L2, bool ST = false>
-__global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArgs C, int rows_cap, int stack_smem) {
+__global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, DevOut O, ClassArgs C, int rows_cap, int stack_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int GT = 32 * GW;
     constexpr int LS = Lvl<WP>::SIZE;
@@ -1193,7 +1199,8 @@ __global__ void __launch_bounds__(512) k_traverse(DevGraph G, DevOut O, ClassArg
                     kpend = npend > 0;
                     kmode = true;
                     enter = false;
-                    pc.stop(PH_SETUP);
+                    pc.stop(PH_CENTRY);
+                    pc.count(PH_CENTRY, (unsigned long long)kclx);
                 }
                 if (GW == 1 && kmode) {
                     constexpr unsigned FULL = 0xffffffffu;

@@ -70,7 +70,7 @@ def test_autotune_changes_schedule_only():
     tuned = mce.mce_run(h, mce.mce_default_opts(tuned=1))
     # every bitset width of the one-warp launch and every block size the tuner may pick
     others = [mce.mce_run(h, mce.mce_default_opts(merge_wp=mw, block_warps=bw))
-              for mw in (1, 4, 12) for bw in (4, 8, 16)]
+              for mw in (1, 4, 12) for bw in (4, 8, 16, 24)]
     mce.mce_destroy(h)
     for r in [tuned] + others:
         assert (r.count, r.hash, r.tree_nodes) == (plain.count, plain.hash, plain.tree_nodes)
