@@ -71,7 +71,8 @@ extern "C" {
 
 /* root ordering */
 #define MCE_ORDER_PLAIN 0   /* roots by descending degeneracy rank within each width class */
-#define MCE_ORDER_PRIORITY 1/* roots by descending opts.root_priority (e.g. learned work estimate) */
+#define MCE_ORDER_PRIORITY 1/* roots by descending opts.root_priority (e.g. learned work estimate);
+                              roots whose priority is negative or NaN follow in the plain order */
 
 typedef struct mce_graph mce_graph; /* opaque; owns its device copies */
 

@@ -660,12 +660,22 @@ static int plan_run(mce_graph *g, const mce_opts *opts_in, unsigned class_mask, 
         int *hb = (int *)dalloc(g, 256 * sizeof(int));
         P->tmp.push_back(hb);
         if (!hb) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
+        int most = 0;
+        for (int c = 0; c < kNumClasses; c++) most = std::max(most, (int)P->counts[c]);
+        int32_t *pf = (int32_t *)dalloc(g, ((size_t)most + 1) * 4);
+        int32_t *pp = (int32_t *)dalloc(g, ((size_t)most + 1) * 4);
+        int32_t *pt = (int32_t *)dalloc(g, (size_t)scan_tmp_words((int64_t)most + 1) * 4);
+        P->tmp.push_back(pf);
+        P->tmp.push_back(pp);
+        P->tmp.push_back(pt);
+        if (!pf || !pp || !pt) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
         for (int c = 0; c < kNumClasses; c++) {
             if (P->counts[c] == 0) continue;
             int32_t *o = (int32_t *)dalloc(g, (size_t)P->counts[c] * 4);
             P->tmp.push_back(o);
             if (!o) { rc = fail(MCE_ENOMEM, "device allocation failed"); goto cleanup; }
-            CK(launch_priority_order(P->lists[c], P->counts[c], g->order, opts.root_priority, hb, o, g->stream));
+            CK(launch_priority_order(P->lists[c], P->counts[c], g->order, opts.root_priority, hb, pf, pp, pt, o,
+                                     g->stream));
             P->lists[c] = o;
         }
     }

@@ -63,6 +63,68 @@ __device__ __forceinline__ void st_relaxed_u64(unsigned long long *p, unsigned l
     asm volatile("st.relaxed.gpu.global.u64 [%0], %1;" ::"l"(p), "l"(v) : "memory");
 }
 
+// First index of a sorted a[0, n) with a[idx] >= key[u], for U keys at once.
+// The steps depend on n only (the range halves whatever the comparison), so
+// the U searches advance in lock step and their loads overlap.
+template <int U>
+__device__ __forceinline__ void lower_bounds(const int32_t *a, int n, const int32_t (&key)[U], int (&pos)[U]) {
+#pragma unroll
+    for (int u = 0; u < U; u++) pos[u] = 0;
+    if (n == 0) return;
+    int len = n;
+    while (len > 1) {
+        const int half = len >> 1;
+#pragma unroll
+        for (int u = 0; u < U; u++) pos[u] = a[pos[u] + half] < key[u] ? pos[u] + half : pos[u];
+        len -= half;
+    }
+#pragma unroll
+    for (int u = 0; u < U; u++) pos[u] += a[pos[u]] < key[u] ? 1 : 0;
+}
+
+// One warp walks 32 sorted lists of ranks at once, lane l's list being
+// col[jb_l, jb_l + cnt_l). The lists are laid end to end and dealt out at
+// stride 32, U entries per lane in flight, so a long list no longer holds up
+// the other lanes. Each entry is looked up in P0 (shared memory, n0 sorted
+// ranks) and hit(l, k) runs for an entry of lane l's list found at index k.
+template <int U, class F>
+__device__ __forceinline__ void warp_walk_lists(const int32_t *col, int jb, int cnt, int lane, const int32_t *p0,
+                                                int n0, F hit) {
+    constexpr unsigned FULL = 0xffffffffu;
+    int inc = cnt;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(FULL, inc, o);
+        if (lane >= o) inc += y;
+    }
+    const int tot = __shfl_sync(FULL, inc, 31);
+    const int exc = inc - cnt;  // where lane l's list starts in the joined range
+    for (int e0 = 0; e0 < tot; e0 += 32 * U) {
+        int ow[U], j[U];
+        int32_t w[U];
+#pragma unroll
+        for (int u = 0; u < U; u++) {
+            const int e = min(e0 + u * 32 + lane, tot - 1);
+            // the list holding e: the last lane whose start is <= e
+            int l = 0;
+#pragma unroll
+            for (int s = 16; s > 0; s >>= 1) {
+                const int st = __shfl_sync(FULL, exc, l + s);
+                if (st <= e) l += s;
+            }
+            ow[u] = l;
+            j[u] = __shfl_sync(FULL, jb, l) + (e - __shfl_sync(FULL, exc, l));
+        }
+#pragma unroll
+        for (int u = 0; u < U; u++) w[u] = col[j[u]];
+        int k[U];
+        lower_bounds<U>(p0, n0, w, k);
+#pragma unroll
+        for (int u = 0; u < U; u++)
+            if (e0 + u * 32 + lane < tot && k[u] < n0 && p0[k[u]] == w[u]) hit(ow[u], k[u]);
+    }
+}
+
 // The worker-list wait of an idle group (one thread). It returns 1 when a
 // donated subtree arrived (*flag was set; it is cleared), 0 when the launch
 // is over (no active group left), and -1 when it gave up. It gives up with

@@ -35,8 +35,10 @@ constexpr int kXCap = 256;
 
 // One warp per root. Roots are all ranks 0..n-1 (list == NULL; outputs
 // indexed by input id) or list[0..n) (outputs indexed by list position).
-// Each warp stages the root's P0 and the in-P0 degree counters in shared
-// memory (2 * stride ints per warp, stride >= degeneracy + 1).
+// Each warp stages the root's P0, the in-P0 degree counters and 32 per-list
+// hit counters in shared memory (2 * stride + 32 ints per warp, stride >=
+// degeneracy + 1). The later lists are walked 32 at a time by the whole warp
+// (warp_walk_lists), as the traversal builds a root's rows.
 __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *out_col, const int32_t *in_ptr,
                                 const int32_t *in_col, const int32_t *order, const int32_t *core_by_id,
                                 int stride, int32_t *raw, float *feat, const int32_t *list) {
@@ -44,8 +46,9 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
     const int lane = threadIdx.x & 31;
     const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int64_t nw = ((int64_t)gridDim.x * blockDim.x) >> 5;
-    int32_t *P0 = fsm + (size_t)(threadIdx.x >> 5) * 2 * stride;
+    int32_t *P0 = fsm + (size_t)(threadIdx.x >> 5) * (2 * stride + 32);
     int32_t *dg = P0 + stride;
+    int32_t *xcnt = dg + stride;
     for (int64_t it = w0; it < n; it += nw) {
         const int64_t r = list ? list[it] : it;
         const int32_t *P0g = out_col + out_ptr[r];
@@ -57,25 +60,25 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
             dg[i] = 0;
         }
         __syncwarp();
-        // edges inside P0: u = P0[i] finds its later neighbours w in P0
+        // edges inside P0: u = P0[i] finds its later neighbours w in P0 (all
+        // of u's later list lies after u; only its part up to P0's last rank
+        // can hold w)
+        const int32_t maxp = n0 > 0 ? P0[n0 - 1] : -1;
         long long eP = 0;
-        for (int i = lane; i < n0; i += 32) {
-            const int32_t u = P0[i];
-            const int32_t *nu = out_col + out_ptr[u];
-            const int lu = out_ptr[u + 1] - out_ptr[u];
-            int c = 0, lo = i + 1;
-            for (int j = 0; j < lu && lo < n0; j++) {
-                const int k = find_sorted(P0, lo, n0, nu[j]);
-                if (k < n0 && P0[k] == nu[j]) {
-                    c++;
-                    atomicAdd(&dg[k], 1);
-                    lo = k + 1;
-                } else {
-                    lo = k;
-                }
+        for (int i0 = 0; i0 < n0; i0 += 32) {
+            const int i = i0 + lane;
+            int jb = 0, cnt = 0;
+            if (i < n0) {
+                const int32_t u = P0[i];
+                jb = out_ptr[u];
+                const int lu = out_ptr[u + 1] - jb;
+                cnt = (lu == 0 || out_col[jb + lu - 1] <= maxp) ? lu : find_sorted(out_col + jb, 0, lu, maxp + 1);
             }
-            atomicAdd(&dg[i], c);
-            eP += c;
+            warp_walk_lists<4>(out_col, jb, cnt, lane, P0, n0, [&](int l, int k) {
+                atomicAdd(&dg[i0 + l], 1);
+                atomicAdd(&dg[k], 1);
+                eP++;
+            });
         }
         __syncwarp();
         long long core_sum = 0, two_hop = 0;
@@ -99,21 +102,31 @@ __global__ void k_root_features(int n, const int32_t *out_ptr, const int32_t *ou
         for (int i = lane; i < x0; i += 32) {
             const int32_t x = X0[i];
             two_hop += (out_ptr[x + 1] - out_ptr[x]) + (in_ptr[x + 1] - in_ptr[x]);
-            if (i >= kXCap) continue;
-            const int32_t *nx = out_col + out_ptr[x];
-            const int lx = out_ptr[x + 1] - out_ptr[x];
-            int c = 0, lo = 0;
-            for (int j = find_sorted(nx, 0, lx, (int32_t)r + 1); j < lx && lo < n0; j++) {
-                const int k = find_sorted(P0, lo, n0, nx[j]);
-                if (k < n0 && P0[k] == nx[j]) {
-                    c++;
-                    lo = k + 1;
-                } else {
-                    lo = k;
-                }
+        }
+        const int xc = min(x0, kXCap);
+        for (int i0 = 0; i0 < xc; i0 += 32) {
+            const int i = i0 + lane;
+            int jb = 0, cnt = 0;
+            if (i < xc) {
+                const int32_t x = X0[i];
+                jb = out_ptr[x];
+                const int lx = out_ptr[x + 1] - jb;
+                const int32_t *nx = out_col + jb;
+                const int j0 = find_sorted(nx, 0, lx, (int32_t)r + 1);
+                const int j1 = (j0 == lx || nx[lx - 1] <= maxp) ? lx : find_sorted(nx, j0, lx, maxp + 1);
+                jb += j0;
+                cnt = j1 - j0;
             }
-            eX += c;
-            xmax = max(xmax, c);
+            xcnt[lane] = 0;
+            __syncwarp();
+            warp_walk_lists<4>(out_col, jb, cnt, lane, P0, n0, [&](int l, int) { atomicAdd(&xcnt[l], 1); });
+            __syncwarp();
+            if (i < xc) {
+                const int c = xcnt[lane];
+                eX += c;
+                xmax = max(xmax, c);
+            }
+            __syncwarp();
         }
         for (int o = 16; o; o >>= 1) {
             eP += __shfl_xor_sync(0xffffffffu, eP, o);
@@ -161,9 +174,9 @@ cudaError_t launch_root_features(int n, const int32_t *out_ptr, const int32_t *o
                                  int degeneracy, int sm_count, int32_t *raw, float *feat, const int32_t *list,
                                  cudaStream_t s) {
     if (n == 0) return cudaSuccess;
-    const int threads = 128;  // 4 warps, each with 2 * stride ints of shared memory
+    const int threads = 128;  // 4 warps, each with 2 * stride + 32 ints of shared memory
     const int stride = (degeneracy + 4) / 4 * 4;
-    const size_t smem = (size_t)(threads / 32) * 2 * stride * sizeof(int32_t);
+    const size_t smem = (size_t)(threads / 32) * (2 * stride + 32) * sizeof(int32_t);
     cudaError_t e = cudaFuncSetAttribute(k_root_features, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

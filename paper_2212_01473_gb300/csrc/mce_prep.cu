@@ -721,9 +721,22 @@ __device__ __forceinline__ int prio_bucket(float p) {
     return kPrioBuckets - 1 - b;
 }
 
-__global__ void k_prio_hist(const int32_t *list, int cnt, const int32_t *order, const float *prio, int *hist) {
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x)
-        atomicAdd(&hist[prio_bucket(prio[order[list[i]]])], 1);
+// Roots with a priority below 0 (or NaN) are unscored: they keep the list's
+// own (plain) order behind all scored roots, placed by a prefix sum of the
+// unscored flags, so neither their order nor one crowded bucket depends on
+// atomics. unscored[0..cnt] gets the flags (unscored[cnt] = 0).
+__global__ void k_prio_hist(const int32_t *list, int cnt, const int32_t *order, const float *prio, int *hist,
+                            int32_t *unscored) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i <= cnt; i += (int64_t)gridDim.x * blockDim.x) {
+        if (i == cnt) {
+            unscored[cnt] = 0;
+            continue;
+        }
+        const float p = prio[order[list[i]]];
+        const bool u = !(p >= 0.f);
+        unscored[i] = u ? 1 : 0;
+        if (!u) atomicAdd(&hist[prio_bucket(p)], 1);
+    }
 }
 
 __global__ void k_prio_offsets(int *hist) {
@@ -735,11 +748,15 @@ __global__ void k_prio_offsets(int *hist) {
     hist[threadIdx.x] = pre;
 }
 
+// upos = exclusive prefix of the unscored flags (upos[cnt] = their number)
 __global__ void k_prio_scatter(const int32_t *list, int cnt, const int32_t *order, const float *prio, int *cursor,
-                               int32_t *out) {
+                               const int32_t *upos, int32_t *out) {
+    const int scored = cnt - upos[cnt];
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < cnt; i += (int64_t)gridDim.x * blockDim.x) {
         const int32_t r = list[i];
-        out[atomicAdd(&cursor[prio_bucket(prio[order[r]])], 1)] = r;
+        const float p = prio[order[r]];
+        if (p >= 0.f) out[atomicAdd(&cursor[prio_bucket(p)], 1)] = r;
+        else out[scored + upos[i]] = r;
     }
 }
 
@@ -885,15 +902,17 @@ cudaError_t launch_subset(const int32_t *list, int cnt, const int32_t *mask, int
 }
 
 cudaError_t launch_priority_order(const int32_t *list, int cnt, const int32_t *order, const float *prio,
-                                  int *hist, int32_t *out, cudaStream_t s) {
+                                  int *hist, int32_t *flags, int32_t *pos, int32_t *scan_tmp, int32_t *out,
+                                  cudaStream_t s) {
     if (cnt <= 0) return cudaSuccess;
     cudaError_t e = cudaMemsetAsync(hist, 0, kPrioBuckets * sizeof(int), s);
     if (e != cudaSuccess) return e;
-    k_prio_hist<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, order, prio, hist);
+    k_prio_hist<<<grid_for(cnt + 1, 256, 65536), 256, 0, s>>>(list, cnt, order, prio, hist, flags);
     count_launch();
+    if ((e = exclusive_scan(flags, pos, (int64_t)cnt + 1, scan_tmp, s)) != cudaSuccess) return e;
     k_prio_offsets<<<1, kPrioBuckets, 0, s>>>(hist);
     count_launch();
-    k_prio_scatter<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, order, prio, hist, out);
+    k_prio_scatter<<<grid_for(cnt, 256, 65536), 256, 0, s>>>(list, cnt, order, prio, hist, pos, out);
     count_launch();
     return cudaGetLastError();
 }

@@ -59,7 +59,11 @@ cudaError_t launch_subset(const int32_t *list, int cnt, const int32_t *mask, int
 
 // roots of list[0..cnt) by descending prio[order[r]] (quarter-unit buckets,
 // any order inside a bucket); hist: 256 ints of scratch
+// Roots of list[0..cnt) by descending prio (256 buckets of a quarter unit);
+// roots with prio < 0 or NaN keep their list order after all others. flags
+// and pos hold cnt + 1 ints, scan_tmp scan_tmp_words(cnt + 1).
 cudaError_t launch_priority_order(const int32_t *list, int cnt, const int32_t *order, const float *prio,
-                                  int *hist, int32_t *out, cudaStream_t s);
+                                  int *hist, int32_t *flags, int32_t *pos, int32_t *scan_tmp, int32_t *out,
+                                  cudaStream_t s);
 
 }  // namespace mce

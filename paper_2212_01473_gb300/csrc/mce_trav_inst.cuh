@@ -28,10 +28,10 @@ cudaError_t plan_wp(int rows, int sm_count, int max_smem_optin, int requested_bl
     L->warps_per_block = gpb * GW;
     L->smem = smem_bytes(lay, gpb);
     L->a_global = AG;
-    auto kern = k_traverse<WP, GW, AG, false, false>;
-    for (auto variant : {k_traverse<WP, GW, AG, false, false>, k_traverse<WP, GW, AG, true, false>,
-                         k_traverse<WP, GW, AG, false, true>, k_traverse<WP, GW, AG, true, true>,
-                         k_traverse<WP, GW, AG, false, false, true>}) {
+    auto kern = k_traverse<WP, GW, AG, false, false, false, 0>;
+    for (auto variant : {k_traverse<WP, GW, AG, false, false, false, 0>, k_traverse<WP, GW, AG, false, false, false, 1>,
+                         k_traverse<WP, GW, AG, true, false>, k_traverse<WP, GW, AG, false, true>,
+                         k_traverse<WP, GW, AG, true, true>, k_traverse<WP, GW, AG, false, false, true>}) {
         cudaError_t e = cudaFuncSetAttribute(variant, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)L->smem);
         if (e != cudaSuccess) return e;
     }
@@ -57,7 +57,8 @@ cudaError_t launch_wp(const ClassLaunch &L, const DevGraph &g, const DevOut &o, 
     else if (o.list) k_traverse<WP, GW, AG, true, false><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     else if (a.level2) k_traverse<WP, GW, AG, false, true><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     else if (a.stats) k_traverse<WP, GW, AG, false, false, true><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
-    else k_traverse<WP, GW, AG, false, false><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
+    else if (a.pivot_ipx) k_traverse<WP, GW, AG, false, false, false, 1><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
+    else k_traverse<WP, GW, AG, false, false, false, 0><<<grid, block, L.smem, s>>>(g, o, a, rows, ss);
     return cudaGetLastError();
 }
 

@@ -303,68 +303,6 @@ __device__ __forceinline__ int nth_set_bit(uint32_t m, int t) {
     return pos;
 }
 
-// First index of a sorted a[0, n) with a[idx] >= key[u], for U keys at once.
-// The steps depend on n only (the range halves whatever the comparison), so
-// the U searches advance in lock step and their loads overlap.
-template <int U>
-__device__ __forceinline__ void lower_bounds(const int32_t *a, int n, const int32_t (&key)[U], int (&pos)[U]) {
-#pragma unroll
-    for (int u = 0; u < U; u++) pos[u] = 0;
-    if (n == 0) return;
-    int len = n;
-    while (len > 1) {
-        const int half = len >> 1;
-#pragma unroll
-        for (int u = 0; u < U; u++) pos[u] = a[pos[u] + half] < key[u] ? pos[u] + half : pos[u];
-        len -= half;
-    }
-#pragma unroll
-    for (int u = 0; u < U; u++) pos[u] += a[pos[u]] < key[u] ? 1 : 0;
-}
-
-// One warp walks 32 sorted lists of ranks at once, lane l's list being
-// col[jb_l, jb_l + cnt_l). The lists are laid end to end and dealt out at
-// stride 32, U entries per lane in flight, so a long list no longer holds up
-// the other lanes. Each entry is looked up in P0 (shared memory, n0 sorted
-// ranks) and hit(l, k) runs for an entry of lane l's list found at index k.
-template <int U, class F>
-__device__ __forceinline__ void warp_walk_lists(const int32_t *col, int jb, int cnt, int lane, const int32_t *p0,
-                                                int n0, F hit) {
-    constexpr unsigned FULL = 0xffffffffu;
-    int inc = cnt;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(FULL, inc, o);
-        if (lane >= o) inc += y;
-    }
-    const int tot = __shfl_sync(FULL, inc, 31);
-    const int exc = inc - cnt;  // where lane l's list starts in the joined range
-    for (int e0 = 0; e0 < tot; e0 += 32 * U) {
-        int ow[U], j[U];
-        int32_t w[U];
-#pragma unroll
-        for (int u = 0; u < U; u++) {
-            const int e = min(e0 + u * 32 + lane, tot - 1);
-            // the list holding e: the last lane whose start is <= e
-            int l = 0;
-#pragma unroll
-            for (int s = 16; s > 0; s >>= 1) {
-                const int st = __shfl_sync(FULL, exc, l + s);
-                if (st <= e) l += s;
-            }
-            ow[u] = l;
-            j[u] = __shfl_sync(FULL, jb, l) + (e - __shfl_sync(FULL, exc, l));
-        }
-#pragma unroll
-        for (int u = 0; u < U; u++) w[u] = col[j[u]];
-        int k[U];
-        lower_bounds<U>(p0, n0, w, k);
-#pragma unroll
-        for (int u = 0; u < U; u++)
-            if (e0 + u * 32 + lane < tot && k[u] < n0 && p0[k[u]] == w[u]) hit(ow[u], k[u]);
-    }
-}
-
 // Copies the rows listed in rows[0..nrows) of a WP-word bit matrix.
 template <int WP, int GW>
 __device__ __forceinline__ void grp_copy_rows(const Grp<GW> &g, const int32_t *rows, int nrows, const uint32_t *src,
@@ -411,8 +349,10 @@ struct PhaseClock {
 // LIST: the variant that also writes each clique's members (mce_run_list);
 // L2: the variant whose tasks are edges (Algorithm 4); ST: the counting
 // variant that also keeps per-phase cycle counters (opts.stats). The plain
-// counting variant carries none of that code.
-template <int WP, int GW, bool AG, bool LIST, bool L2, bool ST = false>
+// counting variant carries none of that code. PV: the pivot rule, fixed at
+// compile time in the counting variants (0 = IP, 1 = IPX), so each carries
+// the code of one rule only; 2 = read from the launch (C.pivot_ipx).
+template <int WP, int GW, bool AG, bool LIST, bool L2, bool ST = false, int PV = 2>
 __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, DevOut O, ClassArgs C, int rows_cap, int stack_smem) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     constexpr int GT = 32 * GW;
@@ -477,6 +417,8 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
     };
     PhaseClock pc{};
     pc.on = ST && g.gl == 0;
+    // IPX: X_X rows are pivot candidates too (Sec. IV-E)
+    const bool ipx_rule = PV == 2 ? C.pivot_ipx != 0 : PV == 1;
 
     // per-group accumulators (meaningful in thread 0 of the group)
     unsigned long long acc_cnt = 0, acc_hash = 0, acc_nodes = 0, acc_don = 0;
@@ -1096,7 +1038,7 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                 kX = 0u;
                 kclx = nx;
                 kxr = f_xr;
-                kxk = C.pivot_ipx ? f_xk : 0u;
+                kxk = ipx_rule ? f_xk : 0u;
                 kRc = 0u;
                 kbase = 1;
                 kd = 0;
@@ -1115,7 +1057,7 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                 // the donor wrote the surviving X_X rows to xcomp, their ranks to xscr
                 kclx = (int)mb[2];
                 kxr = g.lane < kclx ? xcomp[g.lane] : 0u;
-                kxk = (C.pivot_ipx && g.lane < kclx) ? xscr[g.lane] : 0u;
+                kxk = (ipx_rule && g.lane < kclx) ? xscr[g.lane] : 0u;
                 kRc = 0u;
                 kbase = l0 + 1;
                 kd = 0;
@@ -1182,7 +1124,7 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                                 w |= ((xr[lj >> 5] >> (lj & 31)) & 1u) << j;
                             }
                         }
-                        const uint32_t rk = (C.pivot_ipx && i < kclx) ? xrank[e] : 0u;
+                        const uint32_t rk = (ipx_rule && i < kclx) ? xrank[e] : 0u;
                         if (i0 == 0) {
                             kxr = i < kclx ? w : 0u;
                             kxk = rk;
@@ -1204,7 +1146,7 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                 }
                 if (GW == 1 && kmode) {
                     constexpr unsigned FULL = 0xffffffffu;
-                    const bool ipx = C.pivot_ipx != 0;
+                    const bool ipx = ipx_rule;
                     // lane i: clique-hash id of L[i] (lanes past |L| hold a harmless
                     // copy of P0[0]'s), and the saved state of compact depth i
                     const uint64_t kmj = G.mixid[p0[kL]];
@@ -1243,7 +1185,9 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                             const unsigned best = __reduce_max_sync(FULL, key);
                             const int bsc = (int)(best >> 8) - 1;
                             uint32_t prow = __shfl_sync(FULL, kRow, 31 - (int)(best & 255u));
-                            if (ipx && kclx > 0) {
+                            // An X_P candidate adjacent to all of P leaves no branch, and
+                            // so would any X_X row that beat it: skip the X_X scan then
+                            if (ipx && kclx > 0 && bsc < __popc(kP)) {
                                 // the best X_X row: largest score, then smallest rank
                                 int xs = 0;
                                 uint32_t xk = 0u, xrow = 0u;
@@ -1465,7 +1409,7 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                     int best_x_score = -1;  // best X_X score, -1 if none scanned
                     int piv_x = -1;         // X_X slot of the best X_X candidate
                     int scanned = 0;
-                    if (C.pivot_ipx && lpx > 0) {
+                    if (ipx_rule && lpx > 0) {
                         unsigned long long bx = 0;
                         for (int j0 = 0; j0 < lpx; j0 += GT) {
                             const int j = j0 + g.gl;
