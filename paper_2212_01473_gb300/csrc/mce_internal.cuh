@@ -194,13 +194,19 @@ __device__ __forceinline__ bool grid_barrier(GridBar *bar, int *status, uint64_t
             st_release_u(&bar->gen, gen + 1);
         } else {
             // poll the generation word back to back; the status word and the
-            // clock are read every 64 polls, and long waits back off
-            const uint64_t t0 = globaltimer_ns();
+            // clock are read every 64 polls, and long waits back off. The
+            // global timer is not guaranteed to be monotonic: a reading below
+            // the start restarts the measurement instead of wrapping the
+            // unsigned difference into a false give-up.
+            uint64_t t0 = globaltimer_ns();
             unsigned spins = 0;
             while (ld_acquire_u(&bar->gen) == gen) {
                 if ((++spins & 63u) == 0) {
                     if (ld_relaxed(status) & ST_TIMEOUT) { ok = 0; break; }
-                    if (globaltimer_ns() - t0 > timeout_ns) {
+                    const uint64_t now = globaltimer_ns();
+                    if (now < t0) {
+                        t0 = now;
+                    } else if (now - t0 > timeout_ns) {
                         atomicOr(status, ST_TIMEOUT);
                         ok = 0;
                         break;

@@ -26,12 +26,13 @@ __global__ void k_selftest_beat(int *words, uint64_t timeout_ns) {
     if (blockIdx.x == 0) {
         if (idle_wait(flag, active, status, beat, timeout_ns, ~0ull) == 0) words[65] = 1;  // ended by the launch end
     } else {
-        const uint64_t t0 = globaltimer_ns();
+        uint64_t t0 = globaltimer_ns();
         uint64_t last = 0;
         for (;;) {
             const uint64_t now = globaltimer_ns();
+            if (now < t0) t0 = now;  // the global timer stepped back: measure from here
             if (now - t0 > 3 * timeout_ns) break;
-            if (now - last > timeout_ns / 4) {
+            if (now < last || now - last > timeout_ns / 4) {
                 st_relaxed_u64(beat, now);
                 last = now;
             }
