@@ -335,7 +335,7 @@ def form_roofline(mce, h, opts, g, golden, peaks, steps, flush_buf, nodes_key="t
                 dom["wp"], dom["group_warps"], lo, dom["wp"])}
 
 
-def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf, g=None, peaks=None):
+def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf, g=None, peaks=None, forms=None):
     """Learned root order on the same workload, and the 4096-graph batch run
     batched (one set of persistent launches, replayed from a CUDA graph) versus
     graph by graph, all on this GPU."""
@@ -344,7 +344,9 @@ def measure_forms(args, rp_d, col_d, count, value_plain, flush_buf, g=None, peak
     import gen
     import paper_2212_01473_gb300 as mce
     from paper_2212_01473_gb300 import learn
-    forms = {"plain": {"value": value_plain, "unit": "cliques/s"}}
+    # filled in place, so that what was measured survives a later failure
+    forms = {} if forms is None else forms
+    forms["plain"] = {"value": value_plain, "unit": "cliques/s"}
     stream = torch.cuda.current_stream()
 
     def timed(fn, reps):
@@ -619,7 +621,14 @@ def run_ours(args):
         line["config"]["roots"] = "the %d roots with at most %d words per row (|P0| <= %d) of %s, isolated " \
             "vertices included; each step enumerates their first-level subtrees" % (len(roots_np), max_w, 32 * max_w, base)
     if rank == 0 and world == 1 and not args.no_forms and max_w is None:
-        line["forms"] = measure_forms(args, rp_d, col_d, count, value, flush_buf, g, peaks)
+        # the comparisons come after the headline measurement: an error in one
+        # of them is reported in the line instead of losing the line
+        forms = {}
+        try:
+            measure_forms(args, rp_d, col_d, count, value, flush_buf, g, peaks, forms)
+        except Exception as exc:  # noqa: BLE001 - reported, not hidden
+            forms["error"] = "%s: %s" % (type(exc).__name__, exc)
+        line["forms"] = forms
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(g, args.cpu_sample, pool=roots_np)
     if rank == 0:

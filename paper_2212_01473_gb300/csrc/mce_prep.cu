@@ -5,6 +5,8 @@
 // lists in rank space.
 #include <climits>
 
+#include <cooperative_groups.h>
+
 #include "mce_prep.cuh"
 
 namespace mce {
@@ -178,13 +180,77 @@ constexpr int kSoloS = 2 * (kPeelThreads / 32);
 // adjacency lists longer than this are removed by a whole block
 constexpr int kHeavyDeg = 64;
 
+// ------------------------------------------------ narrow stage as a cluster
+// The narrow stage's kNarrowBlocks blocks can run as one thread-block
+// cluster, whose barrier needs no round trip to L2: every CTA holds one
+// mbarrier expecting one arrival from each CTA; at a barrier, thread t <
+// kNarrowBlocks of every CTA arrives (release, cluster scope) on CTA t's
+// mbarrier, and thread 0 waits on its own (acquire, cluster scope), with the
+// grid barrier's bound and status checks. No CTA may leave the kernel while
+// another can still arrive on its mbarrier, so every exit of the cluster
+// kernel passes one hardware cluster barrier; every wait before it is
+// bounded, so every CTA gets there.
+__device__ __forceinline__ void mbar_init(unsigned mb, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mb), "r"(count) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ bool cluster_barrier(unsigned mb, unsigned &phase, int *status, uint64_t timeout_ns) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x < (unsigned)kNarrowBlocks) {
+        unsigned remote;
+        asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(mb), "r"((unsigned)threadIdx.x));
+        asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+    }
+    if (threadIdx.x == 0) {
+        int ok = 1;
+        uint64_t t0 = globaltimer_ns();
+        for (unsigned spins = 1;; spins++) {
+            unsigned done;
+            asm volatile(
+                "{ .reg .pred p; mbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2; "
+                "selp.u32 %0, 1, 0, p; }"
+                : "=r"(done)
+                : "r"(mb), "r"(phase)
+                : "memory");
+            if (done) break;
+            if ((spins & 63u) == 0) {
+                if (ld_relaxed(status) & ST_TIMEOUT) { ok = 0; break; }
+                const uint64_t now = globaltimer_ns();
+                if (now < t0) {
+                    t0 = now;
+                } else if (now - t0 > timeout_ns) {
+                    atomicOr(status, ST_TIMEOUT);
+                    ok = 0;
+                    break;
+                }
+            }
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    phase ^= 1u;
+    return s_ok != 0;
+}
+
+// CL = false: the full grid, launched cooperatively; with handoff set, it
+// stops where the narrow stage would begin and leaves the state in ctl->rs_*.
+// CL = true: one cluster of kNarrowBlocks CTAs that goes on from there (it
+// returns at once when the full grid finished alone).
+template <bool CL>
 __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp, const int32_t *col,
                                                        int32_t *deg, int32_t *rank, int32_t *core,
                                                        int32_t *order, int32_t *remA, int32_t *remB,
                                                        int32_t *segstart, unsigned *bitmap, int *blocksums,
-                                                       PeelCtl *ctl, int *status, uint64_t timeout_ns) {
+                                                       PeelCtl *ctl, int *status, uint64_t timeout_ns,
+                                                       int handoff) {
     __shared__ int sh[64];
     __shared__ long long shl[32];
+    __shared__ __align__(8) unsigned long long cl_mbar;
+    if (CL && vload(&ctl->rs_active) == 0) return;  // the full grid finished alone
+    const unsigned mb = (unsigned)__cvta_generic_to_shared(&cl_mbar);
+    unsigned mb_phase = 0;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
@@ -199,21 +265,14 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             __syncthreads();
             return true;
         }
+        if (CL) return cluster_barrier(mb, mb_phase, status, timeout_ns);
         return grid_barrier(gbar, status, timeout_ns, nbar, bar_target, bar_gen);
     };
-
-    if (tid == 0) ctl->t_start = globaltimer_ns();
-    for (int64_t v = tid; v < n; v += nth) {
-        deg[v] = rp[v + 1] - rp[v];
-        rank[v] = -1;
-        remA[v] = (int32_t)v;
-    }
-    if (!barrier()) return;
 
     // every block keeps the same copies of these
     // t counts sub-rounds (segments of `order`), r every pass and sub-round,
     // L every level-start pass
-    int k = 0, next = 0, nrem = n, t = 0, r = 0, L = 0;
+    int k = 0, next = 0, nrem = n, t = 0, r = 0, L = 0, ns = 0;
     bool remsel = false;
     // A level start is one pass and one barrier. The pass builds S for a
     // guessed k while it reduces the smallest live degree and the live degree
@@ -222,103 +281,147 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     // empty, the pass has only compacted the remaining list, and the next pass
     // takes the reduced minimum. The first level guesses 0.
     int guess = 0;
+    // the cluster kernel starts at the first sub-round of the level where the
+    // full grid stopped
+    bool resume = CL;
+    if (CL) {
+        if (threadIdx.x == 0) mbar_init(mb, kNarrowBlocks);
+        cooperative_groups::this_cluster().sync();  // every mbarrier is ready before the first arrival
+        k = ctl->rs_k;
+        guess = ctl->rs_guess;
+        next = ctl->rs_next;
+        nrem = ctl->rs_nrem;
+        t = ctl->rs_t;
+        r = ctl->rs_r;
+        L = ctl->rs_L;
+        remsel = ctl->rs_remsel != 0;
+        ns = ctl->rs_ns;
+        nbar = kNarrowBlocks;
+    } else {
+        if (tid == 0) ctl->t_start = globaltimer_ns();
+        for (int64_t v = tid; v < n; v += nth) {
+            deg[v] = rp[v + 1] - rp[v];
+            rank[v] = -1;
+            remA[v] = (int32_t)v;
+        }
+        if (!barrier()) goto done;
+    }
     while (next < n) {
-        const int32_t *rem = remsel ? remB : remA;
-        int32_t *rem2 = remsel ? remA : remB;
-        const int ls = L % 3;  // this level's slot of nrem2, minval and sumdeg
-        int lmin = INT_MAX;
-        long long lsum = 0;
-        {
-            // S of the level into order[next..), the rest into the next remaining list
-            int *cnt = &ctl->cnt[r % 3];
-            const int64_t lim = (nrem + 31) / 32 * 32;
-            for (int64_t i = tid; i < lim; i += nth) {
-                bool live = false, inS = false;
-                int v = 0;
-                if (i < nrem) {
-                    v = rem[i];
-                    live = rank[v] < 0;
-                    if (live) {
-                        const int d = deg[v];
-                        lmin = min(lmin, d);
-                        lsum += d;
-                        inS = d <= guess;
+        if (!resume) {
+            const int32_t *rem = remsel ? remB : remA;
+            int32_t *rem2 = remsel ? remA : remB;
+            const int ls = L % 3;  // this level's slot of nrem2, minval and sumdeg
+            int lmin = INT_MAX;
+            long long lsum = 0;
+            {
+                // S of the level into order[next..), the rest into the next remaining list
+                int *cnt = &ctl->cnt[r % 3];
+                const int64_t lim = (nrem + 31) / 32 * 32;
+                for (int64_t i = tid; i < lim; i += nth) {
+                    bool live = false, inS = false;
+                    int v = 0;
+                    if (i < nrem) {
+                        v = rem[i];
+                        live = rank[v] < 0;
+                        if (live) {
+                            const int d = deg[v];
+                            lmin = min(lmin, d);
+                            lsum += d;
+                            inS = d <= guess;
+                        }
                     }
+                    const int ps = warp_push(cnt, inS);
+                    if (inS) {
+                        rank[v] = 0;
+                        core[v] = guess;
+                        order[next + ps] = v;
+                    }
+                    const int pk = warp_push(&ctl->nrem2[ls], live && !inS);
+                    if (live && !inS) rem2[pk] = v;
                 }
-                const int ps = warp_push(cnt, inS);
-                if (inS) {
-                    rank[v] = 0;
-                    core[v] = guess;
-                    order[next + ps] = v;
-                }
-                const int pk = warp_push(&ctl->nrem2[ls], live && !inS);
-                if (live && !inS) rem2[pk] = v;
             }
-        }
-        lmin = block_reduce_min<kPeelThreads>(lmin, sh);
-        for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
-        if (lane == 0) shl[threadIdx.x >> 5] = lsum;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            long long bs = 0;
-            for (int w = 0; w < kPeelThreads / 32; w++) bs += shl[w];
-            if (lmin != INT_MAX) atomicMin(&ctl->minval[ls], lmin);
-            if (bs) atomicAdd(&ctl->sumdeg[ls], (unsigned long long)bs);
-            // slot (L + 1) % 3 was last read after level L - 2's barrier, and
-            // every block has since passed level L - 1's
-            if (bid == 0) {
-                const int lz = (L + 1) % 3;
-                ctl->minval[lz] = INT_MAX;
-                ctl->sumdeg[lz] = 0ull;
-                ctl->nrem2[lz] = 0;
-                ctl->cnt[(r + 1) % 3] = 0;
-            }
-        }
-        if (!barrier()) return;
-        nrem = vload(&ctl->nrem2[ls]);
-        remsel = !remsel;
-        L++;
-        int ns = vload(&ctl->cnt[r % 3]);
-        r++;
-        if (ns == 0) {
-            // no live vertex has degree `guess`: the level is at the smallest live degree
-            guess = vload(&ctl->minval[ls]);
-            continue;
-        }
-        k = guess;
-        guess = k + 1;
-        // every block reads the same sum after the barrier and decides alike
-        const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[ls];
-        const int nlive = nrem + ns;
-        const bool to_solo = !solo && live <= kSoloDegrees && nlive <= kSoloLive && ns <= kSoloS;
-        if (!solo && !to_solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && nlive <= kNarrowLive &&
-            ns <= kNarrowS) {
-            if (blockIdx.x >= kNarrowBlocks) return;
-            if (blockIdx.x == 0 && threadIdx.x == 0) {
-                ctl->t_narrow = globaltimer_ns();
-                ctl->r_narrow = t;
-            }
-            nbar = kNarrowBlocks;
-            nblocks = kNarrowBlocks;
-            tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-            nth = (int64_t)kNarrowBlocks * blockDim.x;
-            gwarp = tid >> 5;
-            nwarps = nth >> 5;
-        }
-        if (to_solo) {
-            if (blockIdx.x != 0) return;
+            lmin = block_reduce_min<kPeelThreads>(lmin, sh);
+            for (int o = 16; o; o >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+            if (lane == 0) shl[threadIdx.x >> 5] = lsum;
+            __syncthreads();
             if (threadIdx.x == 0) {
-                ctl->t_solo = globaltimer_ns();
-                ctl->r_solo = t;
+                long long bs = 0;
+                for (int w = 0; w < kPeelThreads / 32; w++) bs += shl[w];
+                if (lmin != INT_MAX) atomicMin(&ctl->minval[ls], lmin);
+                if (bs) atomicAdd(&ctl->sumdeg[ls], (unsigned long long)bs);
+                // slot (L + 1) % 3 was last read after level L - 2's barrier, and
+                // every block has since passed level L - 1's
+                if (bid == 0) {
+                    const int lz = (L + 1) % 3;
+                    ctl->minval[lz] = INT_MAX;
+                    ctl->sumdeg[lz] = 0ull;
+                    ctl->nrem2[lz] = 0;
+                    ctl->cnt[(r + 1) % 3] = 0;
+                }
             }
-            solo = true;
-            tid = threadIdx.x;
-            nth = blockDim.x;
-            gwarp = tid >> 5;
-            nwarps = nth >> 5;
-            nblocks = 1;
-            bid = 0;
+            if (!barrier()) goto done;
+            nrem = vload(&ctl->nrem2[ls]);
+            remsel = !remsel;
+            L++;
+            ns = vload(&ctl->cnt[r % 3]);
+            r++;
+            if (ns == 0) {
+                // no live vertex has degree `guess`: the level is at the smallest live degree
+                guess = vload(&ctl->minval[ls]);
+                continue;
+            }
+            k = guess;
+            guess = k + 1;
+            // every block reads the same sum after the barrier and decides alike
+            const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[ls];
+            const int nlive = nrem + ns;
+            const bool to_solo = !solo && live <= kSoloDegrees && nlive <= kSoloLive && ns <= kSoloS;
+            if (!solo && !to_solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && nlive <= kNarrowLive &&
+                ns <= kNarrowS) {
+                if (blockIdx.x == 0 && threadIdx.x == 0) {
+                    ctl->t_narrow = globaltimer_ns();
+                    ctl->r_narrow = t;
+                }
+                if (handoff) {
+                    // the cluster kernel goes on from the first sub-round at level k
+                    if (blockIdx.x == 0 && threadIdx.x == 0) {
+                        ctl->rs_k = k;
+                        ctl->rs_guess = guess;
+                        ctl->rs_next = next;
+                        ctl->rs_nrem = nrem;
+                        ctl->rs_t = t;
+                        ctl->rs_r = r;
+                        ctl->rs_L = L;
+                        ctl->rs_remsel = remsel ? 1 : 0;
+                        ctl->rs_ns = ns;
+                        ctl->rs_active = 1;
+                    }
+                    goto done;
+                }
+                if (blockIdx.x >= kNarrowBlocks) goto done;
+                nbar = kNarrowBlocks;
+                nblocks = kNarrowBlocks;
+                tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+                nth = (int64_t)kNarrowBlocks * blockDim.x;
+                gwarp = tid >> 5;
+                nwarps = nth >> 5;
+            }
+            if (to_solo) {
+                if (blockIdx.x != 0) goto done;
+                if (threadIdx.x == 0) {
+                    ctl->t_solo = globaltimer_ns();
+                    ctl->r_solo = t;
+                }
+                solo = true;
+                tid = threadIdx.x;
+                nth = blockDim.x;
+                gwarp = tid >> 5;
+                nwarps = nth >> 5;
+                nblocks = 1;
+                bid = 0;
+            }
         }
+        resume = false;
 
         // sub-rounds at level k
         for (;;) {
@@ -335,7 +438,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     const int v = S[i];
                     atomicOr(&bitmap[v >> 5], 1u << (v & 31));
                 }
-                if (!barrier()) return;
+                if (!barrier()) goto done;
                 const int nw = (n + 31) >> 5;
                 const int chunk = (nw + nblocks - 1) / nblocks;
                 const int w_lo = min(nw, bid * chunk), w_hi = min(nw, w_lo + chunk);
@@ -343,7 +446,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 for (int w = w_lo + threadIdx.x; w < w_hi; w += blockDim.x) c += __popc(bitmap[w]);
                 c = block_reduce_sum<kPeelThreads>(c, sh);
                 if (threadIdx.x == 0) blocksums[bid] = c;
-                if (!barrier()) return;
+                if (!barrier()) goto done;
                 int off = 0;
                 for (int b = threadIdx.x; b < bid; b += blockDim.x) off += blocksums[b];
                 off = block_reduce_sum<kPeelThreads>(off, sh);
@@ -361,7 +464,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     if (w < w_hi) bitmap[w] = 0u;
                     off += tot;
                 }
-                if (!barrier()) return;
+                if (!barrier()) goto done;
             }
             // remove S: the vertices whose degree falls to k form the next sub-round.
             // A vertex of degree <= kHeavyDeg is one warp's work (two 32-edge
@@ -414,7 +517,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 if (e - b <= kHeavyDeg) continue;
                 for (int j0 = b; j0 < e; j0 += blockDim.x) remove_edge(j0 + (int)threadIdx.x < e, j0 + threadIdx.x);
             }
-            if (!barrier()) return;
+            if (!barrier()) goto done;
             next += ns;
             t++;
             ns = vload(&ctl->cnt[r % 3]);
@@ -428,6 +531,9 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
         ctl->k = k;
         ctl->t_end = globaltimer_ns();
     }
+done:
+    // no CTA of the cluster leaves while another can still arrive on its mbarrier
+    if (CL) cooperative_groups::this_cluster().sync();
 }
 
 // Final ranks: sort each short sub-round segment of `order` by vertex id (the
@@ -781,22 +887,69 @@ cudaError_t launch_validate(int n, const int32_t *rp, const int32_t *col, int64_
     return cudaGetLastError();
 }
 
+// The narrow stage runs as one cluster of kNarrowBlocks CTAs when this
+// device can hold one (checked once per device: the non-portable cluster size
+// must be allowed and the occupancy query must find room for a cluster).
+static cudaLaunchConfig_t narrow_cluster_config(cudaStream_t s, cudaLaunchAttribute *at) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(kNarrowBlocks);
+    cfg.blockDim = dim3(kPeelThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = s;
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = kNarrowBlocks;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    return cfg;
+}
+
+static bool narrow_cluster_ok(cudaStream_t s) {
+    static int ok[64];  // per device: 0 unknown, 1 yes, 2 no
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
+    if (ok[dev] == 0) {
+        bool yes = cudaFuncSetAttribute(k_peel<true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess;
+        if (yes) {
+            cudaLaunchAttribute at[1];
+            cudaLaunchConfig_t cfg = narrow_cluster_config(s, at);
+            int clusters = 0;
+            yes = cudaOccupancyMaxActiveClusters(&clusters, k_peel<true>, &cfg) == cudaSuccess && clusters >= 1;
+        }
+        (void)cudaGetLastError();  // a refusal above is an answer, not an error of the caller's
+        ok[dev] = yes ? 1 : 2;
+    }
+    return ok[dev] == 1;
+}
+
 cudaError_t launch_peel(int n, const int32_t *rp, const int32_t *col, PeelBufs &b, int sm_count,
                         uint64_t timeout_ns, cudaStream_t s) {
     int per_sm = 0;
-    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel, kPeelThreads, 0);
+    cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_peel<false>, kPeelThreads, 0);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     int blocks = sm_count;  // per_sm >= 1 checked above
     if (blocks > b.max_blocks) blocks = b.max_blocks;
     int32_t *segstart = b.SA;
+    int handoff = (blocks > kNarrowBlocks && narrow_cluster_ok(s)) ? 1 : 0;
     void *args[] = {(void *)&n,        (void *)&rp,      (void *)&col,         (void *)&b.deg,
                     (void *)&b.rank,   (void *)&b.core,  (void *)&b.order,     (void *)&b.remA,
                     (void *)&b.remB,   (void *)&segstart, (void *)&b.bitmap,   (void *)&b.blocksums,
-                    (void *)&b.ctl,    (void *)&b.status, (void *)&timeout_ns};
+                    (void *)&b.ctl,    (void *)&b.status, (void *)&timeout_ns, (void *)&handoff};
     count_launch();
-    e = cudaLaunchCooperativeKernel((void *)k_peel, dim3(blocks), dim3(kPeelThreads), args, 0, s);
+    e = cudaLaunchCooperativeKernel((void *)k_peel<false>, dim3(blocks), dim3(kPeelThreads), args, 0, s);
     if (e != cudaSuccess) return e;
+    if (handoff) {
+        // the narrow stage, if the full grid stopped there (the kernel returns
+        // at once otherwise)
+        cudaLaunchAttribute at[1];
+        cudaLaunchConfig_t cfg = narrow_cluster_config(s, at);
+        count_launch();
+        e = cudaLaunchKernelEx(&cfg, k_peel<true>, n, rp, col, b.deg, b.rank, b.core, b.order, b.remA, b.remB,
+                               segstart, b.bitmap, b.blocksums, b.ctl, b.status, timeout_ns, 0);
+        if (e != cudaSuccess) return e;
+    }
     k_peel_rank<<<2 * sm_count, kRankThreads, 0, s>>>(n, segstart, b.ctl, b.order, b.rank);
     count_launch();
     return cudaGetLastError();
@@ -816,6 +969,7 @@ __global__ void k_peel_init(PeelCtl *ctl, int n) {
     ctl->bar.gen = 0;
     ctl->t_start = ctl->t_narrow = ctl->t_solo = ctl->t_end = 0ull;
     ctl->r_narrow = ctl->r_solo = -1;
+    ctl->rs_active = 0;
 }
 
 cudaError_t launch_peel_init(PeelCtl *ctl, int n, cudaStream_t s) {

@@ -15,6 +15,11 @@ struct PeelCtl {
     // never reached) and at the end, by block 0; stage sub-rounds likewise
     unsigned long long t_start, t_narrow, t_solo, t_end;
     int r_narrow, r_solo;
+    // handoff to the cluster kernel of the narrow stage: set by block 0 of the
+    // full-grid kernel when it stops there (rs_active = 1), read by every CTA
+    // of the cluster: level k, next guess, ranked so far, remaining-list size,
+    // sub-round, phase and level counters, remaining-list buffer, S size
+    int rs_active, rs_k, rs_guess, rs_next, rs_nrem, rs_t, rs_r, rs_L, rs_remsel, rs_ns;
 };
 
 struct PeelBufs {
