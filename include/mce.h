@@ -27,8 +27,12 @@
  *   - Ownership: the engine copies what it needs; caller buffers are never
  *     retained after a call returns.
  *   - Streams: all GPU work of a handle runs on the stream given at create
- *     time (NULL = a stream the handle creates). Every call is synchronous
- *     with respect to the host on return.
+ *     time. NULL = a stream the handle creates, a blocking one, so that its
+ *     work is ordered with work on the legacy default stream (where, for
+ *     instance, an allocator passed below may hand out memory that the
+ *     caller's pending kernels still use). Every call is synchronous with
+ *     respect to the host on return, and mce_destroy waits for the handle's
+ *     stream before it returns any memory to the allocator.
  *   - Threading: one handle must not be used by two host threads at once;
  *     distinct handles are independent.
  */

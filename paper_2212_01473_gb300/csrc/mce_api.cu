@@ -1,6 +1,7 @@
 // C ABI of the engine (include/mce.h): handle creation (validation, peel,
 // orientation, width classes), runs (persistent traversal launches per width
 // class) and results.
+#include <chrono>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -245,12 +246,14 @@ static T *dnew(mce_graph *g, size_t count, std::vector<void *> *track) {
 static void release_prepared(mce_graph *g);
 
 static void release(mce_graph *g) {
+    // nothing of this handle may still run when its memory goes back to the
+    // allocator, which can hand it out at once to work on another stream
+    if (g->stream) cudaStreamSynchronize(g->stream);
     release_prepared(g);
     void *ps[] = {g->out_ptr, g->out_col, g->in_ptr, g->in_col, g->order, g->rank,
                   g->core,    g->outdeg,  g->gid,    g->mixid,  g->scratch};
     for (void *p : ps) dfree(g, p);
     for (int c = 0; c <= kNumClasses; c++) dfree(g, g->class_roots[c]);
-    if (g->stream) cudaStreamSynchronize(g->stream);
     if (g->own_stream && g->stream) cudaStreamDestroy(g->stream);
     delete g;
 }
@@ -303,7 +306,9 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
     if (stream) {
         g->stream = (cudaStream_t)stream;
     } else {
-        CK(cudaStreamCreateWithFlags(&g->stream, cudaStreamNonBlocking));
+        // blocking: ordered with the legacy default stream, whose pending work
+        // may still touch memory the caller's allocator hands to this handle
+        CK(cudaStreamCreateWithFlags(&g->stream, cudaStreamDefault));
         g->own_stream = true;
     }
     CK(cudaGetDevice(&dev));
@@ -387,12 +392,22 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
             !pb.bitmap || !pb.blocksums || !pb.ctl) { rc = fail(MCE_ENOMEM, "device allocation for the peel failed"); goto cleanup; }
         CK(cudaMemsetAsync(pb.bitmap, 0, (((size_t)n + 31) / 32 + 1) * 4, g->stream));
         CK(launch_peel_init(pb.ctl, n, g->stream));
+        const auto peel_t0 = std::chrono::steady_clock::now();
         if (n > 0) CK(launch_peel(n, d_rp, d_col, pb, g->sm_count, kPeelWaitNs, g->stream));
         CK(cudaMemcpyAsync(&h_status, status, 4, cudaMemcpyDeviceToHost, g->stream));
         PeelCtl hctl{};
         CK(cudaMemcpyAsync(&hctl, pb.ctl, sizeof(PeelCtl), cudaMemcpyDeviceToHost, g->stream));
         CK(cudaStreamSynchronize(g->stream));
-        if (h_status & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "degeneracy peel timed out"); goto cleanup; }
+        if (h_status & ST_TIMEOUT) {
+            const double peel_ms =
+                std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - peel_t0).count();
+            rc = fail(MCE_ETIMEOUT,
+                      "degeneracy peel timed out: a barrier wait passed %.0f s (status 0x%x, %.1f ms on the host, "
+                      "n = %d, narrow stage %s, one-block stage %s)",
+                      kPeelWaitNs / 1e9, (unsigned)h_status, peel_ms, n,
+                      hctl.t_narrow ? "reached" : "not reached", hctl.t_solo ? "reached" : "not reached");
+            goto cleanup;
+        }
         if (hctl.next != n) { rc = fail(MCE_ECUDA, "peel ended early (%d of %d ranked)", hctl.next, n); goto cleanup; }
         g->peel_rounds = hctl.rounds;
         {
@@ -489,6 +504,7 @@ extern "C" int mce_batch_create(const int32_t *graph_ptr, int32_t G, const int32
 
 static int grow_scratch(mce_graph *g, size_t bytes) {
     if (bytes <= g->scratch_bytes) return MCE_OK;
+    if (g->scratch && g->stream) cudaStreamSynchronize(g->stream);  // the old scratch is no longer in use
     dfree(g, g->scratch);
     g->scratch = nullptr;
     g->scratch_bytes = 0;

@@ -459,7 +459,7 @@ extern "C" int mce_model_create(const float *params, const mce_allocator *alloc,
     int dev = 0;
     if (stream) {
         m->stream = (cudaStream_t)stream;
-    } else if ((e = cudaStreamCreateWithFlags(&m->stream, cudaStreamNonBlocking)) != cudaSuccess) {
+    } else if ((e = cudaStreamCreateWithFlags(&m->stream, cudaStreamDefault)) != cudaSuccess) {
         delete m;
         return model_fail(MCE_ECUDA, "cudaStreamCreate", e);
     } else {
@@ -545,6 +545,7 @@ extern "C" int mce_model_train_step(mce_model *m, const float *feat, const float
 
 extern "C" void mce_model_destroy(mce_model *m) {
     if (!m) return;
+    cudaStreamSynchronize(m->stream);  // before the memory goes back to the allocator
     if (m->buf) {
         if (m->has_alloc) m->alloc.free(m->buf, m->alloc.ctx);
         else cudaFreeAsync(m->buf, m->stream);

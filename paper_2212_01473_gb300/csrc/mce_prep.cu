@@ -177,8 +177,11 @@ constexpr int kNarrowS = 2 * kNarrowBlocks * (kPeelThreads / 32);
 constexpr long long kSoloDegrees = 32768;
 constexpr int kSoloLive = 2 * kPeelThreads;
 constexpr int kSoloS = 2 * (kPeelThreads / 32);
-// adjacency lists longer than this are removed by a whole block
+// adjacency lists longer than this are removed by a whole block: the warp
+// that meets such a vertex queues it for its own block (up to kHeavyCap a
+// sub-round; past that, the warp removes it alone)
 constexpr int kHeavyDeg = 64;
+constexpr int kHeavyCap = 1024;
 
 // ------------------------------------------------ narrow stage as a cluster
 // The narrow stage's kNarrowBlocks blocks can run as one thread-block
@@ -248,13 +251,15 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     __shared__ int sh[64];
     __shared__ long long shl[32];
     __shared__ __align__(8) unsigned long long cl_mbar;
+    __shared__ int hv_cnt;             // this block's queued heavy vertices in the current sub-round
+    __shared__ int32_t hv_list[kHeavyCap];
     if (CL && vload(&ctl->rs_active) == 0) return;  // the full grid finished alone
     const unsigned mb = (unsigned)__cvta_generic_to_shared(&cl_mbar);
     unsigned mb_phase = 0;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int64_t nth = (int64_t)gridDim.x * blockDim.x;
     const int lane = threadIdx.x & 31;
-    int64_t gwarp = tid >> 5, nwarps = nth >> 5;
+    int64_t nwarps = nth >> 5;
     int nblocks = gridDim.x, bid = blockIdx.x;
     bool solo = false;
     unsigned nbar = gridDim.x;  // blocks meeting at grid barriers
@@ -284,6 +289,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     // the cluster kernel starts at the first sub-round of the level where the
     // full grid stopped
     bool resume = CL;
+    if (threadIdx.x == 0) hv_cnt = 0;  // published by the first barrier's block barrier
     if (CL) {
         if (threadIdx.x == 0) mbar_init(mb, kNarrowBlocks);
         cooperative_groups::this_cluster().sync();  // every mbarrier is ready before the first arrival
@@ -403,7 +409,6 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 nblocks = kNarrowBlocks;
                 tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
                 nth = (int64_t)kNarrowBlocks * blockDim.x;
-                gwarp = tid >> 5;
                 nwarps = nth >> 5;
             }
             if (to_solo) {
@@ -415,7 +420,6 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                 solo = true;
                 tid = threadIdx.x;
                 nth = blockDim.x;
-                gwarp = tid >> 5;
                 nwarps = nth >> 5;
                 nblocks = 1;
                 bid = 0;
@@ -468,7 +472,8 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             }
             // remove S: the vertices whose degree falls to k form the next sub-round.
             // A vertex of degree <= kHeavyDeg is one warp's work (two 32-edge
-            // chunks in flight); a longer adjacency list is strided over a block.
+            // chunks in flight); a longer adjacency list is strided over the
+            // block whose warp met it, so no block walks all of S.
             int *cn = &ctl->cnt[r % 3];
             int32_t *S2 = S + ns;
             auto remove_edge = [&](bool valid, int j) {
@@ -485,10 +490,24 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     S2[p] = u;
                 }
             };
-            for (int64_t i = gwarp; i < ns; i += nwarps) {
+            // warps numbered block-interleaved: vertex i goes to block
+            // i % nblocks, so the few hubs of a short sub-round land in
+            // different blocks
+            const int64_t iw = (int64_t)(threadIdx.x >> 5) * nblocks + bid;
+            for (int64_t i = iw; i < ns; i += nwarps) {
                 const int v = S[i];
                 const int b = rp[v], e = rp[v + 1];
-                if (e - b > kHeavyDeg) continue;
+                if (e - b > kHeavyDeg) {
+                    int q = 0;
+                    if (lane == 0) q = atomicAdd(&hv_cnt, 1);
+                    q = __shfl_sync(0xffffffffu, q, 0);
+                    if (q < kHeavyCap) {
+                        if (lane == 0) hv_list[q] = v;
+                    } else {
+                        for (int j0 = b; j0 < e; j0 += 32) remove_edge(j0 + lane < e, j0 + lane);
+                    }
+                    continue;
+                }
                 for (int j0 = b; j0 < e; j0 += 64) {
                     const int ja = j0 + lane, jb = ja + 32;
                     const bool va = ja < e, vb = jb < e;
@@ -511,12 +530,16 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     }
                 }
             }
-            for (int64_t i = bid; i < ns; i += nblocks) {
-                const int v = S[i];
+            // the heavy vertices this block's warps queued, each strided over the block
+            __syncthreads();
+            const int nh = min(hv_cnt, kHeavyCap);
+            for (int h = 0; h < nh; h++) {
+                const int v = hv_list[h];
                 const int b = rp[v], e = rp[v + 1];
-                if (e - b <= kHeavyDeg) continue;
                 for (int j0 = b; j0 < e; j0 += blockDim.x) remove_edge(j0 + (int)threadIdx.x < e, j0 + threadIdx.x);
             }
+            __syncthreads();
+            if (threadIdx.x == 0) hv_cnt = 0;
             if (!barrier()) goto done;
             next += ns;
             t++;
