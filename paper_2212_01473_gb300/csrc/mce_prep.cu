@@ -252,8 +252,16 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     __shared__ long long shl[32];
     __shared__ __align__(8) unsigned long long cl_mbar;
     __shared__ int hv_cnt;             // this block's queued heavy vertices in the current sub-round
-    __shared__ int32_t hv_list[kHeavyCap];
+    __shared__ int32_t hv_beg[kHeavyCap], hv_end[kHeavyCap];  // the queued vertices' adjacency ranges
     if (CL && vload(&ctl->rs_active) == 0) return;  // the full grid finished alone
+    // The rings of stage counters (S sizes, remaining-list sizes, level minima
+    // and degree sums): in global memory on the full grid; in the cluster, in
+    // CTA 0's shared memory, which every CTA reaches through distributed
+    // shared memory (no L2 round trip for a push or for reading a size).
+    __shared__ int cl_cnt[3], cl_nrem2[3], cl_minval[3];
+    __shared__ unsigned long long cl_sumdeg[3];
+    int *c_cnt = ctl->cnt, *c_nrem2 = ctl->nrem2, *c_minval = ctl->minval;
+    unsigned long long *c_sumdeg = ctl->sumdeg;
     const unsigned mb = (unsigned)__cvta_generic_to_shared(&cl_mbar);
     unsigned mb_phase = 0;
     int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -292,7 +300,22 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
     if (threadIdx.x == 0) hv_cnt = 0;  // published by the first barrier's block barrier
     if (CL) {
         if (threadIdx.x == 0) mbar_init(mb, kNarrowBlocks);
-        cooperative_groups::this_cluster().sync();  // every mbarrier is ready before the first arrival
+        if (blockIdx.x == 0 && threadIdx.x == 0)
+            for (int i = 0; i < 3; i++) {
+                cl_cnt[i] = ctl->cnt[i];
+                cl_nrem2[i] = ctl->nrem2[i];
+                cl_minval[i] = ctl->minval[i];
+                cl_sumdeg[i] = ctl->sumdeg[i];
+            }
+        // every mbarrier and CTA 0's counters are ready before the first use
+        cooperative_groups::this_cluster().sync();
+        {
+            cooperative_groups::cluster_group cl = cooperative_groups::this_cluster();
+            c_cnt = cl.map_shared_rank(cl_cnt, 0);
+            c_nrem2 = cl.map_shared_rank(cl_nrem2, 0);
+            c_minval = cl.map_shared_rank(cl_minval, 0);
+            c_sumdeg = cl.map_shared_rank(cl_sumdeg, 0);
+        }
         k = ctl->rs_k;
         guess = ctl->rs_guess;
         next = ctl->rs_next;
@@ -321,7 +344,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             long long lsum = 0;
             {
                 // S of the level into order[next..), the rest into the next remaining list
-                int *cnt = &ctl->cnt[r % 3];
+                int *cnt = &c_cnt[r % 3];
                 const int64_t lim = (nrem + 31) / 32 * 32;
                 for (int64_t i = tid; i < lim; i += nth) {
                     bool live = false, inS = false;
@@ -342,7 +365,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                         core[v] = guess;
                         order[next + ps] = v;
                     }
-                    const int pk = warp_push(&ctl->nrem2[ls], live && !inS);
+                    const int pk = warp_push(&c_nrem2[ls], live && !inS);
                     if (live && !inS) rem2[pk] = v;
                 }
             }
@@ -353,33 +376,33 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             if (threadIdx.x == 0) {
                 long long bs = 0;
                 for (int w = 0; w < kPeelThreads / 32; w++) bs += shl[w];
-                if (lmin != INT_MAX) atomicMin(&ctl->minval[ls], lmin);
-                if (bs) atomicAdd(&ctl->sumdeg[ls], (unsigned long long)bs);
+                if (lmin != INT_MAX) atomicMin(&c_minval[ls], lmin);
+                if (bs) atomicAdd(&c_sumdeg[ls], (unsigned long long)bs);
                 // slot (L + 1) % 3 was last read after level L - 2's barrier, and
                 // every block has since passed level L - 1's
                 if (bid == 0) {
                     const int lz = (L + 1) % 3;
-                    ctl->minval[lz] = INT_MAX;
-                    ctl->sumdeg[lz] = 0ull;
-                    ctl->nrem2[lz] = 0;
-                    ctl->cnt[(r + 1) % 3] = 0;
+                    c_minval[lz] = INT_MAX;
+                    c_sumdeg[lz] = 0ull;
+                    c_nrem2[lz] = 0;
+                    c_cnt[(r + 1) % 3] = 0;
                 }
             }
             if (!barrier()) goto done;
-            nrem = vload(&ctl->nrem2[ls]);
+            nrem = vload(&c_nrem2[ls]);
             remsel = !remsel;
             L++;
-            ns = vload(&ctl->cnt[r % 3]);
+            ns = vload(&c_cnt[r % 3]);
             r++;
             if (ns == 0) {
                 // no live vertex has degree `guess`: the level is at the smallest live degree
-                guess = vload(&ctl->minval[ls]);
+                guess = vload(&c_minval[ls]);
                 continue;
             }
             k = guess;
             guess = k + 1;
             // every block reads the same sum after the barrier and decides alike
-            const long long live = (long long)*(volatile unsigned long long *)&ctl->sumdeg[ls];
+            const long long live = (long long)*(volatile unsigned long long *)&c_sumdeg[ls];
             const int nlive = nrem + ns;
             const bool to_solo = !solo && live <= kSoloDegrees && nlive <= kSoloLive && ns <= kSoloS;
             if (!solo && !to_solo && nbar > (unsigned)kNarrowBlocks && live <= kNarrowDegrees && nlive <= kNarrowLive &&
@@ -432,7 +455,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             if (bid == 0 && threadIdx.x == 0) {
                 // cnt[(r+1)%3] held the size read two phases ago, by every block
                 // before the last barrier
-                ctl->cnt[(r + 1) % 3] = 0;
+                c_cnt[(r + 1) % 3] = 0;
                 segstart[t] = next;
             }
             int32_t *S = order + next;
@@ -474,7 +497,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             // A vertex of degree <= kHeavyDeg is one warp's work (two 32-edge
             // chunks in flight); a longer adjacency list is strided over the
             // block whose warp met it, so no block walks all of S.
-            int *cn = &ctl->cnt[r % 3];
+            int *cn = &c_cnt[r % 3];
             int32_t *S2 = S + ns;
             auto remove_edge = [&](bool valid, int j) {
                 bool push = false;
@@ -502,7 +525,10 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
                     if (lane == 0) q = atomicAdd(&hv_cnt, 1);
                     q = __shfl_sync(0xffffffffu, q, 0);
                     if (q < kHeavyCap) {
-                        if (lane == 0) hv_list[q] = v;
+                        if (lane == 0) {
+                            hv_beg[q] = b;
+                            hv_end[q] = e;
+                        }
                     } else {
                         for (int j0 = b; j0 < e; j0 += 32) remove_edge(j0 + lane < e, j0 + lane);
                     }
@@ -534,8 +560,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             __syncthreads();
             const int nh = min(hv_cnt, kHeavyCap);
             for (int h = 0; h < nh; h++) {
-                const int v = hv_list[h];
-                const int b = rp[v], e = rp[v + 1];
+                const int b = hv_beg[h], e = hv_end[h];
                 for (int j0 = b; j0 < e; j0 += blockDim.x) remove_edge(j0 + (int)threadIdx.x < e, j0 + threadIdx.x);
             }
             __syncthreads();
@@ -543,7 +568,7 @@ __global__ void __launch_bounds__(kPeelThreads) k_peel(int n, const int32_t *rp,
             if (!barrier()) goto done;
             next += ns;
             t++;
-            ns = vload(&ctl->cnt[r % 3]);
+            ns = vload(&c_cnt[r % 3]);
             r++;
             if (ns == 0) break;
         }
