@@ -609,6 +609,9 @@ def run_ours(args):
                                  "ipx": "IPX (pivot from P u X)"}[args.pivot],
                        "ms_prep": results[-1].ms_prep, "ms_traverse": results[-1].ms_traverse,
                        "classes": st["classes"], "peel_rounds": st["peel_rounds"],
+                       "peel_stages": {"ms": st["peel_stage_ms"], "sub_rounds": st["peel_stage_rounds"],
+                                       "stages": "full grid, narrow (16 CTAs), one block",
+                                       "narrow_as_cluster": bool(st["peel_cluster"])},
                        "l2": "flushed before every step by a 256 MiB device write",
                        "step": "mce_create (validate, degeneracy peel, orient) + mce_run (traversal) on a "
                                "device-resident CSR",

@@ -289,6 +289,9 @@ typedef struct {
      * device time (globaltimer, ms) and sub-rounds */
     double peel_stage_ms[3];
     int32_t peel_stage_rounds[3];
+    /* 1 when the peel's narrow stage ran as one 16-CTA thread-block cluster,
+     * 0 when it ran on 16 blocks of the full grid or was not reached */
+    int32_t peel_cluster;
 } mce_stats;
 
 int mce_get_stats(const mce_graph *g, mce_stats *out);

@@ -209,6 +209,7 @@ struct mce_graph {
     int64_t peel_rounds = 0;
     double peel_stage_ms[3] = {0, 0, 0};
     int32_t peel_stage_rounds[3] = {0, 0, 0};
+    int32_t peel_cluster = 0;  // the narrow stage ran as a cluster
     uint64_t create_launches = 0;  // kernels launched by create
     mce_stats last{};              // facts of the last run
     Tuned tuned[kNumClasses];      // per width class, from mce_autotune
@@ -422,6 +423,7 @@ static int create_impl(const int32_t *graph_ptr_in, int32_t G, const int32_t *ro
             g->peel_stage_rounds[0] = std::min(rn, rs);
             g->peel_stage_rounds[1] = hctl.r_narrow >= 0 ? rs - rn : 0;
             g->peel_stage_rounds[2] = hctl.r_solo >= 0 ? hctl.rounds - rs : 0;
+            g->peel_cluster = hctl.rs_active ? 1 : 0;
         }
 
         // -------------------------------------------------------- orientation
@@ -911,6 +913,7 @@ static int collect_run(mce_graph *g, RunPlan *P, mce_result *per_graph, uint64_t
         st.peel_stage_ms[i] = g->peel_stage_ms[i];
         st.peel_stage_rounds[i] = g->peel_stage_rounds[i];
     }
+    st.peel_cluster = g->peel_cluster;
     g->last = st;
     if (hflags[1] & ST_TIMEOUT) { rc = fail(MCE_ETIMEOUT, "a traversal wait exceeded %lld ms with no progress", (long long)P->opts.timeout_ms); goto cleanup; }
     if (hflags[1] & ST_BUDGET) { rc = fail(MCE_EBUDGET, "the run exceeded its time budget of %lld ms", (long long)P->opts.run_budget_ms); goto cleanup; }

@@ -67,7 +67,8 @@ class mce_stats(ctypes.Structure):
                 ("class_ms", ctypes.c_double * 16), ("kernel_launches", ctypes.c_uint64),
                 ("peel_rounds", ctypes.c_int64), ("phase_cycles", ctypes.c_uint64 * 9),
                 ("phase_counts", ctypes.c_uint64 * 9), ("class_wp_min", ctypes.c_int32 * 16),
-                ("peel_stage_ms", ctypes.c_double * 3), ("peel_stage_rounds", ctypes.c_int32 * 3)]
+                ("peel_stage_ms", ctypes.c_double * 3), ("peel_stage_rounds", ctypes.c_int32 * 3),
+                ("peel_cluster", ctypes.c_int32)]
 
 
 PHASES = ["setup", "pivot", "branch", "leaf", "partition", "donate", "idle", "backtrack", "compact_entry"]
@@ -349,6 +350,7 @@ def mce_get_stats(h: Handle) -> dict:
         "peel_rounds": int(st.peel_rounds),
         "peel_stage_ms": [float(x) for x in st.peel_stage_ms],
         "peel_stage_rounds": [int(x) for x in st.peel_stage_rounds],
+        "peel_cluster": int(st.peel_cluster),
         "phase_cycles": {PHASES[i]: int(st.phase_cycles[i]) for i in range(len(PHASES))},
         "phase_counts": {PHASES[i]: int(st.phase_counts[i]) for i in range(len(PHASES))},
     }

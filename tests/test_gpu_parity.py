@@ -390,3 +390,21 @@ def test_phase_counters_variant_gives_the_same_results():
     # one setup per task: every root with later neighbours, plus every received subtree
     _, _, outd = mce.mce_get_order(mce.mce_create(g.row_ptr, g.col))
     assert st1["phase_counts"]["setup"] == int((np.asarray(outd) > 0).sum()) + r1.donations
+
+
+def test_peel_narrow_stage_runs_as_cluster():
+    # gen.peel_stages() reaches every stage of the peel; on a GB300 the narrow
+    # stage runs as one 16-CTA thread-block cluster, and the results stay exact
+    g = gen.peel_stages()
+    core_o, rank_o, _, _ = oracle.peel(g.row_ptr, g.col)
+    h = mce.mce_create(g.row_ptr, g.col)
+    try:
+        core, rank, _ = mce.mce_get_order(h)
+        mce.mce_run(h)
+        st = mce.mce_get_stats(h)
+    finally:
+        mce.mce_destroy(h)
+    assert np.array_equal(core, core_o) and np.array_equal(rank, rank_o)
+    assert st["peel_stage_rounds"][1] > 0
+    if torch.cuda.get_device_capability() >= (10, 0):
+        assert st["peel_cluster"] == 1
