@@ -1171,10 +1171,6 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                         return found;
                     };
                     for (;;) {
-                        if ((++iters & 1023u) == 0 && __any_sync(FULL, g.lane == 0 && tick())) {
-                            over_budget = true;
-                            break;
-                        }
                         if (kcentr) {
                             kcentr = false;
                             // pivot over P u X_P: lane u scores |P n N(u)|, ties to the
@@ -1382,6 +1378,12 @@ __global__ void __launch_bounds__(32 * kTravMaxWarps) k_traverse(DevGraph G, Dev
                         kcentr = true;
                         t_nodes++;
                         pc.stop(PH_PARTITION);
+                        // the budget and heartbeat check, on descents only: between two
+                        // descents a compact walk takes at most about 33 steps
+                        if ((++iters & 255u) == 0 && __any_sync(FULL, g.lane == 0 && tick())) {
+                            over_budget = true;
+                            break;
+                        }
                         continue;
                     }
                     // the compact subtree is done; the wide loop backtracks (the
