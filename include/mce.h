@@ -285,7 +285,7 @@ typedef struct {
     /* narrowest row width whose roots the launch ran: one launch takes the
      * roots of every width class of at most 12 words, widest first */
     int32_t class_wp_min[MCE_STATS_MAX_CLASSES];
-    /* the handle's degeneracy peel by stage (full grid, 16 blocks, one block):
+    /* the handle's degeneracy peel by stage (full grid, narrow stage of 16 CTAs, one block):
      * device time (globaltimer, ms) and sub-rounds */
     double peel_stage_ms[3];
     int32_t peel_stage_rounds[3];

@@ -163,9 +163,12 @@ __device__ void block_bitonic(int *a, int len) {
 //
 // As the remaining graph shrinks, fewer blocks go on. A level start may narrow
 // the grid when the live degree sum, the live vertices and the level's S are
-// all small: at most kNarrowDegrees, kNarrowLive and kNarrowS. Blocks
-// kNarrowBlocks and up then return, and the rest meet at cheaper barriers (the
-// dense core's many short sub-rounds are barrier-bound). Within kSoloDegrees,
+// all small: at most kNarrowDegrees, kNarrowLive and kNarrowS. The full grid
+// then hands the rest to one cluster of kNarrowBlocks CTAs (k_peel<true>,
+// below) whose barriers stay inside the cluster, or, where such a cluster
+// cannot be placed, blocks kNarrowBlocks and up return and the rest meet at
+// grid barriers among fewer blocks (the dense core's many short sub-rounds are
+// barrier-bound). Within kSoloDegrees,
 // kSoloLive and kSoloS, block 0 finishes alone with block barriers. A warp
 // removes one vertex at a time, so the stage must not start while S sets of
 // thousands of vertices can still come: the live vertices bound every later
