@@ -168,11 +168,11 @@ __device__ void block_bitonic(int *a, int len) {
 // below) whose barriers stay inside the cluster, or, where such a cluster
 // cannot be placed, blocks kNarrowBlocks and up return and the rest meet at
 // grid barriers among fewer blocks (the dense core's many short sub-rounds are
-// barrier-bound). Within kSoloDegrees,
-// kSoloLive and kSoloS, block 0 finishes alone with block barriers. A warp
-// removes one vertex at a time, so the stage must not start while S sets of
-// thousands of vertices can still come: the live vertices bound every later
-// S. Removal order and core numbers are the same either way.
+// barrier-bound). Within kSoloDegrees, kSoloLive and kSoloS, block 0 finishes
+// alone with block barriers. A warp removes one vertex at a time, so the stage
+// must not start while S sets of thousands of vertices can still come: the
+// live vertices bound every later S. Removal order and core numbers are the
+// same either way.
 constexpr long long kNarrowDegrees = 1ll << 22;
 constexpr int kNarrowBlocks = 16;
 constexpr int kNarrowLive = 2 * kNarrowBlocks * kPeelThreads;
