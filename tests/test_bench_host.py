@@ -72,3 +72,39 @@ def test_reference_arm_prints_the_contract_line():
     assert d["config"]["workload"] == "er_2000"
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["value"] == d["value"]
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["e2e"]["d2h_bytes_per_step"] == 0
+
+
+class MCEError(RuntimeError):
+    """Stands in for the engine's error type (bench.py matches it by name)."""
+
+
+def test_one_gpu_run_measures_once_more_after_an_engine_error(monkeypatch):
+    calls = []
+
+    def fake_run_ours(args):
+        calls.append(getattr(args, "retried_after", None))
+        if len(calls) == 1:
+            raise MCEError("MCE_ETIMEOUT: a wait gave up")
+        return 0
+
+    monkeypatch.setattr(bench, "run_ours", fake_run_ours)
+    monkeypatch.setattr(bench.sys, "argv", ["bench.py"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    assert bench.main() == 0
+    # the second measurement knows which error it follows, for its line
+    assert calls == [None, "MCEError: MCE_ETIMEOUT: a wait gave up"]
+
+
+def test_other_errors_are_not_retried(monkeypatch):
+    def fake_run_ours(args):
+        raise ValueError("not an engine error")
+
+    monkeypatch.setattr(bench, "run_ours", fake_run_ours)
+    monkeypatch.setattr(bench.sys, "argv", ["bench.py"])
+    monkeypatch.delenv("WORLD_SIZE", raising=False)
+    try:
+        bench.main()
+    except ValueError:
+        pass
+    else:
+        raise AssertionError("a non-engine error must propagate")
